@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the MGVI sampling hot path on the 2-D correlated field.
+
+Workload (one step): 2-D 512x512 periodic correlated field with the
+power-spectrum model, exponential response and Poisson counts (rate 10 exp(cf)),
+FP32 vectors with FP64 CG reductions, a batch of B=32 MGVI sample systems
+linearised at one expansion point: the MGVI right-hand side
+b = xi' + J^T sqrt(w) eta, then 100 CG iterations of M_p = J^T N^-1 J + 1 on all
+B systems.  Unit: metric-vector products/s (B * 100 per step).  Inputs are
+larger than L2 (the CG working set is ~0.3 GB) and L2 is also flushed between
+timed steps (outside the per-step CUDA events).
+
+--impl reference times the FP64 CPU oracle (numpy) on a bounded sample of the
+same workload.  Multi-GPU runs are independent replicas (the path has no
+exchange step): every rank runs the same workload and value = all ranks'
+products / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "metric-vector products/s & HBM roofline frac; serve p50/p99 vs plain at 1e-5 rel"
+UNIT = "metric-vector products/s"
+GRID = (512, 512)
+BATCH = 32
+CG_ITERS = 100
+WORKLOAD = "cf2d_512x512_power_poisson_mgvi_cg100"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    return ap.parse_args()
+
+
+def config(batch):
+    return {"workload": WORKLOAD, "grid": list(GRID), "batch": batch, "cg_iters": CG_ITERS,
+            "amplitude": "power-spectrum model, 256 log-|k| bins", "likelihood": "poisson, rate 10 exp(cf)",
+            "l2": "inputs larger than L2 (CG working set ~0.3 GB) and L2 flushed between timed steps"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- oracle leg
+def oracle_setup():
+    from oracle import amplitude as oamp
+    from oracle.cf import CFModel
+    from oracle.likelihood import poisson_weight
+    pr = oamp.AmpPrior(**synth.AMP_PRIOR)
+    om = CFModel(GRID, tuple(1.0 / s for s in GRID), prior=pr)
+    xi_p = synth.normal(synth.SEED_POS, om.latent_size)
+    w = poisson_weight(om.forward(xi_p), 10.0)
+    return om, xi_p, w
+
+
+def oracle_step(om, xi_p, w, seed, iters):
+    """One bounded sample of the workload on the CPU: one system's MGVI
+    right-hand side and `iters` CG iterations (one metric product each)."""
+    from oracle.cg import cg
+    from oracle.metric import metric_apply, mgvi_rhs
+    g = np.random.default_rng(seed)
+    b = mgvi_rhs(om, xi_p, w, g.standard_normal(om.latent_size), g.standard_normal(om.n_field))
+    cg(lambda p: metric_apply(om, xi_p, w, p), b, rtol=0.0, maxiter=iters)
+    return iters
+
+
+def cpu_baseline(target_s=15.0):
+    om, xi_p, w = oracle_setup()
+    t0 = time.perf_counter()
+    n = 0
+    k = 0
+    while time.perf_counter() - t0 < target_s:
+        n += oracle_step(om, xi_p, w, 1000 + k, 20)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} systems x (MGVI rhs + 20 CG iterations) of the 512x512 Poisson metric, "
+                      f"FP64 numpy oracle, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    om, xi_p, w = oracle_setup()
+    iters = 20
+    for i in range(args.warmup):
+        oracle_step(om, xi_p, w, 2000 + i, iters)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(om, xi_p, w, 3000 + i, iters)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * iters / tot
+    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"each step: one system's MGVI rhs + {iters} CG iterations of the 512x512 Poisson "
+                    f"metric, FP64 numpy oracle, single thread"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(1),
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+# ----------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world):
+    import ctypes as C
+
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+    from paper_2402_16683_gb300 import _lib
+
+    lib = _lib.load()
+    lib.nre_launch_count.restype = C.c_ulonglong
+    lib.nre_launch_count.argtypes = []
+    lib.nre_prof_enable.argtypes = [C.c_int]
+    lib.nre_prof_report.argtypes = [C.c_char_p, C.c_size_t]
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = args.batch
+    plan = nre.CorrelatedField(GRID, tuple(1.0 / s for s in GRID), amplitude="power",
+                               prior=dict(synth.AMP_PRIOR), dtype=torch.float32)
+    lik = nre.Likelihood("poisson", scale=10.0)
+    xi_p = torch.tensor(synth.normal(synth.SEED_POS, plan.latent_size), dtype=torch.float32, device=dev)
+    M = nre.Metric(plan, lik, plan.pad(xi_p[None])[0], max_batch=B)
+    g = np.random.default_rng(synth.SEED_RHS + 100 * rank)
+    xi_prime = plan.pad(torch.tensor(g.standard_normal((B, plan.latent_size)), dtype=torch.float32, device=dev))
+    eta = torch.tensor(g.standard_normal((B, plan.n_field)), dtype=torch.float32, device=dev)
+    b = torch.zeros_like(xi_prime)
+    x = torch.zeros_like(xi_prime)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        M.mgvi_rhs(xi_prime, eta, out=b)
+        _, its, rel, st = M.cg(b, rtol=0.0, maxiter=CG_ITERS, x=x)
+        return its
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    lib.nre_prof_enable(1)
+    n0 = lib.nre_launch_count()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    barrier()
+    launches = lib.nre_launch_count() - n0
+    lib.nre_prof_enable(0)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    buf = C.create_string_buffer(1 << 16)
+    _lib.check(lib.nre_prof_report(buf, len(buf)))
+    kern = json.loads(buf.value.decode())
+    t_local = ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    units = world * args.steps * B * CG_ITERS
+    value = units / t_max
+
+    # dominant kernel: largest total device time in the timed region
+    name, (cnt, kms, kbytes) = max(kern.items(), key=lambda kv: kv[1][1])
+    peak, peak_kind = peaks()
+    achieved = kbytes / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "launches": int(cnt), "avg_launch_us": 1e3 * kms / cnt,
+                "algorithmic_bytes_per_launch": kbytes / cnt}
+    kernels = {k: {"launches": int(v[0]), "ms": v[1], "share": v[1] / sum(u[1] for u in kern.values()),
+                   "GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None} for k, v in kern.items()}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier)
+    if rank != 0:
+        return
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config(B), "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+           "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
+           "cg_iterations": its[:1]}
+    print(json.dumps(out), flush=True)
+
+
+def run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier):
+    """The same step through the public API with pinned host buffers: the
+    step's excitations are copied in and the samples copied out inside the
+    timed region."""
+    import torch
+    B = xi_prime.shape[0]
+    dev = xi_prime.device
+    h_xi = torch.empty_like(xi_prime, device="cpu").pin_memory()
+    h_eta = torch.empty_like(eta, device="cpu").pin_memory()
+    h_x = torch.empty_like(x, device="cpu").pin_memory()
+    h_xi.copy_(xi_prime)
+    h_eta.copy_(eta)
+    d_xi = torch.empty_like(xi_prime)
+    d_eta = torch.empty_like(eta)
+
+    def e2e_step():
+        d_xi.copy_(h_xi, non_blocking=True)
+        d_eta.copy_(h_eta, non_blocking=True)
+        M.mgvi_rhs(d_xi, d_eta, out=b)
+        M.cg(b, rtol=0.0, maxiter=CG_ITERS, x=x)
+        h_x.copy_(x, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e_steps = max(1, min(args.steps, 5))
+    ev = []
+    for _ in range(e_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    barrier()
+    e_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    e_t = e_ms / 1e3
+    if world > 1:
+        t = torch.tensor([e_t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_t = float(t.item())
+    return {"value": world * e_steps * B * CG_ITERS / e_t, "unit": UNIT,
+            "h2d_bytes_per_step": int(h_xi.numel() * 4 + h_eta.numel() * 4),
+            "d2h_bytes_per_step": int(h_x.numel() * 4)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * nre.h - C ABI of the GB300 metric-vector-product / CG-sampling library
+ * (NIFTy.re hot path, arXiv:2402.16683).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an int status (NRE_OK = 0 or one of NRE_E*); on error
+ *   nre_last_error() returns a thread-local message.  No C++ exception crosses
+ *   the ABI.  Invalid arguments are rejected before any work is enqueued.
+ * - Array arguments named `xi`, `v`, `s`, ... are DEVICE pointers to contiguous
+ *   C-order arrays of the plan's dtype (NRE_F32: float, NRE_F64: double),
+ *   16-byte aligned.  Arguments documented as "host" are host pointers.
+ * - A batch of latent vectors is [batch][stride] with `stride` from
+ *   *_latent_layout(); entries stride[latent_size:] are padding that the library
+ *   neither reads nor writes.  A batch of position-space fields is [batch][N].
+ * - The caller owns every buffer it passes; the library keeps no caller pointer
+ *   after a call returns (serving: until the request is polled complete).
+ *   Plans own their device workspaces and constant tables; free them with the
+ *   matching *_destroy.
+ * - Work is enqueued on the given cudaStream_t (NULL = legacy default stream) in
+ *   stream order, without host synchronisation, except where a call documents a
+ *   synchronisation (cg_solve's host scalars, serving).
+ * - A plan may be used by one host thread at a time.
+ */
+#ifndef NRE_H
+#define NRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nre_stream_t; /* == cudaStream_t */
+
+/* ------------------------------------------------------------------ status */
+enum {
+  NRE_OK = 0,
+  NRE_EINVAL = 1,    /* bad argument (null pointer, size, dtype, layout)       */
+  NRE_ENOMEM = 2,    /* device or host allocation failed                       */
+  NRE_ECUDA = 3,     /* a CUDA call failed (message holds cudaGetErrorString)  */
+  NRE_ENOTCONV = 4,  /* cg_solve: some system missed rtol within maxiter       */
+  NRE_ETIMEDOUT = 5, /* a bounded device-side wait gave up                     */
+  NRE_EBUSY = 6,     /* serving: request can never fit the HBM budget          */
+  NRE_EAGAIN = 7     /* serving: request still pending                         */
+};
+
+enum { NRE_F32 = 0, NRE_F64 = 1 };
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *nre_last_error(void);
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int nre_version(void);
+
+/* ============================================================ correlated field
+ * Sec. "Gaussian Processes": s = FT o sqrt(P) o xi on a regular periodic grid
+ * (the example uses unit total volume, distances = 1/d).  Reading used here:
+ * FT is the unnormalised multi-dimensional Hartley transform
+ *     H[z]_k = sum_x z_x cas(2 pi sum_d k_d x_d / N_d),  cas = cos + sin,
+ * and the model (log-field, before any response) is
+ *     cf(xi) = offset_mean + H(A_full * xi_field),
+ * where A_full[k] = A(|k|) for k != 0 and A_full[0] = offset_std (the zero mode
+ * of xi_field is the offset excitation).  k_d = m_d / (N_d dx_d) with the folded
+ * index m_d (Nyquist folded to +N_d/2).
+ *
+ * Amplitude kinds:
+ *  NRE_AMP_ARRAY         A_full given per pixel (host array, harmonic C order,
+ *                        entry 0 is the zero mode); no hyper-parameters.
+ *  NRE_AMP_MATERN_FIXED  A_full[k] = (1 + (|k|/k0)^2)^-gamma for k != 0,
+ *                        scaled so that sum_{k!=0} A^2 = variance;
+ *                        A_full[0] = zero_mode; no hyper-parameters.
+ *  NRE_AMP_POWER_MODEL   the non-parametric power-spectrum model of Sec.
+ *                        "Gaussian Processes" (add_fluctuations: fluctuations,
+ *                        loglogavgslope, flexibility, asperity; offset (mean,
+ *                        std)): log-normal / normal hyper-parameters, an
+ *                        integrated Wiener process on n_bins log-|k| bins,
+ *                        normalised to total variance theta_fluct^2.  Computed
+ *                        in FP64 for both dtypes.
+ *
+ * Latent layout of one sample (float/double):
+ *   [0, N)                         xi_field, harmonic C order
+ *   [N, N + n_hyper)               POWER_MODEL only: xi_fluct, xi_slope,
+ *                                  xi_flex, xi_asp, xi1[n_bins-1], xi2[n_bins-1]
+ *   [latent_size, stride)          padding (stride is a multiple of 64)
+ */
+enum { NRE_AMP_ARRAY = 0, NRE_AMP_MATERN_FIXED = 1, NRE_AMP_POWER_MODEL = 2 };
+
+typedef struct {
+  int kind;                 /* NRE_AMP_*                                      */
+  const double *amp_array;  /* ARRAY: host, N values (copied at create)       */
+  double k0, gamma, variance, zero_mode;            /* MATERN_FIXED           */
+  double fluct_mean, fluct_std, slope_mean, slope_std;   /* POWER_MODEL       */
+  double flex_mean, flex_std, asp_mean, asp_std;         /* POWER_MODEL       */
+  double offset_mean;       /* added to cf in position space (all kinds)      */
+  double offset_std;        /* POWER_MODEL: A_full[0]                          */
+  int n_bins;               /* POWER_MODEL: number of log-|k| bins (2..1024)  */
+} nre_cf_amp_params;
+
+typedef struct nre_cf_plan nre_cf_plan;
+
+/* Create a correlated-field plan.  ndim in 1..3; every shape[d] a power of two
+ * in [4, 4096] (shapes in [4, 4096]); spacing[d] > 0 with the same total
+ * length N_d * spacing[d] on every axis (isotropic |k|).  dtype NRE_F32 or
+ * NRE_F64.  Allocates the plan's constant tables on the current device. */
+int cf_create(nre_cf_plan **plan, int ndim, const int64_t *shape,
+              const double *spacing, const nre_cf_amp_params *amp, int dtype);
+int cf_destroy(nre_cf_plan *plan);
+/* N (pixels), n_hyper, latent_size = N + n_hyper and the per-sample stride. */
+int cf_latent_layout(const nre_cf_plan *plan, int64_t *n_field, int64_t *n_hyper,
+                     int64_t *latent_size, int64_t *stride);
+/* Back-compatible short form: latent_size only. */
+int cf_latent_size(const nre_cf_plan *plan, int64_t *latent_size);
+
+/* s[b] = cf(xi[b]) for b < batch.  xi: [batch][stride], s: [batch][N]. */
+int cf_forward(nre_cf_plan *plan, const void *xi, void *s, int batch,
+               nre_stream_t stream);
+/* jv[b] = (d cf / d xi at xi_p[b]) v[b].  xi_p, v: [batch][stride]; jv: [batch][N]. */
+int cf_jvp(nre_cf_plan *plan, const void *xi_p, const void *v, void *jv,
+           int batch, nre_stream_t stream);
+/* g[b] = (d cf / d xi at xi_p[b])^T ct[b].  ct: [batch][N]; g: [batch][stride]. */
+int cf_vjp(nre_cf_plan *plan, const void *xi_p, const void *ct, void *g,
+           int batch, nre_stream_t stream);
+
+/* Host-only helper (no GPU needed): log-|k| bin of every harmonic pixel as the
+ * POWER_MODEL uses it (-1 at k = 0), C order, into host array out[N]. */
+int cf_bin_map(int ndim, const int64_t *shape, const double *spacing,
+               int n_bins, int32_t *out);
+
+/* ===================================================================== ICR
+ * Sec. "Gaussian Processes", ICR paragraph: iterative charted refinement, a GP
+ * on a deformed space refined coarse-to-fine from nearest neighbours.  Reading
+ * used here: a 2-D log-radial chart, level l with n_l = n0 2^l points per axis
+ * at u = (i+1/2)/n_l, v = (j+1/2)/n_l, r = r_min (r_max/r_min)^u, phi = 2 pi v;
+ * Matern-3/2 kernel (rho, var); level 0 is s_0 = chol(K0) xi_0; each coarse
+ * pixel's 3x3 neighbourhood (radial window clamped to the chart, angular axis
+ * periodic) predicts its 2x2 children with R = K_fc K_cc^-1 and adds
+ * chol(K_ff - R K_cf) xi_children.  Matrices are assembled in FP64 on the host.
+ * Latent layout: xi_0, ..., xi_L (each n_l x n_l, C order), then padding to
+ * `stride`.  Output: the finest level, n_L x n_L.
+ */
+typedef struct { int n0; double r_min, r_max; } icr_chart_params;
+typedef struct { double rho, var; } icr_kernel_params;
+typedef struct nre_icr_plan nre_icr_plan;
+
+/* n0 even in [4, 64], n_levels in [1, 10] refinements, n0 * 2^n_levels <= 4096. */
+int icr_create(nre_icr_plan **plan, const icr_chart_params *chart,
+               const icr_kernel_params *kernel, int n_levels, int dtype);
+int icr_destroy(nre_icr_plan *plan);
+int icr_latent_layout(const nre_icr_plan *plan, int64_t *n_out,
+                      int64_t *latent_size, int64_t *stride);
+/* s[b] = ICR(xi[b]); xi: [batch][stride], s: [batch][n_L * n_L]. */
+int icr_forward(nre_icr_plan *plan, const void *xi, void *s, int batch,
+                nre_stream_t stream);
+/* The ICR map is linear: jv = ICR(v) (xi_p is accepted for symmetry, unused). */
+int icr_jvp(nre_icr_plan *plan, const void *xi_p, const void *v, void *jv,
+            int batch, nre_stream_t stream);
+/* g[b] = ICR^T ct[b]; ct: [batch][n_L^2], g: [batch][stride]. */
+int icr_vjp(nre_icr_plan *plan, const void *xi_p, const void *ct, void *g,
+            int batch, nre_stream_t stream);
+
+/* ============================================================== likelihood
+ * Sec. "Building Up Complex Models": Poissonian(data).amend(forward) with
+ * forward = exp(cf); Sec. "Performance": N^-1 is the Fisher metric of the
+ * likelihood.  Folded Fisher weights w at the expansion point (data never enter
+ * the metric):
+ *   NRE_LIK_GAUSS, NRE_RESP_EXP:       w = mask * exp(cf_p)^2 / sigma^2
+ *   NRE_LIK_GAUSS, NRE_RESP_IDENTITY:  w = mask / sigma^2
+ *   NRE_LIK_POISSON (rate = scale * exp(cf)):  w = scale * exp(cf_p)
+ */
+enum { NRE_LIK_GAUSS = 0, NRE_LIK_POISSON = 1 };
+enum { NRE_RESP_EXP = 0, NRE_RESP_IDENTITY = 1 };
+typedef struct nre_lik nre_lik;
+
+/* mask_host: NULL (every pixel observed) or host array of n_data values in
+ * {0, 1} (copied).  sigma_or_scale: noise std (GAUSS) or rate scale (POISSON). */
+int lik_create(nre_lik **lik, int kind, int response, const double *mask_host,
+               int64_t n_data, double sigma_or_scale);
+int lik_destroy(nre_lik *lik);
+
+/* ================================================================= metric
+ * Sec. "Performance": M_p = F_p + 1 with F_p = J^T N^-1 J, the benchmarked
+ * operator that dominates a VI minimisation.  metric_create linearises the
+ * model at xi_p (one latent vector, device) and precomputes w(p), A(p) and the
+ * amplitude linearisation; it owns copies of everything it needs and
+ * workspaces for up to max_batch tangents.  model_plan must outlive it.
+ */
+enum { NRE_MODEL_CF = 0, NRE_MODEL_ICR = 1 };
+typedef struct nre_metric nre_metric;
+
+int metric_create(nre_metric **m, int model_kind, void *model_plan,
+                  const nre_lik *lik, const void *xi_p, int max_batch,
+                  nre_stream_t stream);
+int metric_destroy(nre_metric *m);
+/* out[b] = v[b] + J^T (w * J v[b]), v and out [batch][stride], batch <= max_batch.
+ * out may not alias v. */
+int metric_apply(nre_metric *m, const void *v, void *out, int batch,
+                 nre_stream_t stream);
+
+/* Sec. "Variational Inference": MGVI samples N(p, M_p^-1).  Right-hand side
+ * with covariance M_p:  b = xi_prime + J^T (sqrt(w) * eta).
+ * xi_prime, b: [batch][stride]; eta: [batch][N data].  The sample pair is
+ * p +/- M_p^-1 b. */
+int mgvi_rhs(nre_metric *m, const void *xi_prime, const void *eta, void *b,
+             int batch, nre_stream_t stream);
+
+/* Sec. "Variational Inference" (draw_linear_kwargs, cg_kwargs maxiter): solve
+ * M_p x[b] = b[b] for every b < batch by conjugate gradients, x_0 = 0, with
+ * FP64 inner products and alpha/beta.  A system stops (its x frozen) once
+ * ||r|| <= rtol ||b|| (recursive residual) or after maxiter iterations; rtol = 0
+ * runs exactly maxiter iterations.  iters_out[batch], relres_out[batch] are
+ * HOST arrays (may be NULL), written after a synchronisation of `stream`.
+ * Returns NRE_ENOTCONV if rtol > 0 and some system missed it. */
+int cg_solve(nre_metric *m, const void *b, void *x, int batch, double rtol,
+             int maxiter, int *iters_out, double *relres_out,
+             nre_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NRE_H */

@@ -100,7 +100,7 @@ class CFModel:
         out[:self.n_field] = (self.a_full(hp) * r).ravel()
         if self.prior is not None:
             nz = self.bins.index >= 0
-            gA = np.zeros(self.prior.n_bins)
-            np.add.at(gA, self.bins.index[nz], (fp * r)[nz])
+            gA = np.bincount(self.bins.index[nz], weights=(fp * r)[nz],
+                             minlength=self.prior.n_bins)
             out[self.n_field:] = amp_mod.vjp(hp, gA, self.prior, self.bins)
         return out

@@ -1,0 +1,293 @@
+"""Thin Python binding of the C ABI (include/nre.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory and
+the current stream.  Latent batches are [batch, stride] CUDA tensors (stride
+from the plan; entries beyond ``latent_size`` are padding the library neither
+reads nor writes); position-space batches are [batch, N].
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import check
+
+_DT = {torch.float32: L.NRE_F32, torch.float64: L.NRE_F64}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def bin_map(shape, spacing, n_bins=256):
+    """Host-only: log-|k| bin of every harmonic pixel (-1 at k = 0)."""
+    lib = L.load()
+    shp = (C.c_int64 * len(shape))(*shape)
+    sp = (C.c_double * len(shape))(*spacing)
+    out = np.zeros(int(np.prod(shape)), dtype=np.int32)
+    check(lib.cf_bin_map(len(shape), shp, sp, n_bins, out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out.reshape(shape)
+
+
+class CorrelatedField:
+    """Correlated-field plan (cf_create).
+
+    amplitude: "power" (non-parametric power-spectrum model, ``prior`` dict with
+    fluct / slope / flex / asp (mean, std) pairs, offset_mean, offset_std,
+    n_bins), "matern" (fixed spectrum, ``matern`` dict k0 / gamma / variance /
+    zero_mode) or a per-pixel numpy array (A_full, harmonic C order).
+    """
+
+    def __init__(self, shape, spacing=None, amplitude="power", prior=None, matern=None,
+                 offset_mean=0.0, dtype=torch.float32):
+        lib = L.load()
+        self.shape = tuple(int(s) for s in shape)
+        self.spacing = tuple(float(s) for s in (spacing or [1.0 / s for s in self.shape]))
+        self.dtype = dtype
+        a = L.CFAmpParams()
+        self._arr = None
+        if isinstance(amplitude, np.ndarray):
+            a.kind = L.NRE_AMP_ARRAY
+            self._arr = np.ascontiguousarray(amplitude, dtype=np.float64).ravel()
+            a.amp_array = self._arr.ctypes.data_as(C.POINTER(C.c_double))
+            a.offset_mean = offset_mean
+        elif amplitude == "matern":
+            m = dict(k0=8.0, gamma=1.5, variance=1.0, zero_mode=0.0)
+            m.update(matern or {})
+            a.kind = L.NRE_AMP_MATERN_FIXED
+            a.k0, a.gamma, a.variance, a.zero_mode = m["k0"], m["gamma"], m["variance"], m["zero_mode"]
+            a.offset_mean = offset_mean
+        elif amplitude == "power":
+            pr = dict(fluct=(1.0, 0.5), slope=(-3.0, 0.5), flex=(1.0, 0.5), asp=(0.1, 0.05),
+                      offset_mean=0.0, offset_std=1.0, n_bins=256)
+            pr.update(prior or {})
+            a.kind = L.NRE_AMP_POWER_MODEL
+            a.fluct_mean, a.fluct_std = pr["fluct"]
+            a.slope_mean, a.slope_std = pr["slope"]
+            a.flex_mean, a.flex_std = pr["flex"]
+            a.asp_mean, a.asp_std = pr["asp"]
+            a.offset_mean, a.offset_std = pr["offset_mean"], pr["offset_std"]
+            a.n_bins = pr["n_bins"]
+        else:
+            raise ValueError(f"unknown amplitude {amplitude!r}")
+        h = C.c_void_p()
+        shp = (C.c_int64 * len(self.shape))(*self.shape)
+        sp = (C.c_double * len(self.shape))(*self.spacing)
+        check(lib.cf_create(C.byref(h), len(self.shape), shp, sp, C.byref(a), _DT[dtype]))
+        self.handle = h
+        nf, nh, ls, st = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib.cf_latent_layout(h, C.byref(nf), C.byref(nh), C.byref(ls), C.byref(st)))
+        self.n_field, self.n_hyper, self.latent_size, self.stride = nf.value, nh.value, ls.value, st.value
+        self.n_data = self.n_field
+        self.kind = L.NRE_MODEL_CF
+
+    def __del__(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.cf_destroy(self.handle)
+            self.handle = None
+
+    # layout helpers ---------------------------------------------------
+    def pad(self, x):
+        """[B, latent_size] -> zero-padded [B, stride] (a copy)."""
+        out = torch.zeros(x.shape[0], self.stride, dtype=x.dtype, device=x.device)
+        out[:, :self.latent_size] = x
+        return out
+
+    def unpad(self, x):
+        return x[:, :self.latent_size]
+
+    # raw calls ----------------------------------------------------------
+    def forward(self, xi):
+        B = xi.shape[0]
+        _need(xi, self.dtype, (B, self.stride), "xi")
+        s = torch.empty(B, self.n_field, dtype=self.dtype, device=xi.device)
+        check(L.load().cf_forward(self.handle, _ptr(xi), _ptr(s), B, _stream()))
+        return s
+
+    def jvp(self, xi_p, v):
+        B = v.shape[0]
+        _need(xi_p, self.dtype, (B, self.stride), "xi_p")
+        _need(v, self.dtype, (B, self.stride), "v")
+        out = torch.empty(B, self.n_field, dtype=self.dtype, device=v.device)
+        check(L.load().cf_jvp(self.handle, _ptr(xi_p), _ptr(v), _ptr(out), B, _stream()))
+        return out
+
+    def vjp(self, xi_p, ct):
+        B = ct.shape[0]
+        _need(xi_p, self.dtype, (B, self.stride), "xi_p")
+        _need(ct, self.dtype, (B, self.n_field), "ct")
+        g = torch.zeros(B, self.stride, dtype=self.dtype, device=ct.device)
+        check(L.load().cf_vjp(self.handle, _ptr(xi_p), _ptr(ct), _ptr(g), B, _stream()))
+        return g
+
+    def __call__(self, xi):
+        """Differentiable cf(xi): backward runs cf_vjp, forward-mode AD runs cf_jvp."""
+        return _ModelFn.apply(xi, self)
+
+
+class ICR:
+    """Iterative-charted-refinement plan (icr_create) on the log-radial chart."""
+
+    def __init__(self, n0=8, n_levels=7, r_min=0.1, r_max=1.0, rho=0.1, var=1.0, dtype=torch.float32):
+        lib = L.load()
+        self.dtype = dtype
+        ch = L.ICRChartParams(n0, r_min, r_max)
+        kp = L.ICRKernelParams(rho, var)
+        h = C.c_void_p()
+        check(lib.icr_create(C.byref(h), C.byref(ch), C.byref(kp), n_levels, _DT[dtype]))
+        self.handle = h
+        no, ls, st = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib.icr_latent_layout(h, C.byref(no), C.byref(ls), C.byref(st)))
+        self.n_data, self.latent_size, self.stride = no.value, ls.value, st.value
+        self.n_field = self.n_data
+        self.n_out = self.n_data
+        self.kind = L.NRE_MODEL_ICR
+
+    def __del__(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.icr_destroy(self.handle)
+            self.handle = None
+
+    pad = CorrelatedField.pad
+    unpad = CorrelatedField.unpad
+
+    def forward(self, xi):
+        B = xi.shape[0]
+        _need(xi, self.dtype, (B, self.stride), "xi")
+        s = torch.empty(B, self.n_out, dtype=self.dtype, device=xi.device)
+        check(L.load().icr_forward(self.handle, _ptr(xi), _ptr(s), B, _stream()))
+        return s
+
+    def jvp(self, xi_p, v):
+        B = v.shape[0]
+        _need(v, self.dtype, (B, self.stride), "v")
+        out = torch.empty(B, self.n_out, dtype=self.dtype, device=v.device)
+        check(L.load().icr_jvp(self.handle, _ptr(v), _ptr(v), _ptr(out), B, _stream()))
+        return out
+
+    def vjp(self, xi_p, ct):
+        B = ct.shape[0]
+        _need(ct, self.dtype, (B, self.n_out), "ct")
+        g = torch.zeros(B, self.stride, dtype=self.dtype, device=ct.device)
+        check(L.load().icr_vjp(self.handle, _ptr(ct), _ptr(ct), _ptr(g), B, _stream()))
+        return g
+
+    def __call__(self, xi):
+        return _ModelFn.apply(xi, self)
+
+
+class _ModelFn(torch.autograd.Function):
+    """autograd.Function over a model plan: forward -> *_forward, backward ->
+    *_vjp (hand-written adjoint kernels), forward-mode jvp -> *_jvp."""
+
+    @staticmethod
+    def forward(xi, plan):
+        return plan.forward(xi.contiguous())
+
+    @staticmethod
+    def setup_context(ctx, inputs, output):
+        xi, plan = inputs
+        ctx.plan = plan
+        ctx.save_for_backward(xi)
+        ctx.save_for_forward(xi)
+
+    @staticmethod
+    def backward(ctx, g):
+        (xi,) = ctx.saved_tensors
+        return ctx.plan.vjp(xi.contiguous(), g.contiguous()), None
+
+    @staticmethod
+    def jvp(ctx, xi_t, _plan_t):
+        (xi,) = ctx.saved_tensors
+        return ctx.plan.jvp(xi.contiguous(), xi_t.contiguous())
+
+
+class Likelihood:
+    """lik_create: "gauss" (sigma, optional 0/1 mask, response "exp"/"identity")
+    or "poisson" (rate = scale * exp(cf))."""
+
+    def __init__(self, kind="gauss", sigma=0.1, scale=10.0, mask=None, response="exp", n_data=0):
+        lib = L.load()
+        k = L.NRE_LIK_GAUSS if kind == "gauss" else L.NRE_LIK_POISSON
+        r = L.NRE_RESP_EXP if response == "exp" else L.NRE_RESP_IDENTITY
+        val = sigma if kind == "gauss" else scale
+        mp = None
+        if mask is not None:
+            self._mask = np.ascontiguousarray(mask, dtype=np.float64).ravel()
+            mp = self._mask.ctypes.data_as(C.POINTER(C.c_double))
+            n_data = self._mask.size
+        h = C.c_void_p()
+        check(lib.lik_create(C.byref(h), k, r, mp, int(n_data), float(val)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.lik_destroy(self.handle)
+            self.handle = None
+
+
+class Metric:
+    """metric_create: M_p = J^T N^-1 J + 1 linearised at xi_p ([stride] tensor)."""
+
+    def __init__(self, model, lik, xi_p, max_batch=1):
+        lib = L.load()
+        self.model = model
+        self.lik = lik
+        xi_p = xi_p.reshape(-1)
+        _need(xi_p, model.dtype, (model.stride,), "xi_p")
+        h = C.c_void_p()
+        check(lib.metric_create(C.byref(h), model.kind, model.handle, lik.handle, _ptr(xi_p),
+                                int(max_batch), _stream()))
+        self.handle = h
+        self.max_batch = max_batch
+
+    def __del__(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.metric_destroy(self.handle)
+            self.handle = None
+
+    def apply(self, v, out=None):
+        B = v.shape[0]
+        _need(v, self.model.dtype, (B, self.model.stride), "v")
+        if out is None:
+            out = torch.zeros_like(v)
+        check(L.load().metric_apply(self.handle, _ptr(v), _ptr(out), B, _stream()))
+        return out
+
+    def mgvi_rhs(self, xi_prime, eta, out=None):
+        B = xi_prime.shape[0]
+        _need(xi_prime, self.model.dtype, (B, self.model.stride), "xi_prime")
+        _need(eta, self.model.dtype, (B, self.model.n_data), "eta")
+        if out is None:
+            out = torch.zeros_like(xi_prime)
+        check(L.load().mgvi_rhs(self.handle, _ptr(xi_prime), _ptr(eta), _ptr(out), B, _stream()))
+        return out
+
+    def cg(self, b, rtol=1e-5, maxiter=100, x=None, raise_on_notconv=False):
+        """Solve M x = b per row; returns (x, iterations[B], relres[B], status)."""
+        B = b.shape[0]
+        _need(b, self.model.dtype, (B, self.model.stride), "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        it = (C.c_int * B)()
+        rr = (C.c_double * B)()
+        st = L.load().cg_solve(self.handle, _ptr(b), _ptr(x), B, float(rtol), int(maxiter), it, rr, _stream())
+        if st != L.NRE_OK and (st != L.NRE_ENOTCONV or raise_on_notconv):
+            check(st)
+        return x, list(it), list(rr), st

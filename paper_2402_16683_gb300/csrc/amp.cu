@@ -1,0 +1,264 @@
+// Non-parametric amplitude model sqrt(P) of the correlated field, FP64 for both
+// plan dtypes: forward, JVP and VJP.  One CTA per sample, one thread per log-|k|
+// bin; the integrated Wiener process is two prefix sums, its adjoint two suffix
+// sums.
+//
+// Sec. "Gaussian Processes" (add_fluctuations with fluctuations,
+// loglogavgslope, flexibility, asperity; non_parametric_kind = "power").  The
+// paper defers the equations to its citations; the reading implemented here:
+//   theta_fl, theta_flex, theta_asp log-normal with the given (mean, std) of the
+//   variable itself, theta_slope normal;  D_i = l_i - l_{i-1};
+//   x_i = x_{i-1} + theta_flex sqrt(D_i) xi1_i,
+//   y_i = y_{i-1} + D_i (x_{i-1} + x_i)/2 + theta_flex sqrt(D_i^3/12 + theta_asp D_i) xi2_i,
+//   tau_i = theta_slope (l_i - l_0) + y_i,  a_i = exp(tau_i / 2),
+//   A_i = theta_fl a_i / sqrt(sum_b n_b a_b^2)   (n_b: non-zero modes in bin b).
+#include "cf_internal.cuh"
+
+namespace nre {
+
+namespace {
+
+__device__ double scan_incl(double v, double* buf) {
+  const int i = threadIdx.x;
+  __syncthreads();
+  buf[i] = v;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const double t = (i >= o) ? buf[i - o] : 0.0;
+    __syncthreads();
+    buf[i] += t;
+    __syncthreads();
+  }
+  return buf[i];
+}
+
+__device__ double scan_suffix(double v, double* buf) {
+  const int i = threadIdx.x, n = blockDim.x;
+  __syncthreads();
+  buf[i] = v;
+  __syncthreads();
+  for (int o = 1; o < n; o <<= 1) {
+    const double t = (i + o < n) ? buf[i + o] : 0.0;
+    __syncthreads();
+    buf[i] += t;
+    __syncthreads();
+  }
+  return buf[i];
+}
+
+struct Th {
+  double fl, sl, fx, as;
+};
+
+template <typename T>
+__device__ Th thetas(const AmpPrior& pr, const T* h) {
+  Th t;
+  t.fl = exp(pr.mu_fl + pr.s_fl * double(h[0]));
+  t.sl = pr.sl_m + pr.sl_s * double(h[1]);
+  t.fx = exp(pr.mu_fx + pr.s_fx * double(h[2]));
+  t.as = exp(pr.mu_as + pr.s_as * double(h[3]));
+  return t;
+}
+
+template <typename T>
+__global__ void k_amp_forward(AmpPrior pr, const T* h, int64_t hs, double* state) {
+  __shared__ double buf[1024];
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const T* hb = h + b * hs;
+  double* st = state + (int64_t)b * amp_state_size(nb);
+  const Th th = thetas(pr, hb);
+  const bool act = i < nb;
+  const double l = act ? pr.centres[i] : 0.0;
+  const double l0 = pr.centres[0];
+  const double d = (act && i > 0) ? l - pr.centres[i - 1] : 0.0;
+  const double xi1 = (act && i > 0) ? double(hb[4 + i - 1]) : 0.0;
+  const double xi2 = (act && i > 0) ? double(hb[4 + nb - 1 + i - 1]) : 0.0;
+  const double x = scan_incl(th.fx * sqrt(d) * xi1, buf);
+  const double xprev = i > 0 ? buf[i - 1] : 0.0;
+  const double c = (act && i > 0) ? sqrt(d * d * d / 12.0 + th.as * d) : 0.0;
+  const double incy = (act && i > 0) ? d * (xprev + x) / 2.0 + th.fx * c * xi2 : 0.0;
+  const double y = scan_incl(incy, buf);
+  const double tau = th.sl * (l - l0) + y;
+  const double a = act ? exp(tau / 2.0) : 0.0;
+  const double S = block_sum(act ? pr.counts[i] * a * a : 0.0, red);
+  if (act) {
+    st[as_a(nb) + i] = a;
+    st[as_c(nb) + i] = c;
+    st[as_A(nb) + i] = th.fl * a / sqrt(S);
+    st[as_xi1(nb) + i] = xi1;
+    st[as_xi2(nb) + i] = xi2;
+  }
+  if (i == 0) {
+    st[AS_THFL] = th.fl;
+    st[AS_THSL] = th.sl;
+    st[AS_THFX] = th.fx;
+    st[AS_THAS] = th.as;
+    st[AS_S] = S;
+  }
+}
+
+template <typename T>
+__global__ void k_amp_jvp(AmpPrior pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
+                          double* dA) {
+  __shared__ double buf[1024];
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const double* st = state + b * ss;
+  const T* g = dh + b * dhs;
+  const double th_fl = st[AS_THFL], th_fx = st[AS_THFX], th_as = st[AS_THAS], S = st[AS_S];
+  const double dth_fl = th_fl * pr.s_fl * double(g[0]);
+  const double dth_sl = pr.sl_s * double(g[1]);
+  const double dth_fx = th_fx * pr.s_fx * double(g[2]);
+  const double dth_as = th_as * pr.s_as * double(g[3]);
+  const bool act = i < nb;
+  const double l = act ? pr.centres[i] : 0.0;
+  const double l0 = pr.centres[0];
+  const double d = (act && i > 0) ? l - pr.centres[i - 1] : 0.0;
+  const double xi1 = act ? st[as_xi1(nb) + i] : 0.0;
+  const double xi2 = act ? st[as_xi2(nb) + i] : 0.0;
+  const double c = act ? st[as_c(nb) + i] : 0.0;
+  const double a = act ? st[as_a(nb) + i] : 0.0;
+  const double dxi1 = (act && i > 0) ? double(g[4 + i - 1]) : 0.0;
+  const double dxi2 = (act && i > 0) ? double(g[4 + nb - 1 + i - 1]) : 0.0;
+  const double sd = sqrt(d);
+  const double dx = scan_incl((act && i > 0) ? dth_fx * sd * xi1 + th_fx * sd * dxi1 : 0.0, buf);
+  const double dxprev = i > 0 ? buf[i - 1] : 0.0;
+  double incy = 0.0;
+  if (act && i > 0) {
+    const double dc = d * dth_as / (2.0 * c);
+    incy = d * (dxprev + dx) / 2.0 + (dth_fx * c + th_fx * dc) * xi2 + th_fx * c * dxi2;
+  }
+  const double dy = scan_incl(incy, buf);
+  const double dtau = dth_sl * (l - l0) + dy;
+  const double da = a * dtau / 2.0;
+  const double dS = block_sum(act ? pr.counts[i] * 2.0 * a * da : 0.0, red);
+  const double rs = 1.0 / sqrt(S);
+  if (act) dA[(int64_t)b * nb + i] = dth_fl * a * rs + th_fl * da * rs - th_fl * a * dS * rs * rs * rs / 2.0;
+}
+
+template <typename T>
+__global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const double* partials,
+                          int nparts, const T* base, int64_t bhs, T* out, int64_t ohs) {
+  __shared__ double buf[1024];
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const double* st = state + b * ss;
+  const bool act = i < nb;
+  double gA = 0.0;
+  if (act) {
+    const double* pp = partials + (int64_t)b * nparts * nb + i;
+    for (int c = 0; c < nparts; ++c) gA += pp[(int64_t)c * nb];
+  }
+  const double th_fl = st[AS_THFL], th_fx = st[AS_THFX], th_as = st[AS_THAS], S = st[AS_S];
+  const double rs = 1.0 / sqrt(S);
+  const double a = act ? st[as_a(nb) + i] : 0.0;
+  const double c = act ? st[as_c(nb) + i] : 0.0;
+  const double xi1 = act ? st[as_xi1(nb) + i] : 0.0;
+  const double xi2 = act ? st[as_xi2(nb) + i] : 0.0;
+  const double n = act ? pr.counts[i] : 0.0;
+  const double l = act ? pr.centres[i] : 0.0;
+  const double l0 = pr.centres[0];
+  const double d = (act && i > 0) ? l - pr.centres[i - 1] : 0.0;
+  const double d_next = (i + 1 < nb) ? pr.centres[i + 1] - l : 0.0;
+
+  const double ga_dot = block_sum(gA * a, red);
+  const double g_thfl = ga_dot * rs;
+  const double g_a = th_fl * rs * gA - th_fl * rs * rs * rs * n * a * ga_dot;
+  const double g_tau = g_a * a / 2.0;
+  const double g_thsl = block_sum(g_tau * (l - l0), red);
+  const double y_hat = scan_suffix(g_tau, buf);
+  const double y_hat_next = (i + 1 < (int)blockDim.x) ? buf[i + 1] : 0.0;
+  double x_dir = 0.0, g_xi2 = 0.0, p_fx = 0.0, p_as = 0.0;
+  if (act && i >= 1) {
+    x_dir += y_hat * d / 2.0;
+    g_xi2 = y_hat * th_fx * c;
+    p_fx += y_hat * c * xi2;
+    p_as += y_hat * th_fx * xi2 * d / (2.0 * c);
+  }
+  if (act && i + 1 < nb) x_dir += y_hat_next * d_next / 2.0;
+  const double x_hat = scan_suffix(x_dir, buf);
+  double g_xi1 = 0.0;
+  if (act && i >= 1) {
+    g_xi1 = x_hat * th_fx * sqrt(d);
+    p_fx += x_hat * sqrt(d) * xi1;
+  }
+  const double g_thfx = block_sum(p_fx, red);
+  const double g_thas = block_sum(p_as, red);
+  T* o = out + b * ohs;
+  const T* bb = base ? base + b * bhs : nullptr;
+  if (act && i >= 1) {
+    const int j1 = 4 + i - 1, j2 = 4 + nb - 1 + i - 1;
+    o[j1] = T((bb ? double(bb[j1]) : 0.0) + g_xi1);
+    o[j2] = T((bb ? double(bb[j2]) : 0.0) + g_xi2);
+  }
+  if (i == 0) {
+    const double g4[4] = {g_thfl * th_fl * pr.s_fl, g_thsl * pr.sl_s, g_thfx * th_fx * pr.s_fx,
+                          g_thas * th_as * pr.s_as};
+    for (int j = 0; j < 4; ++j) o[j] = T((bb ? double(bb[j]) : 0.0) + g4[j]);
+  }
+}
+
+int amp_threads(int nb) { return (nb + 31) / 32 * 32; }
+
+}  // namespace
+
+AmpPrior amp_prior_of(const nre_cf_plan* p) {
+  AmpPrior a;
+  a.mu_fl = p->mu_fl;
+  a.s_fl = p->s_fl;
+  a.mu_fx = p->mu_fx;
+  a.s_fx = p->s_fx;
+  a.mu_as = p->mu_as;
+  a.s_as = p->s_as;
+  a.sl_m = p->sl_m;
+  a.sl_s = p->sl_s;
+  a.centres = p->centres.as<double>();
+  a.counts = p->counts.as<double>();
+  a.nb = p->n_bins;
+  return a;
+}
+
+template <typename T>
+int amp_forward(const AmpPrior& pr, const T* h, int64_t hs, double* state, int B, cudaStream_t st) {
+  prof_begin("amp_forward", (double)B * pr.nb * (2 * sizeof(T) + 5 * 8), st);
+  k_amp_forward<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, h, hs, state);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
+            double* dA, int B, cudaStream_t st) {
+  prof_begin("amp_jvp", (double)B * pr.nb * (2 * sizeof(T) + 8) + (ss ? B : 1) * pr.nb * 40.0, st);
+  k_amp_jvp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, dh, dhs, dA);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* partials,
+            int nparts, const T* base_h, int64_t bhs, T* out_h, int64_t ohs, int B,
+            cudaStream_t st) {
+  prof_begin("amp_vjp", (double)B * pr.nb * (8.0 * nparts + (base_h ? 4 : 2) * sizeof(T)) +
+                            (ss ? B : 1) * pr.nb * 40.0, st);
+  k_amp_vjp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, partials, nparts, base_h, bhs,
+                                                  out_h, ohs);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+#define NRE_INST(T)                                                                              \
+  template int amp_forward<T>(const AmpPrior&, const T*, int64_t, double*, int, cudaStream_t);   \
+  template int amp_jvp<T>(const AmpPrior&, const double*, int64_t, const T*, int64_t, double*,   \
+                          int, cudaStream_t);                                                    \
+  template int amp_vjp<T>(const AmpPrior&, const double*, int64_t, const double*, int, const T*, \
+                          int64_t, T*, int64_t, int, cudaStream_t);
+NRE_INST(float)
+NRE_INST(double)
+#undef NRE_INST
+
+}  // namespace nre

@@ -1,0 +1,255 @@
+// Correlated-field plan internals: geometry, amplitude lookup and the fused
+// prologue / middle / epilogue operations applied around the Hartley sweeps.
+//
+// The unnormalised multi-dimensional Hartley transform (Sec. "Gaussian
+// Processes", FT of s = FT o sqrt(P) o xi, read as a DHT) is computed as
+//     H = P o H_0 o ... o H_{D-1},
+// one 1-D DHT per axis plus the reflection combination
+//     D = 2:  P = (I + R_0 + R_1 - R_0 R_1) / 2
+//     D = 3:  P = (R_0 + R_1 + R_2 - R_0 R_1 R_2) / 2
+// (R_d negates the index on axis d), which follows from
+// cas(sum_d a_d) = Re[(1 - i) prod_d exp(i a_d)] and
+// exp(i a) = [(1 + i) cas(a) + (1 - i) cas(-a)] / 2.  P commutes with every H_d,
+// so it is applied in a row sweep (last axis), where a CTA holds every row of a
+// reflection orbit.  Each 1-D DHT of two real lines a, b is one complex FFT of
+// a + i b followed by the Hartley unpack.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace nre {
+
+enum { AMPV_FIXED = 0, AMPV_MODEL = 1 };
+
+// Per-sample amplitude model state (doubles), see amp.cu.
+enum { AS_THFL = 0, AS_THSL = 1, AS_THFX = 2, AS_THAS = 3, AS_S = 4, AS_HDR = 8 };
+inline __host__ __device__ int amp_state_size(int nb) { return AS_HDR + 5 * nb; }
+inline __host__ __device__ int as_a(int nb) { return AS_HDR; }
+inline __host__ __device__ int as_c(int nb) { return AS_HDR + nb; }
+inline __host__ __device__ int as_A(int nb) { return AS_HDR + 2 * nb; }
+inline __host__ __device__ int as_xi1(int nb) { return AS_HDR + 3 * nb; }
+inline __host__ __device__ int as_xi2(int nb) { return AS_HDR + 4 * nb; }
+
+struct Geo {
+  int ndim;
+  int l2[3];  // log2 of the axis lengths, last axis fastest
+  // squared folded harmonic radius q = sum_d m_d^2 of pixel `flat`
+  __device__ __forceinline__ int q_of(int64_t flat) const {
+    int q = 0;
+    for (int d = ndim - 1; d >= 0; --d) {
+      const int n = 1 << l2[d];
+      const int i = (int)(flat & (n - 1));
+      flat >>= l2[d];
+      const int m = i <= (n >> 1) ? i : i - n;
+      q += m * m;
+    }
+    return q;
+  }
+};
+
+// Amplitude A_full at a harmonic pixel.
+template <typename T>
+struct AmpView {
+  int mode;                // AMPV_FIXED or AMPV_MODEL
+  const T* afull;          // FIXED: [N]
+  const double* abin;      // MODEL: A per bin of sample b at abin + b * astride
+  int64_t astride;         // 0: shared by all samples
+  double a0;               // MODEL: amplitude of the zero mode
+  const uint16_t* lut;     // MODEL: bin of q (0xFFFF: zero mode)
+  Geo geo;
+  __device__ __forceinline__ int bin(int64_t flat) const {
+    const int q = geo.q_of(flat);
+    return q == 0 ? -1 : (int)__ldg(&lut[q]);
+  }
+  __device__ __forceinline__ T amp(int b, int64_t flat, int bn) const {
+    if (mode == AMPV_FIXED) return __ldg(&afull[flat]);
+    return bn < 0 ? T(a0) : T(__ldg(&abin[b * astride + bn]));
+  }
+};
+
+enum { PRO_BUF = 0, PRO_AMP = 1, PRO_SQRTW = 2 };
+
+// Value entering the first transform at (sample b, pixel flat).
+template <typename T>
+struct Pro {
+  int mode;
+  const T* x;         // input, sample b at x + b * xs
+  int64_t xs;
+  const T* xi_p;      // PRO_AMP with dA: expansion point field, sample b at xi_p + b * ps
+  int64_t ps;
+  const double* dA;   // PRO_AMP: per-sample dA bins (nullptr: none)
+  int nb;
+  const T* w;         // PRO_SQRTW: weights [N]
+  AmpView<T> av;
+  __device__ __forceinline__ T load(int b, int64_t flat) const {
+    const T v = x[b * xs + flat];
+    if (mode == PRO_BUF) return v;
+    if (mode == PRO_SQRTW) return sqrt(__ldg(&w[flat])) * v;
+    const int bn = av.mode == AMPV_MODEL ? av.bin(flat) : -1;
+    T u = av.amp(b, flat, bn) * v;
+    if (dA != nullptr && bn >= 0) u += T(__ldg(&dA[b * nb + bn])) * xi_p[b * ps + flat];
+    return u;
+  }
+};
+
+enum { EPI_BUF = 0, EPI_OFFSET = 1, EPI_WEIGHT = 2, EPI_AMP = 3 };
+
+// Consumer of the last transform's output at (sample b, pixel flat).
+template <typename T>
+struct Epi {
+  int mode;
+  T* y;               // output, sample b at y + b * ys
+  int64_t ys;
+  double offset;      // EPI_OFFSET / EPI_WEIGHT: offset_mean
+  // EPI_WEIGHT: Fisher weight from cf = offset + value
+  int lik_kind, response;
+  double sig_or_scale;
+  const T* mask;      // [N] or nullptr
+  // EPI_AMP: y = base + A * value; hist[bin] += xi_p * value
+  const T* base;
+  int64_t bs;
+  const T* xi_p;
+  int64_t ps;
+  int bins;           // accumulate the per-bin sums
+  AmpView<T> av;
+
+  __device__ __forceinline__ void store(int b, int64_t flat, T val, double* hist) const {
+    if (mode == EPI_BUF) {
+      y[b * ys + flat] = val;
+    } else if (mode == EPI_OFFSET) {
+      y[b * ys + flat] = T(offset) + val;
+    } else if (mode == EPI_WEIGHT) {
+      const T cf = T(offset) + val;
+      T w;
+      if (lik_kind == NRE_LIK_POISSON) {
+        w = T(sig_or_scale) * exp(cf);
+      } else {
+        const T inv = T(1.0 / (sig_or_scale * sig_or_scale));
+        if (response == NRE_RESP_EXP) {
+          const T s = exp(cf);
+          w = s * s * inv;
+        } else {
+          w = inv;
+        }
+        if (mask != nullptr) w *= __ldg(&mask[flat]);
+      }
+      y[b * ys + flat] = w;
+    } else {
+      const int bn = av.mode == AMPV_MODEL ? av.bin(flat) : -1;
+      T o = av.amp(b, flat, bn) * val;
+      if (base != nullptr) o += base[b * bs + flat];
+      y[b * ys + flat] = o;
+      if (bins && bn >= 0) atomicAdd(&hist[bn], double(xi_p[b * ps + flat] * val));
+    }
+  }
+};
+
+// Middle operation between the two transforms of the metric: t = w * y.
+template <typename T>
+struct Mid {
+  const T* w;  // [N]
+  __device__ __forceinline__ T apply(int64_t flat, T y) const { return __ldg(&w[flat]) * y; }
+};
+
+// Arguments of one row sweep (last axis, length L).
+template <typename T>
+struct RowArgs {
+  int L, log2L, log2Lmax;
+  const typename CplxT<T>::type* tw;
+  int pm;              // 1, 2 or 3: grid dimensionality (P combination)
+  int n_units;         // PM >= 2: row groups per sample; PM == 1: sample pairs
+  int nU;              // units per CTA iteration
+  int B;               // batch
+  const int* grows;    // PM >= 2: rows of group g at grows[g * G + s]
+  const int* gflags;   // PM >= 2: bit0 = R_0 swaps slots in a line, bit1 = R_1 swaps lines
+  Pro<T> pro;
+  Epi<T> epi;
+  Mid<T> mid;
+  int nb;              // bins of the histogram (epi.bins)
+  double* partials;    // [B][gridDim.x][nb] (PM >= 2) or [B][1][nb] (PM == 1)
+};
+
+// Arguments of one sweep along a non-contiguous axis.
+template <typename T>
+struct ColArgs {
+  int L, log2L, log2Lmax;
+  const typename CplxT<T>::type* tw;
+  int64_t inner;       // product of the axis lengths after this axis
+  int W;               // grid columns per unit (even, divides inner)
+  int64_t nblk;        // inner / W
+  int64_t n_units;     // outer * nblk
+  Pro<T> pro;
+  Epi<T> epi;
+  Mid<T> mid;
+  int nb;
+  double* partials;    // [B][gridDim.x][nb]
+};
+
+}  // namespace nre
+
+// The opaque plan of the C ABI.
+struct nre_cf_plan {
+  int ndim = 0, dtype = NRE_F32;
+  int n[3] = {1, 1, 1}, l2[3] = {0, 0, 0};
+  int64_t N = 0, nrows = 0;
+  int Lmax = 0, log2Lmax = 0;
+  int amp_kind = 0;
+  double offset_mean = 0.0, offset_std = 1.0;
+  int n_bins = 0, n_hyper = 0;
+  int64_t latent = 0, stride = 0;
+  // prior of the power model: log-normal (mu, s) and slope (mean, std)
+  double mu_fl = 0, s_fl = 0, mu_fx = 0, s_fx = 0, mu_as = 0, s_as = 0, sl_m = 0, sl_s = 0;
+  int n_groups = 0, G = 1;
+  nre::DevBuf tw;        // complex twiddles, Lmax entries, plan dtype
+  nre::DevBuf afull;     // fixed kinds: A_full [N], plan dtype
+  nre::DevBuf lut;       // model: uint16 bin of q
+  nre::DevBuf centres;   // model: double[n_bins]
+  nre::DevBuf counts;    // model: double[n_bins]
+  nre::DevBuf grows;     // int[n_groups * G]
+  nre::DevBuf gflags;    // int[n_groups]
+  // workspaces grown on demand by the cf_* calls
+  nre::DevBuf ws_tmp0, ws_tmp1, ws_state, ws_dA, ws_part;
+};
+
+namespace nre {
+
+// Amplitude-model kernels (amp.cu)
+struct AmpPrior {
+  double mu_fl, s_fl, mu_fx, s_fx, mu_as, s_as, sl_m, sl_s;
+  const double* centres;
+  const double* counts;
+  int nb;
+};
+AmpPrior amp_prior_of(const nre_cf_plan* p);
+// state[b] from the hyper-latents at h + b * hs (n_hyper doubles or floats).
+template <typename T>
+int amp_forward(const AmpPrior& pr, const T* h, int64_t hs, double* state, int B, cudaStream_t st);
+// dA[b] = JVP at state (sample b at state + b * ss) in direction dh[b].
+template <typename T>
+int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
+            double* dA, int B, cudaStream_t st);
+// out_h[b] = base_h[b] (optional) + VJP at state of gA[b] = sum_c partials[b][c][:].
+template <typename T>
+int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* partials,
+            int nparts, const T* base_h, int64_t bhs, T* out_h, int64_t ohs, int B,
+            cudaStream_t st);
+
+// Sweep chains (sweeps.cu).  Runs one Hartley transform (mid == nullptr) or the
+// metric's transform pair with t = w * y between them (mid != nullptr) over a
+// batch, fusing the prologue into the first sweep and the epilogue into the
+// last.  tmp0/tmp1 hold B * N elements each.  *nparts receives the number of
+// histogram partials per sample written by the last sweep.
+template <typename T>
+int run_hartley(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
+                const Mid<T>* mid, T* tmp0, T* tmp1, double* partials, int* nparts,
+                cudaStream_t st);
+// Maximum number of histogram partials per sample of any sweep of the plan.
+int max_parts(const nre_cf_plan* p);
+// Workspace growth helper.
+int ensure(DevBuf& b, size_t bytes);
+
+template <typename T>
+AmpView<T> amp_view(const nre_cf_plan* p, const double* abin, int64_t astride);
+
+}  // namespace nre

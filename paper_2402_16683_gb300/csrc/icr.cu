@@ -1,0 +1,564 @@
+// Iterative charted refinement (ICR) on a 2-D log-radial chart.
+//
+// Sec. "Gaussian Processes", ICR paragraph: a GP on a deformed space, built by
+// refining a coarse draw level by level from nearest-neighbour relations on
+// coarsenings of the chart.  Reading implemented here (no equations in the
+// paper): level l has n_l = n0 2^l points per axis at u = (i+1/2)/n_l,
+// v = (j+1/2)/n_l, mapped by r = r_min (r_max/r_min)^u, phi = 2 pi v; Matern-3/2
+// kernel; s_0 = chol(K0) xi_0; coarse pixel (i, j) with its 3x3 neighbourhood
+// (rows clamp(i-1, 0, n-3) + {0,1,2}, columns j-1..j+1 mod n) predicts its 2x2
+// children: s_f = R_i s_nbhd + L_i xi_f, R_i = K_fc K_cc^-1,
+// L_i = chol(K_ff - R_i K_cf).  Rotation invariance makes R, L depend only on
+// (level, radial row); they are assembled in FP64 on the host.
+//
+// Kernels: one thread per coarse pixel.  The forward reads the 9 neighbours
+// (coalesced along the angular axis) and the 2x2 excitations as two 2-vector
+// loads, and writes the children the same way.  The adjoint is a deterministic
+// gather: each coarse pixel collects R^T g from the children of every coarse
+// pixel whose neighbourhood contains it (up to 5 radial rows near the clamped
+// edges), and writes L^T g for its own children.
+#include <cmath>
+#include <vector>
+
+#include "metric_internal.cuh"
+
+struct nre_icr_plan {
+  int dtype = NRE_F32;
+  int n0 = 8, n_levels = 7;
+  double r_min = 0.1, r_max = 1.0, rho = 0.1, var = 1.0;
+  std::vector<int> sizes;        // n_l, l = 0..n_levels
+  std::vector<int64_t> offsets;  // latent offset of level l
+  int64_t latent = 0, stride = 0, n_out = 0;
+  nre::DevBuf L0;                // [n0^2][n0^2] lower (row-major), plan dtype
+  nre::DevBuf mats;              // per level: [n_l][52]: R (4x9 row-major), L (4x4 row-major)
+  std::vector<int64_t> mat_off;  // element offset of level l in mats
+  nre::DevBuf ws_a, ws_b, ws_c;  // per-batch level buffers
+};
+
+namespace {
+
+using nre::prof_begin;
+using nre::prof_end;
+
+constexpr int ICR_THREADS = 256;
+constexpr int MAT = 52;  // 36 (R) + 16 (L)
+
+// ---------------------------------------------------------------- host math
+struct P2 {
+  double x, y;
+};
+
+P2 chart_pos(const nre_icr_plan* p, int level, double i, double j) {
+  const double n = p->sizes[level];
+  const double u = (i + 0.5) / n, v = (j + 0.5) / n;
+  const double r = p->r_min * std::pow(p->r_max / p->r_min, u);
+  const double phi = 2.0 * M_PI * v;
+  return {r * std::cos(phi), r * std::sin(phi)};
+}
+
+double matern32(const nre_icr_plan* p, P2 a, P2 b) {
+  const double d = std::sqrt((a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y));
+  const double t = std::sqrt(3.0) * d / p->rho;
+  return p->var * (1.0 + t) * std::exp(-t);
+}
+
+// In-place lower Cholesky of the n x n row-major matrix; false if not SPD.
+bool cholesky(std::vector<double>& A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+    if (!(s > 0.0)) return false;
+    const double d = std::sqrt(s);
+    A[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = t / d;
+    }
+    for (int k = j + 1; k < n; ++k) A[j * n + k] = 0.0;
+  }
+  return true;
+}
+
+bool cholesky_jitter(std::vector<double> A, int n, double jitter, std::vector<double>& L) {
+  L = A;
+  if (cholesky(L, n)) return true;
+  for (int i = 0; i < n; ++i) A[i * n + i] += jitter;
+  L = A;
+  return cholesky(L, n);
+}
+
+// Solve (L L^T) X = Bm for X (n x m), L lower n x n, Bm row-major n x m.
+void chol_solve(const std::vector<double>& L, int n, std::vector<double>& X, int m) {
+  for (int c = 0; c < m; ++c) {
+    for (int i = 0; i < n; ++i) {  // forward
+      double s = X[i * m + c];
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * X[k * m + c];
+      X[i * m + c] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // backward with L^T
+      double s = X[i * m + c];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * X[k * m + c];
+      X[i * m + c] = s / L[i * n + i];
+    }
+  }
+}
+
+__host__ __device__ inline int window(int n, int i) {
+  int w = i - 1;
+  if (w < 0) w = 0;
+  if (w > n - 3) w = n - 3;
+  return w;
+}
+
+// R (4x9) and L (4x4) for coarse row i of `level`, appended to out.
+bool level_row_matrices(const nre_icr_plan* p, int level, int i, double* out) {
+  const int nc = p->sizes[level];
+  const int w = window(nc, i);
+  P2 pc[9], pf[4];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) pc[3 * a + b] = chart_pos(p, level, w + a, (b - 1 + nc) % nc);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) pf[2 * a + b] = chart_pos(p, level + 1, 2 * i + a, b);
+  std::vector<double> Kcc(81), X(36), Kff(16);
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) Kcc[r * 9 + c] = matern32(p, pc[r], pc[c]);
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 4; ++c) X[r * 4 + c] = matern32(p, pc[r], pf[c]);  // K_cf
+  std::vector<double> Kcf = X;
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) Kff[r * 4 + c] = matern32(p, pf[r], pf[c]);
+  std::vector<double> Lcc;
+  if (!cholesky_jitter(Kcc, 9, 1e-10 * p->var, Lcc)) return false;
+  chol_solve(Lcc, 9, X, 4);  // X = K_cc^-1 K_cf (9x4); R = X^T
+  double* R = out;
+  for (int k = 0; k < 4; ++k)
+    for (int n = 0; n < 9; ++n) R[k * 9 + n] = X[n * 4 + k];
+  std::vector<double> D(16);
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      double s = Kff[r * 4 + c];
+      for (int n = 0; n < 9; ++n) s -= R[r * 9 + n] * Kcf[n * 4 + c];
+      D[r * 4 + c] = s;
+    }
+  for (int r = 0; r < 4; ++r)  // symmetrise the rounding of the Schur complement
+    for (int c = 0; c < r; ++c) D[r * 4 + c] = D[c * 4 + r] = 0.5 * (D[r * 4 + c] + D[c * 4 + r]);
+  std::vector<double> LD;
+  if (!cholesky_jitter(D, 4, 1e-10 * p->var, LD)) return false;
+  for (int k = 0; k < 16; ++k) out[36 + k] = LD[k];
+  return true;
+}
+
+// ---------------------------------------------------------------- kernels
+template <typename T>
+__global__ void k_icr_level0(const T* L0, const T* xi, int64_t xs, T* s0, int64_t ss, int n2) {
+  const int b = blockIdx.y;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    T acc = T(0);
+    for (int j = 0; j <= i; ++j) acc += L0[i * n2 + j] * xi[b * xs + j];
+    s0[b * ss + i] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_icr_level0_t(const T* L0, const T* g0, int64_t gs, T* out, int64_t os,
+                               const T* base, int64_t bs, int n2) {
+  const int b = blockIdx.y;
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+    T acc = T(0);
+    for (int i = j; i < n2; ++i) acc += L0[i * n2 + j] * g0[b * gs + i];
+    if (base) acc += base[b * bs + j];
+    out[b * os + j] = acc;
+  }
+}
+
+// s_f = R s_nbhd + L xi_f for every coarse pixel; optional pointwise weight
+// `scale` [nf^2] applied to s_f (the metric's w * L v).
+template <typename T>
+__global__ void __launch_bounds__(ICR_THREADS) k_icr_refine(int nc, const T* __restrict__ mats,
+                                                           const T* s_c, int64_t scs,
+                                                           const T* xi_f, int64_t xs, T* s_f,
+                                                           int64_t sfs, const T* scale) {
+  typedef typename nre::CplxT<T>::type V2;
+  const int b = blockIdx.y;
+  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= (int64_t)nc * nc) return;
+  const int i = (int)(pix / nc), j = (int)(pix - (int64_t)i * nc);
+  const T* M = mats + (int64_t)i * MAT;
+  const int w = window(nc, i);
+  const int jm = j == 0 ? nc - 1 : j - 1, jp = j == nc - 1 ? 0 : j + 1;
+  const T* sc = s_c + b * scs;
+  T nb[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T* row = sc + (int64_t)(w + a) * nc;
+    nb[3 * a + 0] = row[jm];
+    nb[3 * a + 1] = row[j];
+    nb[3 * a + 2] = row[jp];
+  }
+  const int nf = 2 * nc;
+  const T* xf = xi_f + b * xs;
+  const V2 x0 = *reinterpret_cast<const V2*>(xf + (int64_t)(2 * i) * nf + 2 * j);
+  const V2 x1 = *reinterpret_cast<const V2*>(xf + (int64_t)(2 * i + 1) * nf + 2 * j);
+  const T e[4] = {x0.x, x0.y, x1.x, x1.y};
+  T o[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T acc = T(0);
+#pragma unroll
+    for (int n = 0; n < 9; ++n) acc += __ldg(&M[k * 9 + n]) * nb[n];
+#pragma unroll
+    for (int m = 0; m <= k; ++m) acc += __ldg(&M[36 + k * 4 + m]) * e[m];
+    o[k] = acc;
+  }
+  const int64_t f0 = (int64_t)(2 * i) * nf + 2 * j, f1 = f0 + nf;
+  if (scale) {
+    o[0] *= scale[f0];
+    o[1] *= scale[f0 + 1];
+    o[2] *= scale[f1];
+    o[3] *= scale[f1 + 1];
+  }
+  T* sf = s_f + b * sfs;
+  V2 y0, y1;
+  y0.x = o[0];
+  y0.y = o[1];
+  y1.x = o[2];
+  y1.y = o[3];
+  *reinterpret_cast<V2*>(sf + f0) = y0;
+  *reinterpret_cast<V2*>(sf + f1) = y1;
+}
+
+// Adjoint of one refinement: g_c = sum R^T g_children (gather), and
+// g_xi_f = base + L^T g_children for this pixel's own children.
+template <typename T>
+__global__ void __launch_bounds__(ICR_THREADS) k_icr_refine_t(int nc, const T* __restrict__ mats,
+                                                             const T* g_f, int64_t gfs, T* g_c,
+                                                             int64_t gcs, T* g_xi, int64_t gxs,
+                                                             const T* base, int64_t bs) {
+  typedef typename nre::CplxT<T>::type V2;
+  const int b = blockIdx.y;
+  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= (int64_t)nc * nc) return;
+  const int ip = (int)(pix / nc), jp = (int)(pix - (int64_t)ip * nc);
+  const int nf = 2 * nc;
+  const T* gf = g_f + b * gfs;
+  // own children: L^T g
+  {
+    const int64_t f0 = (int64_t)(2 * ip) * nf + 2 * jp, f1 = f0 + nf;
+    const V2 a0 = *reinterpret_cast<const V2*>(gf + f0);
+    const V2 a1 = *reinterpret_cast<const V2*>(gf + f1);
+    const T g[4] = {a0.x, a0.y, a1.x, a1.y};
+    const T* M = mats + (int64_t)ip * MAT + 36;
+    T o[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = m; k < 4; ++k) acc += __ldg(&M[k * 4 + m]) * g[k];
+      o[m] = acc;
+    }
+    T* gx = g_xi + b * gxs;
+    if (base) {
+      const T* bb = base + b * bs;
+      o[0] += bb[f0];
+      o[1] += bb[f0 + 1];
+      o[2] += bb[f1];
+      o[3] += bb[f1 + 1];
+    }
+    V2 y0, y1;
+    y0.x = o[0];
+    y0.y = o[1];
+    y1.x = o[2];
+    y1.y = o[3];
+    *reinterpret_cast<V2*>(gx + f0) = y0;
+    *reinterpret_cast<V2*>(gx + f1) = y1;
+  }
+  // gather R^T g from the coarse pixels whose neighbourhood holds (ip, jp)
+  T acc = T(0);
+  const int i_lo = ip - 2 < 0 ? 0 : ip - 2, i_hi = ip + 2 > nc - 1 ? nc - 1 : ip + 2;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const int a = ip - window(nc, i);
+    if (a < 0 || a > 2) continue;
+    const T* M = mats + (int64_t)i * MAT;
+#pragma unroll
+    for (int bcol = 0; bcol < 3; ++bcol) {
+      int j = jp - (bcol - 1);
+      j = j < 0 ? j + nc : (j >= nc ? j - nc : j);
+      const int64_t f0 = (int64_t)(2 * i) * nf + 2 * j;
+      const V2 a0 = *reinterpret_cast<const V2*>(gf + f0);
+      const V2 a1 = *reinterpret_cast<const V2*>(gf + f0 + nf);
+      const int n = 3 * a + bcol;
+      acc += __ldg(&M[0 * 9 + n]) * a0.x + __ldg(&M[1 * 9 + n]) * a0.y + __ldg(&M[2 * 9 + n]) * a1.x +
+             __ldg(&M[3 * 9 + n]) * a1.y;
+    }
+  }
+  g_c[b * gcs + pix] = acc;
+}
+
+template <typename T>
+__global__ void k_scale_sqrt(const T* w, const T* x, int64_t xs, T* y, int64_t ys, int64_t n) {
+  const int b = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[b * ys + i] = sqrt(w[i]) * x[b * xs + i];
+}
+
+template <typename T>
+__global__ void k_fill_inv_var(T* w, const T* mask, T inv, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = mask ? inv * mask[i] : inv;
+}
+
+dim3 pix_grid(int64_t npix, int B) { return dim3((unsigned)((npix + ICR_THREADS - 1) / ICR_THREADS), B); }
+
+template <typename T>
+int ensure_ws(nre_icr_plan* p, int B) {
+  const int64_t big = (int64_t)p->sizes[p->n_levels - 1] * p->sizes[p->n_levels - 1];
+  NRE_TRY(nre::ensure(p->ws_a, (size_t)B * big * sizeof(T)));
+  NRE_TRY(nre::ensure(p->ws_b, (size_t)B * big * sizeof(T)));
+  return NRE_OK;
+}
+
+// s = ICR(xi) (optionally times `scale`), batch B.
+template <typename T>
+int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cudaStream_t st) {
+  NRE_TRY(ensure_ws<T>(p, B));
+  const int64_t big = (int64_t)p->sizes[p->n_levels - 1] * p->sizes[p->n_levels - 1];
+  T* bufs[2] = {p->ws_a.as<T>(), p->ws_b.as<T>()};
+  const int n0 = p->n0, n2 = n0 * n0;
+  const T* L0 = p->L0.as<T>();
+  const T* mats = p->mats.as<T>();
+  prof_begin("icr_level0", (double)B * 2 * n2 * sizeof(T), st);
+  k_icr_level0<T><<<dim3(1, B), 64, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  for (int l = 0; l < p->n_levels; ++l) {
+    const int nc = p->sizes[l];
+    const bool last = l == p->n_levels - 1;
+    T* out = last ? s : bufs[(l + 1) & 1];
+    const int64_t os = last ? p->n_out : big;
+    prof_begin("icr_refine", (double)nc * nc * sizeof(T) * (9.0 * B + (last && scale ? 4.0 : 0.0)), st);
+    k_icr_refine<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
+        nc, mats + p->mat_off[l], bufs[l & 1], big, xi + p->offsets[l + 1], p->stride, out, os,
+        last ? scale : nullptr);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+  }
+  return NRE_OK;
+}
+
+// g = base + ICR^T ct, batch B (ct: [B][n_out]).
+template <typename T>
+int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, int B, cudaStream_t st) {
+  NRE_TRY(ensure_ws<T>(p, B));
+  const int64_t big = (int64_t)p->sizes[p->n_levels - 1] * p->sizes[p->n_levels - 1];
+  T* bufs[2] = {p->ws_a.as<T>(), p->ws_b.as<T>()};
+  const T* mats = p->mats.as<T>();
+  const T* gin = ct;
+  int64_t gis = cts;
+  int which = 0;
+  for (int l = p->n_levels - 1; l >= 0; --l) {
+    const int nc = p->sizes[l];
+    T* gc = bufs[which];
+    prof_begin("icr_refine_t", (double)nc * nc * sizeof(T) * B * (base ? 13.0 : 9.0), st);
+    k_icr_refine_t<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
+        nc, mats + p->mat_off[l], gin, gis, gc, big, g + p->offsets[l + 1], p->stride,
+        base ? base + p->offsets[l + 1] : nullptr, p->stride);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+    gin = gc;
+    gis = big;
+    which ^= 1;
+  }
+  const int n2 = p->n0 * p->n0;
+  prof_begin("icr_level0_t", (double)B * (base ? 3 : 2) * n2 * sizeof(T), st);
+  k_icr_level0_t<T><<<dim3(1, B), 64, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int upload_tables(nre_icr_plan* p, const std::vector<double>& L0, const std::vector<double>& mats) {
+  std::vector<T> a(L0.begin(), L0.end()), m(mats.begin(), mats.end());
+  NRE_TRY(p->L0.upload(a.data(), a.size() * sizeof(T)));
+  NRE_TRY(p->mats.upload(m.data(), m.size() * sizeof(T)));
+  return NRE_OK;
+}
+
+}  // namespace
+
+namespace nre {
+
+int icr_layout(const nre_icr_plan* p, int64_t* n_out, int64_t* latent, int64_t* stride, int* dtype) {
+  *n_out = p->n_out;
+  *latent = p->latent;
+  *stride = p->stride;
+  *dtype = p->dtype;
+  return NRE_OK;
+}
+
+int icr_metric_setup(nre_metric* m, cudaStream_t st) {
+  const size_t es = m->dtype == NRE_F64 ? 8 : 4;
+  NRE_TRY(m->w.alloc(m->n_data * es));
+  NRE_TRY(m->tmp0.alloc((size_t)m->max_batch * m->n_data * es));
+  const double inv = 1.0 / (m->lik.sig_or_scale * m->lik.sig_or_scale);
+  if (m->dtype == NRE_F64) {
+    if (!m->lik.mask.empty()) NRE_TRY(m->mask.upload(m->lik.mask.data(), m->lik.mask.size() * 8));
+    prof_begin("icr_fill", 0.0, st);
+    k_fill_inv_var<double><<<64, 256, 0, st>>>(m->w.as<double>(), m->mask.p ? m->mask.as<double>() : nullptr, inv, m->n_data);
+    prof_end(st);
+  } else {
+    if (!m->lik.mask.empty()) {
+      std::vector<float> mk(m->lik.mask.begin(), m->lik.mask.end());
+      NRE_TRY(m->mask.upload(mk.data(), mk.size() * 4));
+    }
+    prof_begin("icr_fill", 0.0, st);
+    k_fill_inv_var<float><<<64, 256, 0, st>>>(m->w.as<float>(), m->mask.p ? m->mask.as<float>() : nullptr, (float)inv, m->n_data);
+  }
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+static int icr_metric_apply_t(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
+  T* s = m->tmp0.as<T>();
+  NRE_TRY(icr_forward_t<T>(m->icr, v, s, B, m->w.as<T>(), st));
+  return icr_vjp_t<T>(m->icr, s, m->n_data, out, v, B, st);
+}
+
+int icr_metric_apply(nre_metric* m, const void* v, void* out, int B, cudaStream_t st) {
+  if (m->dtype == NRE_F64) return icr_metric_apply_t<double>(m, (const double*)v, (double*)out, B, st);
+  return icr_metric_apply_t<float>(m, (const float*)v, (float*)out, B, st);
+}
+
+template <typename T>
+static int icr_rhs_t(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cudaStream_t st) {
+  T* t = m->tmp0.as<T>();
+  prof_begin("icr_scale", (double)m->n_data * sizeof(T) * (2.0 * B + 1.0), st);
+  k_scale_sqrt<T><<<dim3(64, B), 256, 0, st>>>(m->w.as<T>(), eta, m->n_data, t, m->n_data, m->n_data);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return icr_vjp_t<T>(m->icr, t, m->n_data, b, xi_prime, B, st);
+}
+
+int icr_mgvi_rhs(nre_metric* m, const void* xi_prime, const void* eta, void* b, int B, cudaStream_t st) {
+  if (m->dtype == NRE_F64)
+    return icr_rhs_t<double>(m, (const double*)xi_prime, (const double*)eta, (double*)b, B, st);
+  return icr_rhs_t<float>(m, (const float*)xi_prime, (const float*)eta, (float*)b, B, st);
+}
+
+}  // namespace nre
+
+using namespace nre;
+
+extern "C" {
+
+int icr_create(nre_icr_plan** plan, const icr_chart_params* chart, const icr_kernel_params* kernel,
+               int n_levels, int dtype) {
+  clear_error();
+  if (!plan || !chart || !kernel) return set_error(NRE_EINVAL, "NULL argument");
+  *plan = nullptr;
+  if (chart->n0 < 4 || chart->n0 > 64 || (chart->n0 & 1))
+    return set_error(NRE_EINVAL, "n0 must be even and in [4, 64] (levels are read as 2-vectors)");
+  if (n_levels < 1 || n_levels > 10) return set_error(NRE_EINVAL, "n_levels must be in [1, 10]");
+  if ((int64_t)chart->n0 << n_levels > 4096) return set_error(NRE_EINVAL, "n0 * 2^n_levels must be <= 4096");
+  if (!(chart->r_min > 0 && chart->r_max > chart->r_min)) return set_error(NRE_EINVAL, "need 0 < r_min < r_max");
+  if (!(kernel->rho > 0 && kernel->var > 0)) return set_error(NRE_EINVAL, "need rho > 0 and var > 0");
+  if (dtype != NRE_F32 && dtype != NRE_F64) return set_error(NRE_EINVAL, "dtype must be NRE_F32 or NRE_F64");
+  nre_icr_plan* p = new nre_icr_plan();
+  p->dtype = dtype;
+  p->n0 = chart->n0;
+  p->n_levels = n_levels;
+  p->r_min = chart->r_min;
+  p->r_max = chart->r_max;
+  p->rho = kernel->rho;
+  p->var = kernel->var;
+  int64_t off = 0;
+  for (int l = 0; l <= n_levels; ++l) {
+    const int n = p->n0 << l;
+    p->sizes.push_back(n);
+    p->offsets.push_back(off);
+    off += (int64_t)n * n;
+  }
+  p->latent = off;
+  p->stride = round_up(off, 64);
+  p->n_out = (int64_t)p->sizes.back() * p->sizes.back();
+  // level 0
+  const int n2 = p->n0 * p->n0;
+  std::vector<double> K0((size_t)n2 * n2), L0;
+  for (int a = 0; a < n2; ++a)
+    for (int b = 0; b < n2; ++b)
+      K0[(size_t)a * n2 + b] = matern32(p, chart_pos(p, 0, a / p->n0, a % p->n0), chart_pos(p, 0, b / p->n0, b % p->n0));
+  if (!cholesky_jitter(K0, n2, 1e-10 * p->var, L0)) {
+    delete p;
+    return set_error(NRE_EINVAL, "level-0 kernel matrix is not positive definite");
+  }
+  std::vector<double> mats;
+  for (int l = 0; l < n_levels; ++l) {
+    p->mat_off.push_back((int64_t)mats.size());
+    const int nc = p->sizes[l];
+    for (int i = 0; i < nc; ++i) {
+      double buf[MAT];
+      if (!level_row_matrices(p, l, i, buf)) {
+        delete p;
+        return set_error(NRE_EINVAL, "refinement matrices of level %d row %d are not positive definite", l, i);
+      }
+      mats.insert(mats.end(), buf, buf + MAT);
+    }
+  }
+  const int s = dtype == NRE_F64 ? upload_tables<double>(p, L0, mats) : upload_tables<float>(p, L0, mats);
+  if (s != NRE_OK) {
+    delete p;
+    return s;
+  }
+  *plan = p;
+  return NRE_OK;
+}
+
+int icr_destroy(nre_icr_plan* plan) {
+  delete plan;
+  return NRE_OK;
+}
+
+int icr_latent_layout(const nre_icr_plan* p, int64_t* n_out, int64_t* latent_size, int64_t* stride) {
+  clear_error();
+  if (!p) return set_error(NRE_EINVAL, "plan must not be NULL");
+  if (n_out) *n_out = p->n_out;
+  if (latent_size) *latent_size = p->latent;
+  if (stride) *stride = p->stride;
+  return NRE_OK;
+}
+
+#define NRE_ICR_CHECK(ptrs)                                                   \
+  clear_error();                                                              \
+  if (!plan) return set_error(NRE_EINVAL, "plan must not be NULL");           \
+  if (batch < 0 || batch > 65535) return set_error(NRE_EINVAL, "batch must be in [0, 65535]"); \
+  if (batch == 0) return NRE_OK;                                              \
+  if (!(ptrs)) return set_error(NRE_EINVAL, "NULL array argument");
+
+int icr_forward(nre_icr_plan* plan, const void* xi, void* s, int batch, nre_stream_t stream) {
+  NRE_ICR_CHECK(xi && s);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->dtype == NRE_F64) return icr_forward_t<double>(plan, (const double*)xi, (double*)s, batch, nullptr, st);
+  return icr_forward_t<float>(plan, (const float*)xi, (float*)s, batch, nullptr, st);
+}
+
+int icr_jvp(nre_icr_plan* plan, const void* xi_p, const void* v, void* jv, int batch, nre_stream_t stream) {
+  (void)xi_p;
+  NRE_ICR_CHECK(v && jv);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->dtype == NRE_F64) return icr_forward_t<double>(plan, (const double*)v, (double*)jv, batch, nullptr, st);
+  return icr_forward_t<float>(plan, (const float*)v, (float*)jv, batch, nullptr, st);
+}
+
+int icr_vjp(nre_icr_plan* plan, const void* xi_p, const void* ct, void* g, int batch, nre_stream_t stream) {
+  (void)xi_p;
+  NRE_ICR_CHECK(ct && g);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->dtype == NRE_F64)
+    return icr_vjp_t<double>(plan, (const double*)ct, plan->n_out, (double*)g, nullptr, batch, st);
+  return icr_vjp_t<float>(plan, (const float*)ct, plan->n_out, (float*)g, nullptr, batch, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// Likelihood weights, the metric M_p = J^T N^-1 J + 1 and the MGVI right-hand
+// side for the correlated field.
+//
+// Sec. "Performance": the benchmarked operator is M_p := F_p + 1 with
+// F_p = J^T N^-1 J (N^-1 the Fisher metric of the Poisson likelihood).  With the
+// response Jacobian folded into a per-pixel weight w (likelihood.h comments in
+// nre.h) one application is
+//     u = A * v_field + dA(v_hyper) * xi_p      (harmonic prologue)
+//     y = H u,  t = w * y,  r = H t             (two Hartley transforms)
+//     out_field = v_field + A * r,
+//     out_hyper = v_hyper + VJP_amp(sum_{k in bin} xi_p[k] r[k]).
+// Sec. "Variational Inference": an MGVI right-hand side with covariance M_p is
+// b = xi' + J^T (sqrt(w) * eta).
+#include <cmath>
+#include <cstring>
+
+#include "metric_internal.cuh"
+
+using namespace nre;
+
+namespace {
+
+template <typename T>
+int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
+  nre_cf_plan* p = m->cf;
+  const int64_t N = p->N;
+  NRE_TRY(m->xi_p.alloc(p->stride * sizeof(T)));
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->xi_p.p, xi_p_in, p->latent * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  NRE_TRY(m->w.alloc(N * sizeof(T)));
+  if (!m->lik.mask.empty()) {
+    std::vector<T> mk(m->lik.mask.begin(), m->lik.mask.end());
+    NRE_TRY(m->mask.upload(mk.data(), mk.size() * sizeof(T)));
+  }
+  NRE_TRY(m->tmp0.alloc((size_t)m->max_batch * N * sizeof(T)));
+  NRE_TRY(m->tmp1.alloc((size_t)m->max_batch * N * sizeof(T)));
+  const T* xp = m->xi_p.as<T>();
+  Pro<T> pro{};
+  pro.mode = PRO_AMP;
+  pro.x = xp;
+  pro.xs = 0;
+  Epi<T> epi{};
+  epi.mode = EPI_WEIGHT;
+  epi.y = m->w.as<T>();
+  epi.ys = 0;
+  epi.offset = p->offset_mean;
+  epi.lik_kind = m->lik.kind;
+  epi.response = m->lik.response;
+  epi.sig_or_scale = m->lik.sig_or_scale;
+  epi.mask = m->mask.p ? m->mask.as<T>() : nullptr;
+  if (p->amp_kind == NRE_AMP_POWER_MODEL) {
+    const int nb = p->n_bins;
+    NRE_TRY(m->state.alloc(amp_state_size(nb) * sizeof(double)));
+    NRE_TRY(m->dA.alloc((size_t)m->max_batch * nb * sizeof(double)));
+    NRE_TRY(m->part.alloc((size_t)m->max_batch * max_parts(p) * nb * sizeof(double)));
+    NRE_TRY(amp_forward<T>(amp_prior_of(p), xp + N, 0, m->state.as<double>(), 1, st));
+    pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+  } else {
+    pro.av = amp_view<T>(p, nullptr, 0);
+  }
+  int np = 0;
+  return run_hartley<T>(p, 1, pro, epi, nullptr, m->tmp0.as<T>(), m->tmp1.as<T>(), nullptr, &np, st);
+}
+
+template <typename T>
+int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
+  nre_cf_plan* p = m->cf;
+  const int64_t N = p->N, S = p->stride;
+  const T* xp = m->xi_p.as<T>();
+  Pro<T> pro{};
+  pro.mode = PRO_AMP;
+  pro.x = v;
+  pro.xs = S;
+  Epi<T> epi{};
+  epi.mode = EPI_AMP;
+  epi.y = out;
+  epi.ys = S;
+  epi.base = v;
+  epi.bs = S;
+  Mid<T> mid{m->w.as<T>()};
+  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const int nb = p->n_bins;
+  const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
+  if (model) {
+    NRE_TRY(amp_jvp<T>(pr, m->state.as<double>(), 0, v + N, S, m->dA.as<double>(), B, st));
+    pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+    pro.dA = m->dA.as<double>();
+    pro.nb = nb;
+    pro.xi_p = xp;
+    pro.ps = 0;
+    epi.av = pro.av;
+    epi.bins = 1;
+    epi.xi_p = xp;
+    epi.ps = 0;
+  } else {
+    pro.av = amp_view<T>(p, nullptr, 0);
+    epi.av = pro.av;
+  }
+  int np = 0;
+  NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
+                         model ? m->part.as<double>() : nullptr, &np, st));
+  if (model)
+    NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,
+                       B, st));
+  return NRE_OK;
+}
+
+template <typename T>
+int cf_mgvi_rhs(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cudaStream_t st) {
+  nre_cf_plan* p = m->cf;
+  const int64_t N = p->N, S = p->stride;
+  const T* xp = m->xi_p.as<T>();
+  Pro<T> pro{};
+  pro.mode = PRO_SQRTW;
+  pro.x = eta;
+  pro.xs = N;
+  pro.w = m->w.as<T>();
+  Epi<T> epi{};
+  epi.mode = EPI_AMP;
+  epi.y = b;
+  epi.ys = S;
+  epi.base = xi_prime;
+  epi.bs = S;
+  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const int nb = p->n_bins;
+  if (model) {
+    epi.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+    epi.bins = 1;
+    epi.xi_p = xp;
+    epi.ps = 0;
+  } else {
+    epi.av = amp_view<T>(p, nullptr, 0);
+  }
+  int np = 0;
+  NRE_TRY(run_hartley<T>(p, B, pro, epi, nullptr, m->tmp0.as<T>(), m->tmp1.as<T>(),
+                         model ? m->part.as<double>() : nullptr, &np, st));
+  if (model)
+    NRE_TRY(amp_vjp<T>(amp_prior_of(p), m->state.as<double>(), 0, m->part.as<double>(), np,
+                       xi_prime + N, S, b + N, S, B, st));
+  return NRE_OK;
+}
+
+}  // namespace
+
+namespace nre {
+int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st) {
+  if (m->model_kind == NRE_MODEL_ICR) return icr_metric_apply(m, v, out, batch, st);
+  if (m->dtype == NRE_F64) return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st);
+  return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st);
+}
+}  // namespace nre
+
+extern "C" {
+
+int lik_create(nre_lik** lik, int kind, int response, const double* mask_host, int64_t n_data,
+               double sigma_or_scale) {
+  clear_error();
+  if (!lik) return set_error(NRE_EINVAL, "lik must not be NULL");
+  *lik = nullptr;
+  if (kind != NRE_LIK_GAUSS && kind != NRE_LIK_POISSON) return set_error(NRE_EINVAL, "unknown likelihood kind %d", kind);
+  if (response != NRE_RESP_EXP && response != NRE_RESP_IDENTITY) return set_error(NRE_EINVAL, "unknown response %d", response);
+  if (kind == NRE_LIK_POISSON && response != NRE_RESP_EXP)
+    return set_error(NRE_EINVAL, "the Poisson likelihood uses the exponential response");
+  if (!(sigma_or_scale > 0) || !std::isfinite(sigma_or_scale))
+    return set_error(NRE_EINVAL, "sigma / scale must be positive");
+  if (n_data < 0) return set_error(NRE_EINVAL, "n_data must be >= 0");
+  nre_lik* l = new nre_lik();
+  l->kind = kind;
+  l->response = response;
+  l->sig_or_scale = sigma_or_scale;
+  l->n_data = n_data;
+  if (mask_host) {
+    if (kind == NRE_LIK_POISSON) {
+      delete l;
+      return set_error(NRE_EINVAL, "the Poisson likelihood takes no mask");
+    }
+    l->mask.assign(mask_host, mask_host + n_data);
+  }
+  *lik = l;
+  return NRE_OK;
+}
+
+int lik_destroy(nre_lik* lik) {
+  delete lik;
+  return NRE_OK;
+}
+
+int metric_create(nre_metric** out, int model_kind, void* model_plan, const nre_lik* lik,
+                  const void* xi_p, int max_batch, nre_stream_t stream) {
+  clear_error();
+  if (!out || !model_plan || !lik || !xi_p) return set_error(NRE_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > 65535) return set_error(NRE_EINVAL, "max_batch must be in [1, 65535]");
+  cudaStream_t st = (cudaStream_t)stream;
+  nre_metric* m = new nre_metric();
+  m->model_kind = model_kind;
+  m->max_batch = max_batch;
+  m->lik = *lik;
+  int s = NRE_OK;
+  if (model_kind == NRE_MODEL_CF) {
+    m->cf = (nre_cf_plan*)model_plan;
+    m->dtype = m->cf->dtype;
+    m->n_data = m->cf->N;
+    m->latent = m->cf->latent;
+    m->stride = m->cf->stride;
+    if (!m->lik.mask.empty() && (int64_t)m->lik.mask.size() != m->n_data)
+      s = set_error(NRE_EINVAL, "mask has %lld entries, the grid %lld", (long long)m->lik.mask.size(),
+                    (long long)m->n_data);
+    else
+      s = m->dtype == NRE_F64 ? cf_metric_setup<double>(m, xi_p, st) : cf_metric_setup<float>(m, xi_p, st);
+  } else if (model_kind == NRE_MODEL_ICR) {
+    m->icr = (nre_icr_plan*)model_plan;
+    int dt;
+    s = icr_layout(m->icr, &m->n_data, &m->latent, &m->stride, &dt);
+    m->dtype = dt;
+    if (s == NRE_OK) {
+      if (m->lik.kind != NRE_LIK_GAUSS || m->lik.response != NRE_RESP_IDENTITY)
+        s = set_error(NRE_EINVAL, "the ICR metric takes a Gaussian likelihood with identity response");
+      else if (!m->lik.mask.empty() && (int64_t)m->lik.mask.size() != m->n_data)
+        s = set_error(NRE_EINVAL, "mask size does not match the ICR output");
+      else {
+        const size_t es = m->dtype == NRE_F64 ? 8 : 4;
+        s = m->xi_p.alloc(m->stride * es);
+        if (s == NRE_OK) {
+          cudaError_t e = cudaMemcpyAsync(m->xi_p.p, xi_p, m->latent * es, cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) s = set_error(NRE_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+        }
+        if (s == NRE_OK) s = icr_metric_setup(m, st);
+      }
+    }
+  } else {
+    s = set_error(NRE_EINVAL, "unknown model kind %d", model_kind);
+  }
+  if (s != NRE_OK) {
+    delete m;
+    return s;
+  }
+  *out = m;
+  return NRE_OK;
+}
+
+int metric_destroy(nre_metric* m) {
+  delete m;
+  return NRE_OK;
+}
+
+int metric_apply(nre_metric* m, const void* v, void* out, int batch, nre_stream_t stream) {
+  clear_error();
+  if (!m) return set_error(NRE_EINVAL, "metric must not be NULL");
+  if (batch < 0 || batch > m->max_batch) return set_error(NRE_EINVAL, "batch %d outside [0, max_batch=%d]", batch, m->max_batch);
+  if (batch == 0) return NRE_OK;
+  if (!v || !out) return set_error(NRE_EINVAL, "NULL array argument");
+  if (v == out) return set_error(NRE_EINVAL, "out may not alias v");
+  return metric_apply_impl(m, v, out, batch, (cudaStream_t)stream);
+}
+
+int mgvi_rhs(nre_metric* m, const void* xi_prime, const void* eta, void* b, int batch, nre_stream_t stream) {
+  clear_error();
+  if (!m) return set_error(NRE_EINVAL, "metric must not be NULL");
+  if (batch < 0 || batch > m->max_batch) return set_error(NRE_EINVAL, "batch %d outside [0, max_batch=%d]", batch, m->max_batch);
+  if (batch == 0) return NRE_OK;
+  if (!xi_prime || !eta || !b) return set_error(NRE_EINVAL, "NULL array argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (m->model_kind == NRE_MODEL_ICR) return icr_mgvi_rhs(m, xi_prime, eta, b, batch, st);
+  if (m->dtype == NRE_F64)
+    return cf_mgvi_rhs<double>(m, (const double*)xi_prime, (const double*)eta, (double*)b, batch, st);
+  return cf_mgvi_rhs<float>(m, (const float*)xi_prime, (const float*)eta, (float*)b, batch, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,429 @@
+// Hartley sweeps of the correlated field: one HBM pass per sweep, each a batch
+// of 1-D DHTs along one axis with fused prologue / middle / epilogue.
+//
+// Row sweep (last, contiguous axis).  A unit is a reflection orbit of rows of
+// one sample (D = 2: rows {i, -i}; D = 3: rows {(+-i0, +-i1)}), or for D = 1 a
+// pair of samples.  Two real rows form one complex line; after the FFT a thread
+// owns the positions x and -x of every line of its unit, so the Hartley unpack,
+// the reflection combination P and the epilogue run in registers.
+//
+// Column sweep (any other axis).  A unit is W adjacent grid columns of one
+// outer index; columns 2p and 2p+1 form complex line p, which is one aligned
+// 2-element vector load per position, so loads and stores stay coalesced.  The
+// axis-0 sweep of the metric runs the first transform's last DHT, t = w * y and
+// the second transform's first DHT back to back in shared memory.
+#include "cf_internal.cuh"
+
+namespace nre {
+
+constexpr int SWEEP_THREADS = 256;
+
+template <typename T, int PM, bool MID>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
+  typedef typename CplxT<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LPU = (PM == 3) ? 2 : 1;  // complex lines per unit
+  const int L = a.L, Lh = L >> 1;
+  const int nl = a.nU * LPU;
+  const LayRow lay{LayRow::stride(L)};
+  C* bufA = reinterpret_cast<C*>(smem_raw);
+  C* bufB = bufA + nl * lay.ls;
+  double* hist = reinterpret_cast<double*>(bufB + nl * lay.ls);
+  const int nhist = (PM == 1) ? 2 * a.nU : 1;
+  const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  if (bins)
+    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = 0.0;
+  const int bsample = (PM == 1) ? 0 : blockIdx.y;
+
+  for (int u0 = blockIdx.x * a.nU; u0 < a.n_units; u0 += gridDim.x * a.nU) {
+    // ---- load (prologue)
+    for (int q = threadIdx.x; q < nl * L; q += blockDim.x) {
+      const int line = q / L, x = q - line * L;
+      const int u = line / LPU, li = line - u * LPU;
+      const int unit = u0 + u;
+      T re = T(0), im = T(0);
+      if (unit < a.n_units) {
+        if (PM == 1) {
+          const int s0 = 2 * unit;
+          re = a.pro.load(s0, x);
+          if (s0 + 1 < a.B) im = a.pro.load(s0 + 1, x);
+        } else {
+          const int G = 2 * LPU;
+          const int r0 = a.grows[unit * G + 2 * li], r1 = a.grows[unit * G + 2 * li + 1];
+          re = a.pro.load(bsample, (int64_t)r0 * L + x);
+          im = a.pro.load(bsample, (int64_t)r1 * L + x);
+        }
+      }
+      bufA[lay.idx(line, x)] = cmake<C>(re, im);
+    }
+    __syncthreads();
+    C* Z = block_fft(bufA, bufB, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
+    if constexpr (MID) {
+      // D = 1 only: y = H u, t = w * y, then the second transform.
+      for (int q = threadIdx.x; q < a.nU * (Lh + 1); q += blockDim.x) {
+        const int u = q / (Lh + 1), x = q - u * (Lh + 1);
+        const int xm = (L - x) & (L - 1);
+        C z = Z[lay.idx(u, x)], zm = Z[lay.idx(u, xm)];
+        T ha[2], hb[2];
+        hartley_unpack<T>(z, zm, ha, hb);
+        const T w0 = a.mid.w[x], w1 = a.mid.w[xm];
+        Z[lay.idx(u, x)] = cmake<C>(w0 * ha[0], w0 * hb[0]);
+        if (xm != x) Z[lay.idx(u, xm)] = cmake<C>(w1 * ha[1], w1 * hb[1]);
+      }
+      __syncthreads();
+      C* other = (Z == bufA) ? bufB : bufA;
+      Z = block_fft(Z, other, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
+    }
+    // ---- unpack, P, epilogue
+    for (int q = threadIdx.x; q < a.nU * (Lh + 1); q += blockDim.x) {
+      const int u = q / (Lh + 1), x = q - u * (Lh + 1);
+      const int unit = u0 + u;
+      if (unit >= a.n_units) continue;
+      const int xm = (L - x) & (L - 1);
+      if (PM == 1) {
+        T ha[2], hb[2];
+        hartley_unpack<T>(Z[lay.idx(u, x)], Z[lay.idx(u, xm)], ha, hb);
+        const int s0 = 2 * unit;
+        double* h0 = hist + (2 * u) * a.nb;
+        a.epi.store(s0, x, ha[0], h0);
+        if (xm != x) a.epi.store(s0, xm, ha[1], h0);
+        if (s0 + 1 < a.B) {
+          a.epi.store(s0 + 1, x, hb[0], h0 + a.nb);
+          if (xm != x) a.epi.store(s0 + 1, xm, hb[1], h0 + a.nb);
+        }
+      } else if (PM == 2) {
+        T R[2][2];
+        hartley_unpack<T>(Z[lay.idx(u, x)], Z[lay.idx(u, xm)], R[0], R[1]);
+        const bool f0 = a.gflags[unit] & 1;
+        const T half = T(0.5);
+        T V[2][2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int s0 = f0 ? 1 - s : s;
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+            V[s][p] = half * (R[s][p] + R[s0][p] + R[s][1 - p] - R[s0][1 - p]);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int64_t row = a.grows[unit * 2 + s];
+          a.epi.store(bsample, row * L + x, V[s][0], hist);
+          if (xm != x) a.epi.store(bsample, row * L + xm, V[s][1], hist);
+        }
+      } else {
+        T R[4][2];
+        hartley_unpack<T>(Z[lay.idx(2 * u, x)], Z[lay.idx(2 * u, xm)], R[0], R[1]);
+        hartley_unpack<T>(Z[lay.idx(2 * u + 1, x)], Z[lay.idx(2 * u + 1, xm)], R[2], R[3]);
+        const int fl = a.gflags[unit];
+        const bool f0 = fl & 1, f1 = fl & 2;
+        const T half = T(0.5);
+        T V[4][2];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int s0 = f0 ? (s ^ 1) : s;
+          const int s1 = f1 ? (s ^ 2) : s;
+          const int s01 = f1 ? (s0 ^ 2) : s0;
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+            V[s][p] = half * (R[s0][p] + R[s1][p] + R[s][1 - p] - R[s01][1 - p]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int64_t row = a.grows[unit * 4 + s];
+          a.epi.store(bsample, row * L + x, V[s][0], hist);
+          if (xm != x) a.epi.store(bsample, row * L + xm, V[s][1], hist);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (bins) {
+    if (PM == 1) {
+      for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
+        const int hs = i / a.nb, bn = i - hs * a.nb;
+        const int sample = 2 * (blockIdx.x * a.nU) + hs;
+        if (sample < a.B) a.partials[(int64_t)sample * a.nb + bn] = hist[i];
+      }
+    } else {
+      double* dst = a.partials + ((int64_t)bsample * gridDim.x + blockIdx.x) * a.nb;
+      for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+    }
+  }
+}
+
+template <typename T, bool MID>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_col_sweep(ColArgs<T> a) {
+  typedef typename CplxT<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L, Lh = L >> 1;
+  const int nl = a.W >> 1;
+  const LayCol lay{nl};
+  C* bufA = reinterpret_cast<C*>(smem_raw);
+  C* bufB = bufA + nl * L;
+  double* hist = reinterpret_cast<double*>(bufB + nl * L);
+  const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  if (bins)
+    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = 0.0;
+  const int b = blockIdx.y;
+
+  for (int64_t unit = blockIdx.x; unit < a.n_units; unit += gridDim.x) {
+    const int64_t o = unit / a.nblk;
+    const int64_t c0 = (unit - o * a.nblk) * a.W;
+    const int64_t base = o * L * a.inner + c0;
+    for (int q = threadIdx.x; q < nl * L; q += blockDim.x) {
+      const int l = q / nl, p = q - l * nl;
+      const int64_t flat = base + (int64_t)l * a.inner + 2 * p;
+      bufA[lay.idx(p, l)] = cmake<C>(a.pro.load(b, flat), a.pro.load(b, flat + 1));
+    }
+    __syncthreads();
+    C* Z = block_fft(bufA, bufB, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
+    if constexpr (MID) {
+      for (int q = threadIdx.x; q < nl * (Lh + 1); q += blockDim.x) {
+        const int l = q / nl, p = q - l * nl;
+        const int lm = (L - l) & (L - 1);
+        T ha[2], hb[2];
+        hartley_unpack<T>(Z[lay.idx(p, l)], Z[lay.idx(p, lm)], ha, hb);
+        const int64_t f0 = base + (int64_t)l * a.inner + 2 * p;
+        const int64_t f1 = base + (int64_t)lm * a.inner + 2 * p;
+        Z[lay.idx(p, l)] = cmake<C>(a.mid.apply(f0, ha[0]), a.mid.apply(f0 + 1, hb[0]));
+        if (lm != l) Z[lay.idx(p, lm)] = cmake<C>(a.mid.apply(f1, ha[1]), a.mid.apply(f1 + 1, hb[1]));
+      }
+      __syncthreads();
+      C* other = (Z == bufA) ? bufB : bufA;
+      Z = block_fft(Z, other, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
+    }
+    for (int q = threadIdx.x; q < nl * (Lh + 1); q += blockDim.x) {
+      const int l = q / nl, p = q - l * nl;
+      const int lm = (L - l) & (L - 1);
+      T ha[2], hb[2];
+      hartley_unpack<T>(Z[lay.idx(p, l)], Z[lay.idx(p, lm)], ha, hb);
+      const int64_t f0 = base + (int64_t)l * a.inner + 2 * p;
+      a.epi.store(b, f0, ha[0], hist);
+      a.epi.store(b, f0 + 1, hb[0], hist);
+      if (lm != l) {
+        const int64_t f1 = base + (int64_t)lm * a.inner + 2 * p;
+        a.epi.store(b, f1, ha[1], hist);
+        a.epi.store(b, f1 + 1, hb[1], hist);
+      }
+    }
+    __syncthreads();
+  }
+  if (bins) {
+    double* dst = a.partials + ((int64_t)b * gridDim.x + blockIdx.x) * a.nb;
+    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+  }
+}
+
+// ------------------------------------------------------------------ launch
+namespace {
+
+// Complex lines a row-sweep CTA holds per iteration (>= 2 for D = 3).
+int row_lines(int L) { return L >= 2048 ? 1 : 2048 / L; }
+// Grid columns a column-sweep unit holds (even, divides inner).
+int col_width(int L, int64_t inner, int csize) {
+  int budget = (csize == 8) ? 4096 : 2048;  // complex elements per buffer
+  int W = 2 * (budget / L);
+  if (W > 32) W = 32;
+  if (W < 2) W = 2;
+  while (W > inner) W >>= 1;
+  return W;
+}
+constexpr int kMaxGridX = 128;  // CTAs per sample of a sweep (fixed per plan)
+
+template <typename T>
+size_t row_smem(int L, int nl, int nhist, int nb) {
+  return (size_t)2 * nl * LayRow::stride(L) * sizeof(typename CplxT<T>::type) +
+         (size_t)nhist * nb * sizeof(double);
+}
+
+// Algorithmic bytes of a sweep: per-sample arrays count B times, arrays shared
+// by the batch (expansion point, weights, fixed spectrum) once.
+template <typename T>
+double sweep_bytes(const Pro<T>& pro, const Epi<T>& epi, const Mid<T>* mid, bool has_mid, int B,
+                   int64_t N) {
+  const double e = (double)N * sizeof(T);
+  double per = 1.0, shared = 0.0;  // the input x and the output y
+  per += 1.0;
+  if (pro.mode == PRO_AMP) {
+    if (pro.av.mode == AMPV_FIXED) shared += 1.0;
+    if (pro.dA) (pro.ps ? per : shared) += 1.0;
+  } else if (pro.mode == PRO_SQRTW) {
+    shared += 1.0;
+  }
+  if (epi.mode == EPI_AMP) {
+    if (epi.base) per += 1.0;
+    if (epi.bins) (epi.ps ? per : shared) += 1.0;
+    if (epi.av.mode == AMPV_FIXED && !(pro.mode == PRO_AMP && pro.av.mode == AMPV_FIXED)) shared += 1.0;
+  } else if (epi.mode == EPI_WEIGHT && epi.mask) {
+    shared += 1.0;
+  }
+  if (has_mid) shared += 1.0;
+  return e * (per * B + shared);
+}
+
+const char* row_name(int pm, bool mid, int es) {
+  static const char* names[2][4] = {
+      {"row_sweep_f32_1d", "row_sweep_f32_1d_metric", "row_sweep_f32_2d", "row_sweep_f32_3d"},
+      {"row_sweep_f64_1d", "row_sweep_f64_1d_metric", "row_sweep_f64_2d", "row_sweep_f64_3d"}};
+  const int t = es == 8 ? 1 : 0;
+  return pm == 1 ? names[t][mid ? 1 : 0] : names[t][pm];
+}
+
+template <typename T, int PM, bool MID>
+int launch_row(const RowArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
+  auto k = k_row_sweep<T, PM, MID>;
+  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  prof_begin(row_name(PM, MID, sizeof(T)), sweep_bytes<T>(a.pro, a.epi, &a.mid, MID, a.B, N), st);
+  k<<<grid, SWEEP_THREADS, smem, st>>>(a);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T, bool MID>
+int launch_col(const ColArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
+  auto k = k_col_sweep<T, MID>;
+  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const char* name = sizeof(T) == 8 ? (MID ? "col_sweep_f64_metric" : "col_sweep_f64")
+                                    : (MID ? "col_sweep_f32_metric" : "col_sweep_f32");
+  prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, MID, (int)grid.y, N), st);
+  k<<<grid, SWEEP_THREADS, smem, st>>>(a);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
+              const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st) {
+  RowArgs<T> a{};
+  const int D = p->ndim;
+  a.L = p->n[D - 1];
+  a.log2L = p->l2[D - 1];
+  a.log2Lmax = p->log2Lmax;
+  a.tw = p->tw.as<typename CplxT<T>::type>();
+  a.pm = D;
+  a.B = B;
+  a.pro = pro;
+  a.epi = epi;
+  if (mid) a.mid = *mid;
+  a.nb = p->n_bins > 0 ? p->n_bins : 1;
+  a.partials = partials;
+  a.grows = p->grows.as<int>();
+  a.gflags = p->gflags.as<int>();
+  const int nl = row_lines(a.L);
+  dim3 grid;
+  int nhist;
+  if (D == 1) {
+    a.n_units = (B + 1) / 2;
+    a.nU = nl < a.n_units ? nl : a.n_units;
+    // keep the per-sample histograms (2 per unit) within 48 KB of shared memory
+    const int hist_cap = (epi.mode == EPI_AMP && epi.bins) ? 3072 / a.nb : nl;
+    if (a.nU > hist_cap) a.nU = hist_cap < 1 ? 1 : hist_cap;
+    grid = dim3((a.n_units + a.nU - 1) / a.nU, 1);
+    nhist = 2 * a.nU;
+    *nparts = 1;
+  } else {
+    const int lpu = (D == 3) ? 2 : 1;
+    a.nU = nl / lpu < 1 ? 1 : nl / lpu;
+    a.n_units = p->n_groups;
+    int gx = (a.n_units + a.nU - 1) / a.nU;
+    if (gx > kMaxGridX) gx = kMaxGridX;
+    grid = dim3(gx, B);
+    nhist = 1;
+    *nparts = gx;
+  }
+  const int nlines = a.nU * ((D == 3) ? 2 : 1);
+  const size_t smem = row_smem<T>(a.L, nlines, epi.mode == EPI_AMP && epi.bins ? nhist : 0, a.nb);
+  if (D == 1) {
+    return mid ? launch_row<T, 1, true>(a, grid, smem, st, p->N) : launch_row<T, 1, false>(a, grid, smem, st, p->N);
+  }
+  if (mid) return set_error(NRE_EINVAL, "internal: row sweep middle op needs D = 1");
+  return D == 2 ? launch_row<T, 2, false>(a, grid, smem, st, p->N) : launch_row<T, 3, false>(a, grid, smem, st, p->N);
+}
+
+template <typename T>
+int col_sweep(const nre_cf_plan* p, int axis, int B, const Pro<T>& pro, const Epi<T>& epi,
+              const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st) {
+  ColArgs<T> a{};
+  a.L = p->n[axis];
+  a.log2L = p->l2[axis];
+  a.log2Lmax = p->log2Lmax;
+  a.tw = p->tw.as<typename CplxT<T>::type>();
+  int64_t inner = 1, outer = 1;
+  for (int d = axis + 1; d < p->ndim; ++d) inner *= p->n[d];
+  for (int d = 0; d < axis; ++d) outer *= p->n[d];
+  a.inner = inner;
+  a.W = col_width(a.L, inner, (int)sizeof(typename CplxT<T>::type));
+  a.nblk = inner / a.W;
+  a.n_units = outer * a.nblk;
+  a.pro = pro;
+  a.epi = epi;
+  if (mid) a.mid = *mid;
+  a.nb = p->n_bins > 0 ? p->n_bins : 1;
+  a.partials = partials;
+  int64_t gx = a.n_units < kMaxGridX ? a.n_units : kMaxGridX;
+  *nparts = (int)gx;
+  const size_t smem = (size_t)2 * (a.W / 2) * a.L * sizeof(typename CplxT<T>::type) +
+                      (epi.mode == EPI_AMP && epi.bins ? (size_t)a.nb * sizeof(double) : 0);
+  dim3 grid((unsigned)gx, B);
+  return mid ? launch_col<T, true>(a, grid, smem, st, p->N) : launch_col<T, false>(a, grid, smem, st, p->N);
+}
+
+template <typename T>
+Pro<T> pro_buf(const T* x, int64_t xs) {
+  Pro<T> r{};
+  r.mode = PRO_BUF;
+  r.x = x;
+  r.xs = xs;
+  return r;
+}
+template <typename T>
+Epi<T> epi_buf(T* y, int64_t ys) {
+  Epi<T> r{};
+  r.mode = EPI_BUF;
+  r.y = y;
+  r.ys = ys;
+  return r;
+}
+
+}  // namespace
+
+int max_parts(const nre_cf_plan* p) { return kMaxGridX; }
+
+template <typename T>
+int run_hartley(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
+                const Mid<T>* mid, T* tmp0, T* tmp1, double* partials, int* nparts,
+                cudaStream_t st) {
+  const int D = p->ndim;
+  const int64_t N = p->N;
+  int np = 0;
+  if (D == 1) return row_sweep<T>(p, B, pro, epi, mid, partials, nparts, st);
+  if (D == 2) {
+    if (!mid) {
+      NRE_TRY(row_sweep<T>(p, B, pro, epi_buf<T>(tmp0, N), nullptr, nullptr, &np, st));
+      return col_sweep<T>(p, 0, B, pro_buf<T>(tmp0, N), epi, nullptr, partials, nparts, st);
+    }
+    NRE_TRY(row_sweep<T>(p, B, pro, epi_buf<T>(tmp0, N), nullptr, nullptr, &np, st));
+    NRE_TRY(col_sweep<T>(p, 0, B, pro_buf<T>(tmp0, N), epi_buf<T>(tmp1, N), mid, nullptr, &np, st));
+    return row_sweep<T>(p, B, pro_buf<T>(tmp1, N), epi, nullptr, partials, nparts, st);
+  }
+  // D == 3
+  if (!mid) {
+    NRE_TRY(row_sweep<T>(p, B, pro, epi_buf<T>(tmp0, N), nullptr, nullptr, &np, st));
+    NRE_TRY(col_sweep<T>(p, 1, B, pro_buf<T>(tmp0, N), epi_buf<T>(tmp1, N), nullptr, nullptr, &np, st));
+    return col_sweep<T>(p, 0, B, pro_buf<T>(tmp1, N), epi, nullptr, partials, nparts, st);
+  }
+  NRE_TRY(row_sweep<T>(p, B, pro, epi_buf<T>(tmp0, N), nullptr, nullptr, &np, st));
+  NRE_TRY(col_sweep<T>(p, 1, B, pro_buf<T>(tmp0, N), epi_buf<T>(tmp1, N), nullptr, nullptr, &np, st));
+  NRE_TRY(col_sweep<T>(p, 0, B, pro_buf<T>(tmp1, N), epi_buf<T>(tmp0, N), mid, nullptr, &np, st));
+  NRE_TRY(col_sweep<T>(p, 1, B, pro_buf<T>(tmp0, N), epi_buf<T>(tmp1, N), nullptr, nullptr, &np, st));
+  return row_sweep<T>(p, B, pro_buf<T>(tmp1, N), epi, nullptr, partials, nparts, st);
+}
+
+template int run_hartley<float>(const nre_cf_plan*, int, const Pro<float>&, const Epi<float>&,
+                                const Mid<float>*, float*, float*, double*, int*, cudaStream_t);
+template int run_hartley<double>(const nre_cf_plan*, int, const Pro<double>&, const Epi<double>&,
+                                 const Mid<double>*, double*, double*, double*, int*, cudaStream_t);
+
+}  // namespace nre

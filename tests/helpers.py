@@ -1,0 +1,72 @@
+"""Shared helpers of the GPU parity tests: plans and oracle models built from the
+same parameters, seeded inputs, and the error measures the tolerances use."""
+import numpy as np
+import torch
+
+import synth
+from oracle import amplitude as oamp
+from oracle.cf import CFModel, matern_fixed_amplitude
+
+DEV = "cuda:0"
+
+
+def tdtype(name):
+    return torch.float64 if name == "f64" else torch.float32
+
+
+def cf_pair(shape, kind, dtype, n_bins=256, prior=None, spacing=None):
+    """(GPU plan, oracle model) for the same correlated field."""
+    import paper_2402_16683_gb300 as nre
+    sp = spacing or tuple(1.0 / s for s in shape)
+    if kind == "matern":
+        plan = nre.CorrelatedField(shape, sp, amplitude="matern", matern=synth.FIXED_1D, dtype=tdtype(dtype))
+        om = CFModel(shape, sp, fixed_amp=matern_fixed_amplitude(shape, sp, **synth.FIXED_1D))
+    else:
+        pr = dict(synth.AMP_PRIOR)
+        pr["n_bins"] = n_bins
+        if prior:
+            pr.update(prior)
+        plan = nre.CorrelatedField(shape, sp, amplitude="power", prior=pr, dtype=tdtype(dtype))
+        om = CFModel(shape, sp, prior=oamp.AmpPrior(**pr))
+    return plan, om
+
+
+def rounded(x, dtype):
+    """Inputs as the GPU sees them (float32 runs get the rounded copy), in float64."""
+    return np.asarray(x, dtype=np.float32 if dtype == "f32" else np.float64).astype(np.float64)
+
+
+def to_dev(plan, x):
+    """[B, latent] float64 numpy -> padded [B, stride] device tensor of the plan dtype."""
+    t = torch.tensor(np.atleast_2d(x), dtype=plan.dtype, device=DEV)
+    return plan.pad(t)
+
+
+def field_to_dev(plan, x):
+    return torch.tensor(np.atleast_2d(x), dtype=plan.dtype, device=DEV).contiguous()
+
+
+def host(t, n=None):
+    a = t.detach().double().cpu().numpy()
+    return a if n is None else a[:, :n]
+
+
+def rel_max(got, ref):
+    """max |got - ref| / max |ref| (the FP64 and FP32 parity measure)."""
+    ref = np.asarray(ref)
+    den = np.max(np.abs(ref))
+    return float(np.max(np.abs(np.asarray(got) - ref)) / (den if den > 0 else 1.0))
+
+
+def rel_l2(got, ref):
+    ref = np.asarray(ref)
+    den = np.linalg.norm(ref)
+    return float(np.linalg.norm(np.asarray(got) - ref) / (den if den > 0 else 1.0))
+
+
+def blocks_rel(got, ref, n_field):
+    """rel_max of the field block and of the hyper-parameter block separately."""
+    e = [rel_max(got[:n_field], ref[:n_field])]
+    if ref.shape[0] > n_field:
+        e.append(rel_max(got[n_field:], ref[n_field:]))
+    return max(e)

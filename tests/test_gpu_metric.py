@@ -1,0 +1,199 @@
+"""GPU parity of the metric M_p = J^T N^-1 J + 1, the MGVI right-hand side and
+batched CG through the C ABI, against the FP64 oracle.
+
+Tolerances: metric products and right-hand sides rel_max <= 1e-12 (FP64) and
+<= 1e-5 (FP32).  CG iterates under rounding: FP64 iterates are compared per
+iteration with tolerance 1e-12 * max(1, kappa_hat) * k (kappa_hat from the
+oracle's Lanczos coefficients); FP32 solves are judged by the FP64 true
+residual ||b - M x|| / ||b|| computed by the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import DEV, blocks_rel, cf_pair, host, rel_l2, rel_max, rounded, to_dev
+from oracle.cg import cg as ocg
+from oracle.likelihood import gaussian_weight, poisson_weight
+from oracle.metric import metric_apply as ometric
+from oracle.metric import mgvi_rhs as orhs
+
+pytestmark = pytest.mark.gpu
+
+
+def _lik(nre, kind, om, mask=None, sigma=0.1):
+    if kind == "poisson":
+        return nre.Likelihood("poisson", scale=10.0), lambda cf: poisson_weight(cf, 10.0)
+    return (nre.Likelihood("gauss", sigma=sigma, mask=mask),
+            lambda cf: gaussian_weight(cf, sigma, mask=None if mask is None else mask.reshape(cf.shape)))
+
+
+def _setup(shape, kind, dtype, lik, seed=1, max_batch=4, n_bins=256, mask=None, sigma=0.1, xi_scale=1.0):
+    import paper_2402_16683_gb300 as nre
+    plan, om = cf_pair(shape, kind, dtype, n_bins=n_bins)
+    xi_p = rounded(xi_scale * synth.normal(seed, om.latent_size), dtype)
+    L, wfun = _lik(nre, lik, om, mask=mask, sigma=sigma)
+    M = nre.Metric(plan, L, to_dev(plan, xi_p)[0], max_batch=max_batch)
+    w = wfun(om.forward(xi_p))
+    return plan, om, M, xi_p, w
+
+
+def lanczos_kappa(om, xi_p, w, b, iters):
+    """Condition-number estimate from the CG (Lanczos) coefficients of the oracle."""
+    alphas, betas = [], []
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    for _ in range(iters):
+        q = ometric(om, xi_p, w, p)
+        a = rr / (p @ q)
+        r = r - a * q
+        rn = r @ r
+        be = rn / rr
+        alphas.append(a)
+        betas.append(be)
+        p = r + be * p
+        rr = rn
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for i in range(k):
+        T[i, i] = 1 / alphas[i] + (betas[i - 1] / alphas[i - 1] if i > 0 else 0)
+        if i + 1 < k:
+            T[i, i + 1] = T[i + 1, i] = np.sqrt(betas[i]) / alphas[i]
+    ev = np.linalg.eigvalsh(T)
+    return ev[-1] / ev[0]
+
+
+@pytest.mark.parametrize("shape,kind,dtype,lik", [
+    ((256,), "matern", "f64", "gauss"),
+    ((256,), "power", "f64", "poisson"),
+    ((32, 64), "power", "f64", "poisson"),
+    ((16, 8, 32), "power", "f64", "gauss"),
+    ((512, 512), "power", "f32", "poisson"),
+    ((64, 64, 64), "power", "f32", "gauss"),
+    ((4096,), "power", "f32", "gauss"),
+    ((1024, 1024), "power", "f32", "gauss"),
+])
+def test_metric_apply(shape, kind, dtype, lik):
+    plan, om, M, xi_p, w = _setup(shape, kind, dtype, lik)
+    B = 3
+    v = rounded(np.random.default_rng(5).standard_normal((B, om.latent_size)), dtype)
+    out = host(M.apply(to_dev(plan, v)), om.latent_size)
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    for b in range(B):
+        assert blocks_rel(out[b], ometric(om, xi_p, w, v[b]), om.n_field) <= tol
+
+
+def test_metric_masked_gaussian_3d():
+    shape = (16, 32, 16)
+    n = int(np.prod(shape))
+    mask = synth.mask_fraction(synth.SEED_MASK, n, 0.1)
+    plan, om, M, xi_p, w = _setup(shape, "power", "f32", "gauss", mask=mask, sigma=0.05)
+    v = rounded(np.random.default_rng(6).standard_normal((2, om.latent_size)), "f32")
+    out = host(M.apply(to_dev(plan, v)), om.latent_size)
+    for b in range(2):
+        assert blocks_rel(out[b], ometric(om, xi_p, w, v[b]), om.n_field) <= 1e-5
+
+
+def test_metric_full_size_3d_256_sampled():
+    """3-D 256^3 (the largest workload) at batch 1: the whole product against the
+    oracle's (FFT-based, a few seconds)."""
+    shape = (256, 256, 256)
+    n = int(np.prod(shape))
+    mask = synth.mask_fraction(synth.SEED_MASK, n, 0.1)
+    plan, om, M, xi_p, w = _setup(shape, "power", "f32", "gauss", mask=mask, sigma=0.05, max_batch=1)
+    v = rounded(synth.normal(synth.SEED_TANGENT, om.latent_size), "f32")
+    out = host(M.apply(to_dev(plan, v[None])), om.latent_size)[0]
+    ref = ometric(om, xi_p, w, v)
+    assert blocks_rel(out, ref, om.n_field) <= 1e-5
+
+
+@pytest.mark.parametrize("shape,kind,dtype,lik", [
+    ((256,), "matern", "f64", "gauss"),
+    ((64, 32), "power", "f64", "poisson"),
+    ((512, 512), "power", "f32", "poisson"),
+    ((8, 16, 32), "power", "f32", "gauss"),
+])
+def test_mgvi_rhs(shape, kind, dtype, lik):
+    plan, om, M, xi_p, w = _setup(shape, kind, dtype, lik)
+    g = np.random.default_rng(8)
+    xp = rounded(g.standard_normal((2, om.latent_size)), dtype)
+    eta = rounded(g.standard_normal((2, om.n_field)), dtype)
+    b = host(M.mgvi_rhs(to_dev(plan, xp), torch.tensor(eta, dtype=plan.dtype, device=DEV)), om.latent_size)
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    for i in range(2):
+        assert blocks_rel(b[i], orhs(om, xi_p, w, xp[i], eta[i]), om.n_field) <= tol
+
+
+def test_cg_config1_per_iteration():
+    """1-D N=256, FP64, fixed spectrum, Gaussian sigma 0.1 at p = xi_true: the
+    50-iteration solve.
+
+    CG iterates are chaotic under rounding: perturbing b by one ulp changes the
+    oracle's own iterate at k = 20 by ~3e-4.  So (a) while the oracle's
+    one-ulp sensitivity is below 1e-13 (k <= 10 here) the GPU iterate must
+    match to 1e-12 * max(1, kappa_hat); (b) at every k the GPU iterate must be
+    as good in the energy norm ||x_k - x*||_M as the oracle's (CG optimality)
+    up to the spread the oracle shows under one-ulp perturbations of b."""
+    from oracle.metric import dense_metric
+    plan, om, M, xi_p, w = _setup((256,), "matern", "f64", "gauss", seed=synth.SEED_TRUTH)
+    b = synth.normal(synth.SEED_RHS, 256)
+    kappa = lanczos_kappa(om, xi_p, w, b, 50)
+    Md = dense_metric(om, xi_p, w)
+    xs = np.linalg.solve(Md, b)
+    enorm = lambda x: np.sqrt((x - xs) @ Md @ (x - xs) / (xs @ Md @ xs))
+    runs = []
+    for t in range(3):
+        bp = b if t == 0 else b * (1 + 1e-16 * np.random.default_rng(t).standard_normal(256))
+        hist = {}
+        ocg(lambda p: ometric(om, xi_p, w, p), bp, rtol=0.0, maxiter=50,
+            callback=lambda k, x: hist.__setitem__(k, x.copy()))
+        runs.append(hist)
+    for k in [1, 2, 5, 10, 15, 20, 25, 35, 50]:
+        x, its, rel, st = M.cg(to_dev(plan, b), rtol=0.0, maxiter=k)
+        assert its[0] == k
+        xg = host(x, 256)[0]
+        sens = max(rel_l2(runs[t][k], runs[0][k]) for t in (1, 2))
+        if sens < 1e-13:
+            assert rel_l2(xg, runs[0][k]) <= 1e-12 * max(1.0, kappa), (k, rel_l2(xg, runs[0][k]))
+        e_or = [enorm(runs[t][k]) for t in range(3)]
+        spread = max(e_or) - min(e_or)
+        assert enorm(xg) <= max(e_or) + 10 * spread + 1e-12, (k, enorm(xg), e_or)
+
+
+def test_cg_batched_fp64_2d_converges():
+    plan, om, M, xi_p, w = _setup((32, 32), "power", "f64", "poisson", max_batch=3)
+    g = np.random.default_rng(9)
+    b = g.standard_normal((3, om.latent_size))
+    x, its, rel, st = M.cg(to_dev(plan, b), rtol=1e-10, maxiter=2000)
+    assert st == 0
+    xs = host(x, om.latent_size)
+    for i in range(3):
+        assert rel[i] <= 1e-10
+        true = rel_l2(ometric(om, xi_p, w, xs[i]), b[i])
+        assert true <= 1e-9
+        xr, _, _ = ocg(lambda p: ometric(om, xi_p, w, p), b[i], rtol=1e-12, maxiter=5000)
+        assert rel_l2(xs[i], xr) <= 1e-7
+
+
+def test_cg_fp32_512_true_residual():
+    """2-D 512^2 Poisson (FP32 vectors, FP64 dots): batched solve to 1e-5; the
+    oracle's FP64 true residual must agree."""
+    plan, om, M, xi_p, w = _setup((512, 512), "power", "f32", "poisson", max_batch=2)
+    b = rounded(np.random.default_rng(10).standard_normal((2, om.latent_size)), "f32")
+    x, its, rel, st = M.cg(to_dev(plan, b), rtol=1e-5, maxiter=1000)
+    assert st == 0, (its, rel)
+    xs = host(x, om.latent_size)
+    for i in range(2):
+        true = rel_l2(ometric(om, xi_p, w, xs[i]), b[i])
+        assert true <= 3e-5, (i, true, rel[i])
+
+
+def test_cg_fixed_iterations_and_notconv():
+    plan, om, M, xi_p, w = _setup((64, 64), "power", "f32", "poisson", max_batch=2)
+    b = rounded(np.random.default_rng(11).standard_normal((2, om.latent_size)), "f32")
+    x, its, rel, st = M.cg(to_dev(plan, b), rtol=0.0, maxiter=7)
+    assert its == [7, 7] and st == 0
+    x, its, rel, st = M.cg(to_dev(plan, b), rtol=1e-12, maxiter=3)
+    assert st == 4  # NRE_ENOTCONV
