@@ -215,6 +215,33 @@ int cg_solve(nre_metric *m, const void *b, void *x, int batch, double rtol,
              int maxiter, int *iters_out, double *relres_out,
              nre_stream_t stream);
 
+/* ================================================================ tracing
+ * Launch accounting for measurement tools.  nre_launch_count() counts every
+ * kernel launch the library has issued in this process.  While tracing is
+ * enabled (nre_prof_enable(1)) each launch is also bracketed by CUDA events on
+ * its stream and tagged with its algorithmic bytes (unique bytes of its global
+ * inputs and outputs); nre_prof_report() synchronises the device and writes a
+ * JSON object {"kernel": [launches, total_ms, bytes], ...} of the traced
+ * launches into buf[len] (NRE_EINVAL if too small), then clears the record. */
+unsigned long long nre_launch_count(void);
+int nre_prof_enable(int on);
+int nre_prof_report(char *buf, size_t len);
+
+/* Preconditioner of cg_solve on this metric (default NRE_PRECOND_NONE: textbook
+ * CG, whose iterates are those of the unpreconditioned method).
+ * NRE_PRECOND_HARMONIC (correlated field only): the exact inverse of the metric
+ * with the weight w replaced by its mean w_bar, applied in harmonic
+ * coordinates.  With c = N w_bar the field block is diag(D), D_k = 1 + c A_k^2,
+ * and the power-spectrum hyper-parameters h couple through the amplitude
+ * Jacobian G = dA/dh; the preconditioner solves the block system by the Schur
+ * complement S = I + c G^T diag(U) G, U_b = sum_{k in b} xi_p[k]^2 / D_k
+ * (n_hyper x n_hyper, factored on the host in FP64, applied in FP32).  It
+ * changes the CG iterates but not the solution; the stopping test stays on the
+ * unpreconditioned residual ||r|| / ||b||.  Setup synchronises `stream`.
+ * This is an addition for solves to a tolerance: the paper runs plain CG. */
+enum { NRE_PRECOND_NONE = 0, NRE_PRECOND_HARMONIC = 1 };
+int metric_set_precond(nre_metric *m, int kind, nre_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

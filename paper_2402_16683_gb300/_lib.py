@@ -15,6 +15,7 @@ NRE_AMP_ARRAY, NRE_AMP_MATERN_FIXED, NRE_AMP_POWER_MODEL = 0, 1, 2
 NRE_LIK_GAUSS, NRE_LIK_POISSON = 0, 1
 NRE_RESP_EXP, NRE_RESP_IDENTITY = 0, 1
 NRE_MODEL_CF, NRE_MODEL_ICR = 0, 1
+NRE_PRECOND_NONE, NRE_PRECOND_HARMONIC = 0, 1
 
 STATUS_NAMES = {0: "NRE_OK", 1: "NRE_EINVAL", 2: "NRE_ENOMEM", 3: "NRE_ECUDA", 4: "NRE_ENOTCONV",
                 5: "NRE_ETIMEDOUT", 6: "NRE_EBUSY", 7: "NRE_EAGAIN"}
@@ -74,6 +75,9 @@ SIGNATURES = {
     "mgvi_rhs": [_P, _P, _P, _P, C.c_int, _P],
     "cg_solve": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                  C.POINTER(C.c_double), _P],
+    "metric_set_precond": [_P, C.c_int, _P],
+    "nre_prof_enable": [C.c_int],
+    "nre_prof_report": [C.c_char_p, C.c_size_t],
 }
 
 _lib = None
@@ -94,6 +98,8 @@ def load():
         f.restype = C.c_int
     lib.nre_last_error.argtypes = []
     lib.nre_last_error.restype = C.c_char_p
+    lib.nre_launch_count.argtypes = []
+    lib.nre_launch_count.restype = C.c_ulonglong
     _lib = lib
     return lib
 

@@ -279,6 +279,12 @@ class Metric:
         check(L.load().mgvi_rhs(self.handle, _ptr(xi_prime), _ptr(eta), _ptr(out), B, _stream()))
         return out
 
+    def set_precond(self, kind="harmonic"):
+        """Select cg's preconditioner: "harmonic" (correlated field: the exact
+        inverse of the metric with w replaced by its mean) or None."""
+        k = L.NRE_PRECOND_HARMONIC if kind == "harmonic" else L.NRE_PRECOND_NONE
+        check(L.load().metric_set_precond(self.handle, k, _stream()))
+
     def cg(self, b, rtol=1e-5, maxiter=100, x=None, raise_on_notconv=False):
         """Solve M x = b per row; returns (x, iterations[B], relres[B], status)."""
         B = b.shape[0]

@@ -52,11 +52,21 @@ def build(force=False, verbose=False, extra_flags=()):
         flags += ["-Xptxas", "-v"]
     jobs = []
     objs = []
+    units = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        if os.path.basename(src) == "sweeps_inst.cu":
+            # one object per (dtype, line length) so the sweep kernels build in parallel
+            for t in ("float", "double"):
+                for l2 in range(3, 13):
+                    units.append((src, f"sweeps_{t}_{1 << l2}",
+                                  [f"-DNRE_SWEEP_T={t}", f"-DNRE_SWEEP_L={1 << l2}"]))
+        else:
+            units.append((src, os.path.basename(src), []))
+    for src, tag, defs in units:
+        obj = os.path.join(BUILD, tag + ".o")
         objs.append(obj)
         if force or verbose or _stale(obj, src, headers):
-            jobs.append([nv, "-c", src, "-o", obj] + flags)
+            jobs.append([nv, "-c", src, "-o", obj] + flags + defs)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

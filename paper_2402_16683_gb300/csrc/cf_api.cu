@@ -35,6 +35,9 @@ AmpView<T> amp_view(const nre_cf_plan* p, const double* abin, int64_t astride) {
   v.astride = astride;
   v.a0 = p->offset_std;
   v.lut = p->lut.as<uint16_t>();
+  v.bpix = nullptr;
+  v.tab = nullptr;
+  v.a0t = T(p->offset_std);
   v.geo.ndim = p->ndim;
   for (int d = 0; d < 3; ++d) v.geo.l2[d] = p->l2[d];
   return v;

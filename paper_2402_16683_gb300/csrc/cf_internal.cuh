@@ -20,7 +20,7 @@
 
 namespace nre {
 
-enum { AMPV_FIXED = 0, AMPV_MODEL = 1 };
+enum { AMPV_FIXED = 0, AMPV_MODEL = 1, AMPV_PIX = 2, AMPV_TAB = 3 };
 
 // Per-sample amplitude model state (doubles), see amp.cu.
 enum { AS_THFL = 0, AS_THSL = 1, AS_THFX = 2, AS_THAS = 3, AS_S = 4, AS_HDR = 8 };
@@ -51,21 +51,33 @@ struct Geo {
 // Amplitude A_full at a harmonic pixel.
 template <typename T>
 struct AmpView {
-  int mode;                // AMPV_FIXED or AMPV_MODEL
-  const T* afull;          // FIXED: [N]
+  int mode;                // AMPV_FIXED, AMPV_MODEL or AMPV_PIX
+  const T* afull;          // FIXED and PIX: A per pixel [N]
   const double* abin;      // MODEL: A per bin of sample b at abin + b * astride
   int64_t astride;         // 0: shared by all samples
   double a0;               // MODEL: amplitude of the zero mode
   const uint16_t* lut;     // MODEL: bin of q (0xFFFF: zero mode)
+  const int16_t* bpix;     // PIX (and TAB when set): bin per pixel (-1: zero mode)
+  const T* tab;            // TAB: A per bin of this CTA's sample, in shared memory
+  T a0t;                   // TAB: a0 in T
   Geo geo;
   __device__ __forceinline__ int bin(int64_t flat) const {
+    if (bpix != nullptr && mode != AMPV_MODEL) return (int)__ldg(&bpix[flat]);
     const int q = geo.q_of(flat);
     return q == 0 ? -1 : (int)__ldg(&lut[q]);
   }
+  // With `stab` (this CTA's per-bin table in shared memory) the per-bin modes
+  // read A from it.
+  __device__ __forceinline__ T amp_t(int b, int64_t flat, int bn, const T* stab) const {
+    if (stab != nullptr && mode != AMPV_FIXED) return bn < 0 ? a0t : stab[bn];
+    return amp(b, flat, bn);
+  }
   __device__ __forceinline__ T amp(int b, int64_t flat, int bn) const {
-    if (mode == AMPV_FIXED) return __ldg(&afull[flat]);
+    if (mode == AMPV_TAB) return bn < 0 ? a0t : tab[bn];
+    if (mode != AMPV_MODEL) return __ldg(&afull[flat]);
     return bn < 0 ? T(a0) : T(__ldg(&abin[b * astride + bn]));
   }
+  __device__ __forceinline__ bool binned() const { return mode != AMPV_FIXED; }
 };
 
 enum { PRO_BUF = 0, PRO_AMP = 1, PRO_SQRTW = 2 };
@@ -81,15 +93,25 @@ struct Pro {
   const double* dA;   // PRO_AMP: per-sample dA bins (nullptr: none)
   int nb;
   const T* w;         // PRO_SQRTW: weights [N]
+  const T* sdA;       // dA of this CTA's sample in shared memory (set by the kernel)
   AmpView<T> av;
-  __device__ __forceinline__ T load(int b, int64_t flat) const {
-    const T v = x[b * xs + flat];
+  __device__ __forceinline__ T load(int b, int64_t flat) const { return apply(b, flat, x[b * xs + flat]); }
+  // The prologue of the input value v = x[b][flat] (already loaded); stab /
+  // stdA: per-bin A and dA of this CTA's sample in shared memory, or nullptr.
+  __device__ __forceinline__ T apply(int b, int64_t flat, T v, const T* stab = nullptr,
+                                     const T* stdA = nullptr) const {
     if (mode == PRO_BUF) return v;
     if (mode == PRO_SQRTW) return sqrt(__ldg(&w[flat])) * v;
-    const int bn = av.mode == AMPV_MODEL ? av.bin(flat) : -1;
-    T u = av.amp(b, flat, bn) * v;
-    if (dA != nullptr && bn >= 0) u += T(__ldg(&dA[b * nb + bn])) * xi_p[b * ps + flat];
+    const int bn = av.binned() ? av.bin(flat) : -1;
+    T u = av.amp_t(b, flat, bn, stab) * v;
+    if (dA != nullptr && bn >= 0) u += (stdA ? stdA[bn] : T(__ldg(&dA[b * nb + bn]))) * xi_p[b * ps + flat];
     return u;
+  }
+  // Values at flat and flat + 1 (flat even) as one complex pair.
+  __device__ __forceinline__ typename CplxT<T>::type load2(int b, int64_t flat) const {
+    typedef typename CplxT<T>::type C;
+    if (mode == PRO_BUF) return *reinterpret_cast<const C*>(x + b * xs + flat);
+    return cmake<C>(load(b, flat), load(b, flat + 1));
   }
 };
 
@@ -114,7 +136,17 @@ struct Epi {
   int bins;           // accumulate the per-bin sums
   AmpView<T> av;
 
-  __device__ __forceinline__ void store(int b, int64_t flat, T val, double* hist) const {
+  // Writes the output of pixel `flat` of sample b.  EPI_AMP with bins also
+  // returns the pixel's contribution xi_p * value to its log-|k| bin (bn = -1:
+  // none); the caller reduces the contributions.
+  __device__ __forceinline__ void store(int b, int64_t flat, T val, int& bn_out, T& contrib) const {
+    store_b(b, flat, val, (mode == EPI_AMP && base != nullptr) ? base[b * bs + flat] : T(0), bn_out, contrib);
+  }
+  // As store, with the EPI_AMP base value already loaded.
+  __device__ __forceinline__ void store_b(int b, int64_t flat, T val, T bval, int& bn_out, T& contrib,
+                                          const T* stab = nullptr) const {
+    bn_out = -1;
+    contrib = T(0);
     if (mode == EPI_BUF) {
       y[b * ys + flat] = val;
     } else if (mode == EPI_OFFSET) {
@@ -136,12 +168,31 @@ struct Epi {
       }
       y[b * ys + flat] = w;
     } else {
-      const int bn = av.mode == AMPV_MODEL ? av.bin(flat) : -1;
-      T o = av.amp(b, flat, bn) * val;
-      if (base != nullptr) o += base[b * bs + flat];
+      const int bn = av.binned() ? av.bin(flat) : -1;
+      const T o = av.amp_t(b, flat, bn, stab) * val + bval;
       y[b * ys + flat] = o;
-      if (bins && bn >= 0) atomicAdd(&hist[bn], double(xi_p[b * ps + flat] * val));
+      if (bins && bn >= 0) {
+        bn_out = bn;
+        contrib = xi_p[b * ps + flat] * val;
+      }
     }
+  }
+  // Outputs at flat and flat + 1 (flat even).
+  __device__ __forceinline__ void store2(int b, int64_t flat, T v0, T v1, int (&bn)[2], T (&c)[2]) const {
+    if (mode == EPI_BUF) {
+      *reinterpret_cast<typename CplxT<T>::type*>(y + b * ys + flat) = cmake<typename CplxT<T>::type>(v0, v1);
+      bn[0] = bn[1] = -1;
+      c[0] = c[1] = T(0);
+      return;
+    }
+    store(b, flat, v0, bn[0], c[0]);
+    store(b, flat + 1, v1, bn[1], c[1]);
+  }
+  __device__ __forceinline__ void store(int b, int64_t flat, T val, double* hist) const {
+    int bn;
+    T c;
+    store(b, flat, val, bn, c);
+    if (bn >= 0) atomicAdd(&hist[bn], double(c));
   }
 };
 
@@ -150,6 +201,11 @@ template <typename T>
 struct Mid {
   const T* w;  // [N]
   __device__ __forceinline__ T apply(int64_t flat, T y) const { return __ldg(&w[flat]) * y; }
+  __device__ __forceinline__ typename CplxT<T>::type apply2(int64_t flat, T y0, T y1) const {
+    typedef typename CplxT<T>::type C;
+    const C ww = __ldg(reinterpret_cast<const C*>(w + flat));
+    return cmake<C>(ww.x * y0, ww.y * y1);
+  }
 };
 
 // Arguments of one row sweep (last axis, length L).

@@ -34,26 +34,83 @@ __device__ void write_partial(double acc, double* part) {
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
+// As write_partial; the last block of system blockIdx.y to finish then sums
+// the partials in block order (deterministic) and calls fin(total) from
+// thread 0.  counter[system] must be 0 on entry and is reset.
+template <class F>
+__device__ void finish_partial(double acc, double* part, unsigned* counter, F fin) {
+  __shared__ double red[CG_THREADS / 32];
+  __shared__ bool last;
+  const double t = block_sum(acc, red);
+  const int b = blockIdx.y, nblk = gridDim.x;
+  if (threadIdx.x == 0) {
+    part[b * nblk + blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(&counter[b], 1u) == (unsigned)(nblk - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0;
+    const volatile double* vp = part + b * nblk;
+    for (int i = 0; i < nblk; ++i) s += vp[i];
+    fin(s);
+    counter[b] = 0;
+  }
+}
+
+// 16-byte vector of T (4 floats or 2 doubles).
+template <typename T>
+struct alignas(16) V16 {
+  static constexpr int W = 16 / sizeof(T);
+  T e[W];
+};
+
+// Grid-stride loop over the n entries of system blockIdx.y, 16-byte vectors
+// first (the system offset is a multiple of 64 elements), then the scalar
+// tail.  f(i, w) handles W consecutive entries starting at i (w = W) or one
+// entry (w = 1).
+template <typename T, class F>
+__device__ __forceinline__ void for_vec(int64_t n, F f) {
+  constexpr int W = V16<T>::W;
+  const int64_t nv = n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += stride) f(v * W, W);
+  for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) f(i, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ V16<T> ldv(const T* p) { return *reinterpret_cast<const V16<T>*>(p); }
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const V16<T>& v) { *reinterpret_cast<V16<T>*>(p) = v; }
+
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_init(const T* b, T* x, T* r, T* p, int64_t n,
                                                        int64_t S, double* part) {
   const int64_t off = (int64_t)blockIdx.y * S;
   double acc = 0.0;
-  T run = T(0);
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T v = b[off + i];
-    x[off + i] = T(0);
-    r[off + i] = v;
-    p[off + i] = v;
-    run += v * v;
-    if (++cnt == 8) {
+  for_vec<T>(n, [&](int64_t i, int w) {
+    if (w > 1) {
+      const V16<T> v = ldv(b + off + i);
+      V16<T> z;
+      T run = T(0);  // one vector
+#pragma unroll
+      for (int k = 0; k < V16<T>::W; ++k) {
+        z.e[k] = T(0);
+        run += v.e[k] * v.e[k];
+      }
+      stv(x + off + i, z);
+      stv(r + off + i, v);
+      stv(p + off + i, v);
       acc += double(run);
-      run = T(0);
-      cnt = 0;
+    } else {
+      const T v = b[off + i];
+      x[off + i] = T(0);
+      r[off + i] = v;
+      p[off + i] = v;
+      acc += double(v * v);
     }
-  }
-  acc += double(run);
+  });
   write_partial(acc, part);
 }
 
@@ -68,92 +125,108 @@ __global__ void k_cg_start(double* sc, const double* part, int nblk, double rtol
   c[SC_ALPHA] = 0.0;
   c[SC_BETA] = 0.0;
   c[SC_ITERS] = 0.0;
-  c[SC_ACTIVE] = (s > 0.0 && (rtol <= 0.0 || sqrt(s) > rtol * sqrt(s))) ? 1.0 : 0.0;
+  c[SC_ACTIVE] = (s > 0.0 && rtol < 1.0) ? 1.0 : 0.0;
 }
 
+// p.q, then alpha = r.r / p.q for the system (last block).
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, int64_t n, int64_t S,
-                                                      double* part) {
+                                                      double* part, unsigned* counter, double* sc) {
   const int64_t off = (int64_t)blockIdx.y * S;
   double acc = 0.0;
-  T run = T(0);
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    run += a[off + i] * q[off + i];
-    if (++cnt == 8) {
-      acc += double(run);
-      run = T(0);
-      cnt = 0;
+  for_vec<T>(n, [&](int64_t i, int w) {
+    T run = T(0);  // one vector's products in T, folded into FP64
+    if (w > 1) {
+      const V16<T> u = ldv(a + off + i), v = ldv(q + off + i);
+#pragma unroll
+      for (int k = 0; k < V16<T>::W; ++k) run += u.e[k] * v.e[k];
+    } else {
+      run = a[off + i] * q[off + i];
     }
-  }
-  acc += double(run);
-  write_partial(acc, part);
+    acc += double(run);
+  });
+  double* c = sc + blockIdx.y * SC_N;
+  finish_partial(acc, part, counter, [&](double pq) {
+    c[SC_ALPHA] = (c[SC_ACTIVE] != 0.0 && pq != 0.0) ? c[SC_RR] / pq : 0.0;
+  });
 }
 
-// alpha = r.r / p.Mp from the dot partials (every block sums them in the same
-// order), then x += alpha p, r -= alpha q and partials of r'.r'.
+// x += alpha p, r -= alpha q; then (last block) beta = r'.r' / r.r, the
+// iteration count and the convergence test.  A system that has converged
+// keeps beta = 0 and its x, r frozen.
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_update(T* x, T* r, const T* p, const T* q, int64_t n,
-                                                         int64_t S, const double* sc, const double* pq_part,
-                                                         double* rr_part) {
-  const int b = blockIdx.y, nblk = gridDim.x;
-  const double* c = sc + b * SC_N;
+                                                         int64_t S, double* sc, double* rr_part,
+                                                         unsigned* counter, double rtol) {
+  const int b = blockIdx.y;
+  double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
-  double pq = 0.0;
-  for (int i = 0; i < nblk; ++i) pq += pq_part[b * nblk + i];
-  const double alpha_d = active && pq != 0.0 ? c[SC_RR] / pq : 0.0;
-  const T alpha = T(alpha_d);
+  const T alpha = T(c[SC_ALPHA]);
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
-  T run = T(0);
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = r[off + i];
-    if (active) {
-      x[off + i] += alpha * p[off + i];
-      ri -= alpha * q[off + i];
-      r[off + i] = ri;
+  for_vec<T>(n, [&](int64_t i, int w) {
+    T run = T(0);
+    if (w > 1) {
+      V16<T> ri = ldv(r + off + i);
+      if (active) {
+        V16<T> xi = ldv(x + off + i);
+        const V16<T> pi = ldv(p + off + i), qi = ldv(q + off + i);
+#pragma unroll
+        for (int k = 0; k < V16<T>::W; ++k) {
+          xi.e[k] += alpha * pi.e[k];
+          ri.e[k] -= alpha * qi.e[k];
+        }
+        stv(x + off + i, xi);
+        stv(r + off + i, ri);
+      }
+#pragma unroll
+      for (int k = 0; k < V16<T>::W; ++k) run += ri.e[k] * ri.e[k];
+    } else {
+      T ri = r[off + i];
+      if (active) {
+        x[off + i] += alpha * p[off + i];
+        ri -= alpha * q[off + i];
+        r[off + i] = ri;
+      }
+      run = ri * ri;
     }
-    run += ri * ri;
-    if (++cnt == 8) {
-      acc += double(run);
-      run = T(0);
-      cnt = 0;
+    acc += double(run);
+  });
+  finish_partial(acc, rr_part, counter, [&](double rr_new) {
+    if (c[SC_ACTIVE] == 0.0) {
+      c[SC_BETA] = 0.0;
+      return;
     }
-  }
-  acc += double(run);
-  write_partial(acc, rr_part);
+    c[SC_BETA] = rr_new / c[SC_RR];
+    c[SC_RR] = rr_new;
+    c[SC_ITERS] += 1.0;
+    if (rtol > 0.0 && sqrt(rr_new) <= rtol * sqrt(c[SC_BB])) {
+      c[SC_ACTIVE] = 0.0;
+      c[SC_BETA] = 0.0;
+    }
+  });
 }
 
-// beta = r'.r' / r.r; p = r' + beta p; bookkeeping of the scalars.  Block 0 of
-// each system updates the scalars after all blocks have read them: the scalar
-// update is deferred to k_cg_finish.
+// p = r + beta p with beta from the update kernel (0 for a frozen system).
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_pupdate(T* p, const T* r, int64_t n, int64_t S,
-                                                          const double* sc, const double* rr_part,
-                                                          int nblk_rr) {
+                                                          const double* sc) {
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
   if (c[SC_ACTIVE] == 0.0) return;
-  double rr_new = 0.0;
-  for (int i = 0; i < nblk_rr; ++i) rr_new += rr_part[b * nblk_rr + i];
-  const T beta = T(rr_new / c[SC_RR]);
+  const T beta = T(c[SC_BETA]);
   const int64_t off = (int64_t)b * S;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[off + i] = r[off + i] + beta * p[off + i];
-}
-
-__global__ void k_cg_finish(double* sc, const double* rr_part, int nblk, double rtol) {
-  const int b = blockIdx.x;
-  if (threadIdx.x != 0) return;
-  double* c = sc + b * SC_N;
-  if (c[SC_ACTIVE] == 0.0) return;
-  double rr_new = 0.0;
-  for (int i = 0; i < nblk; ++i) rr_new += rr_part[b * nblk + i];
-  c[SC_BETA] = rr_new / c[SC_RR];
-  c[SC_RR] = rr_new;
-  c[SC_ITERS] += 1.0;
-  if (rtol > 0.0 && sqrt(rr_new) <= rtol * sqrt(c[SC_BB])) c[SC_ACTIVE] = 0.0;
+  for_vec<T>(n, [&](int64_t i, int w) {
+    if (w > 1) {
+      const V16<T> ri = ldv(r + off + i);
+      V16<T> pi = ldv(p + off + i);
+#pragma unroll
+      for (int k = 0; k < V16<T>::W; ++k) pi.e[k] = ri.e[k] + beta * pi.e[k];
+      stv(p + off + i, pi);
+    } else {
+      p[off + i] = r[off + i] + beta * p[off + i];
+    }
+  });
 }
 
 template <typename T>
@@ -165,13 +238,15 @@ int cg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* 
   NRE_TRY(ensure(m->cg_q, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_sc, (size_t)B * SC_N * sizeof(double)));
   const int nblk = cg_blocks(n);
-  NRE_TRY(ensure(m->cg_part, (size_t)2 * B * nblk * sizeof(double)));
+  NRE_TRY(ensure(m->cg_part, (size_t)2 * B * nblk * sizeof(double) + (size_t)B * sizeof(unsigned)));
   T* r = m->cg_r.as<T>();
   T* p = m->cg_p.as<T>();
   T* q = m->cg_q.as<T>();
   double* sc = m->cg_sc.as<double>();
   double* part_a = m->cg_part.as<double>();
   double* part_b = part_a + (size_t)B * nblk;
+  unsigned* counter = reinterpret_cast<unsigned*>(part_b + (size_t)B * nblk);
+  NRE_TRY_CUDA(cudaMemsetAsync(counter, 0, (size_t)B * sizeof(unsigned), st));
   const dim3 grid(nblk, B);
   const double vb = (double)B * n * sizeof(T);
   prof_begin("cg_init", 4 * vb, st);
@@ -186,16 +261,13 @@ int cg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* 
   for (int it = 0; it < maxiter; ++it) {
     NRE_TRY(metric_apply_impl(m, p, q, B, st));
     prof_begin("cg_dot", 2 * vb, st);
-    k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(p, q, n, S, part_a);
+    k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(p, q, n, S, part_a, counter, sc);
     prof_end(st);
     prof_begin("cg_update", 6 * vb, st);
-    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, r, p, q, n, S, sc, part_a, part_b);
+    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, r, p, q, n, S, sc, part_b, counter, rtol);
     prof_end(st);
     prof_begin("cg_pupdate", 3 * vb, st);
-    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(p, r, n, S, sc, part_b, nblk);
-    prof_end(st);
-    prof_begin("cg_scalars", 0.0, st);
-    k_cg_finish<<<B, 32, 0, st>>>(sc, part_b, nblk, rtol);
+    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(p, r, n, S, sc);
     prof_end(st);
     NRE_CHECK_LAUNCH();
     if (rtol > 0.0 && (it + 1) % check_every == 0 && it + 1 < maxiter) {
@@ -233,6 +305,8 @@ extern "C" int cg_solve(nre_metric* m, const void* b, void* x, int batch, double
   if (batch == 0) return NRE_OK;
   if (!b || !x) return set_error(NRE_EINVAL, "NULL array argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (m->precond != NRE_PRECOND_NONE)
+    return pcg_solve_impl(m, b, x, batch, rtol, maxiter, iters_out, relres_out, st);
   if (m->dtype == NRE_F64)
     return cg_t<double>(m, (const double*)b, (double*)x, batch, rtol, maxiter, iters_out, relres_out, st);
   return cg_t<float>(m, (const float*)b, (float*)x, batch, rtol, maxiter, iters_out, relres_out, st);

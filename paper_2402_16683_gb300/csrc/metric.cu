@@ -20,6 +20,35 @@ using namespace nre;
 
 namespace {
 
+// Per-pixel amplitude and bin of the expansion point (power model).
+template <typename T>
+__global__ void k_pix_tables(AmpView<T> av, T* apix, int16_t* bpix, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int bn = av.bin(i);
+    apix[i] = av.amp(0, i, bn);
+    bpix[i] = (int16_t)bn;
+  }
+}
+
+}  // namespace
+
+namespace nre {
+template <typename T>
+AmpView<T> metric_view(const nre_metric* m) {
+  const nre_cf_plan* p = m->cf;
+  if (p->amp_kind != NRE_AMP_POWER_MODEL) return amp_view<T>(p, nullptr, 0);
+  AmpView<T> v = amp_view<T>(p, m->state.as<double>() + as_A(p->n_bins), 0);
+  v.mode = AMPV_PIX;
+  v.afull = m->apix.as<T>();
+  v.bpix = m->bpix.as<int16_t>();
+  return v;
+}
+template AmpView<float> metric_view<float>(const nre_metric*);
+template AmpView<double> metric_view<double>(const nre_metric*);
+}  // namespace nre
+
+namespace {
+
 template <typename T>
 int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   nre_cf_plan* p = m->cf;
@@ -54,6 +83,12 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
     NRE_TRY(m->part.alloc((size_t)m->max_batch * max_parts(p) * nb * sizeof(double)));
     NRE_TRY(amp_forward<T>(amp_prior_of(p), xp + N, 0, m->state.as<double>(), 1, st));
     pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+    NRE_TRY(m->apix.alloc(N * sizeof(T)));
+    NRE_TRY(m->bpix.alloc(N * sizeof(int16_t)));
+    prof_begin("pix_tables", (double)N * (sizeof(T) + 2), st);
+    k_pix_tables<T><<<304, 256, 0, st>>>(pro.av, m->apix.as<T>(), m->bpix.as<int16_t>(), N);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
   } else {
     pro.av = amp_view<T>(p, nullptr, 0);
   }
@@ -82,7 +117,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
   if (model) {
     NRE_TRY(amp_jvp<T>(pr, m->state.as<double>(), 0, v + N, S, m->dA.as<double>(), B, st));
-    pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+    pro.av = metric_view<T>(m);
     pro.dA = m->dA.as<double>();
     pro.nb = nb;
     pro.xi_p = xp;
@@ -123,7 +158,7 @@ int cf_mgvi_rhs(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cud
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   const int nb = p->n_bins;
   if (model) {
-    epi.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
+    epi.av = metric_view<T>(m);
     epi.bins = 1;
     epi.xi_p = xp;
     epi.ps = 0;

@@ -1,0 +1,154 @@
+// Register-resident complex FFT of one line per thread group.
+//
+// A line of L = 2^n complex values is held by L/8 threads, 8 values each.  The
+// transform is the self-sorting (Stockham) sequence of radix-8 passes and one
+// final radix-4 or radix-2 pass (forward sign exp(-2 pi i k x / L)):
+//   pass with radix R, Ns = product of earlier radices, butterflies j < L/R:
+//     v_r = in[j + r L/R] * W_{Ns R}^{(j mod Ns) r},  v <- DFT_R(v),
+//     out[(j div Ns) Ns R + (j mod Ns) + r Ns] = v_r.
+// Thread t owns the butterflies j = t + (L/8) m, m < 8/R, so the first pass
+// reads in[t + s L/8] (s = 0..7): exactly the elements the thread loads from
+// global memory, coalesced across threads.  After the last pass the thread
+// owns X[t + s L/8] in natural order, which feeds the Hartley unpack, the
+// epilogue stores or the next transform without another pass through shared
+// memory.  Between passes the values go through a padded shared buffer of the
+// line (one pad element per 16).
+#pragma once
+
+#include <type_traits>
+
+#include "fft.cuh"
+
+namespace nre {
+
+__host__ __device__ constexpr int rpad(int e) { return e + (e >> 4); }
+// Line stride: padded length plus one, so that lines sit on different banks
+// (the stride is an odd number of complex elements).
+__host__ __device__ constexpr int rline(int L) { return L + L / 16 + 1; }
+// Line stride when NL lines are interleaved across the lanes of a warp: the
+// lines start 16/NL complex elements apart modulo 16.
+__host__ __device__ constexpr int rline_il(int L, int NL) { return L + L / 16 + (NL < 16 ? 16 / NL : 1); }
+
+struct SyncBlock {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncWarp {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+// Named barrier of the `count` threads of one line (ids 1..15; 0 is __syncthreads).
+struct SyncNamed {
+  int id, count;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+  }
+};
+
+template <typename C, int L, int NS, int LPT>
+struct RegPass {
+  static constexpr int REM = L / NS;
+  static constexpr int R = REM >= 8 ? 8 : REM;
+  static constexpr int T8 = L / 8;
+  static constexpr int M = 8 / R;
+  static constexpr bool LAST = (NS * R == L);
+
+  template <class Sync>
+  __device__ __forceinline__ static void run(C (&v)[LPT][8], C* const* sm,
+                                             const C* __restrict__ tw, int t, Sync sync) {
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        if constexpr (NS > 1) {
+          const int j = t + T8 * m;
+          const int k = j & (NS - 1);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[q][m * R + r] = cmul(v[q][m * R + r], tw[k * r * (L / (NS * R))]);
+        }
+        dftR<R>(&v[q][m * R]);
+      }
+    }
+    if constexpr (LAST) {
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        C o[8];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+          for (int r = 0; r < R; ++r) o[m + r * M] = v[q][m * R + r];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[q][s] = o[s];
+      }
+    } else {
+      typedef RegPass<C, L, NS * R, LPT> Next;
+      constexpr int R2 = Next::R, M2 = 8 / R2;
+#pragma unroll
+      for (int q = 0; q < LPT; ++q)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int j = t + T8 * m;
+          const int k = j & (NS - 1);
+          const int base = (j - k) * R + k;
+#pragma unroll
+          for (int r = 0; r < R; ++r) sm[q][rpad(base + r * NS)] = v[q][m * R + r];
+        }
+      sync();
+#pragma unroll
+      for (int q = 0; q < LPT; ++q)
+#pragma unroll
+        for (int m = 0; m < M2; ++m)
+#pragma unroll
+          for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][rpad(t + T8 * m + r * (L / R2))];
+      sync();
+      Next::run(v, sm, tw, t, sync);
+    }
+  }
+};
+
+// Forward FFT of LPT lines; v[q][s] = line_q[t + s L/8] in and X_q[t + s L/8] out.
+template <typename C, int L, int LPT, class Sync>
+__device__ __forceinline__ void reg_fft(C (&v)[LPT][8], C* const* sm, const C* tw, int t, Sync sync) {
+  RegPass<C, L, 1, LPT>::run(v, sm, tw, t, sync);
+}
+
+// zm[q][s] = X_q[-(t + s L/8) mod L] through the shared line buffers.
+template <typename C, int L, int LPT, class Sync>
+__device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8], C* const* sm, int t,
+                                           Sync sync) {
+  constexpr int T8 = L / 8;
+#pragma unroll
+  for (int q = 0; q < LPT; ++q)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) sm[q][rpad(t + T8 * s)] = v[q][s];
+  sync();
+#pragma unroll
+  for (int q = 0; q < LPT; ++q)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) zm[q][s] = sm[q][rpad((L - (t + T8 * s)) & (L - 1))];
+  sync();
+}
+
+// Sum `val` over the runs of equal `key` among the lanes of a warp (runs are
+// maximal ranges of consecutive lanes with the same key) and add each run's
+// total to hist[key] from its last lane.  key < 0: no contribution.
+// The run sums are formed in V (the plan's value type: FP32 products of FP32
+// data are summed over at most 32 lanes) and accumulated in FP64.
+template <typename V>
+__device__ __forceinline__ void warp_run_add(int key, V val, double* hist) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  if (__all_sync(full, key < 0)) return;
+  const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const V ov = __shfl_up_sync(full, val, o);
+    const int orid = __shfl_up_sync(full, rid, o);
+    if (lane >= o && orid == rid) val += ov;
+  }
+  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  if (tail && key >= 0) atomicAdd(&hist[key], double(val));
+}
+
+}  // namespace nre

@@ -12,9 +12,12 @@
 // 2-element vector load per position, so loads and stores stay coalesced.  The
 // axis-0 sweep of the metric runs the first transform's last DHT, t = w * y and
 // the second transform's first DHT back to back in shared memory.
-#include "cf_internal.cuh"
+#include "sweeps_launch.cuh"
 
 namespace nre {
+
+NRE_DECL_SWEEP_T(float)
+NRE_DECL_SWEEP_T(double)
 
 constexpr int SWEEP_THREADS = 256;
 
@@ -228,45 +231,11 @@ int col_width(int L, int64_t inner, int csize) {
   while (W > inner) W >>= 1;
   return W;
 }
-constexpr int kMaxGridX = 128;  // CTAs per sample of a sweep (fixed per plan)
 
 template <typename T>
 size_t row_smem(int L, int nl, int nhist, int nb) {
   return (size_t)2 * nl * LayRow::stride(L) * sizeof(typename CplxT<T>::type) +
          (size_t)nhist * nb * sizeof(double);
-}
-
-// Algorithmic bytes of a sweep: per-sample arrays count B times, arrays shared
-// by the batch (expansion point, weights, fixed spectrum) once.
-template <typename T>
-double sweep_bytes(const Pro<T>& pro, const Epi<T>& epi, const Mid<T>* mid, bool has_mid, int B,
-                   int64_t N) {
-  const double e = (double)N * sizeof(T);
-  double per = 1.0, shared = 0.0;  // the input x and the output y
-  per += 1.0;
-  if (pro.mode == PRO_AMP) {
-    if (pro.av.mode == AMPV_FIXED) shared += 1.0;
-    if (pro.dA) (pro.ps ? per : shared) += 1.0;
-  } else if (pro.mode == PRO_SQRTW) {
-    shared += 1.0;
-  }
-  if (epi.mode == EPI_AMP) {
-    if (epi.base) per += 1.0;
-    if (epi.bins) (epi.ps ? per : shared) += 1.0;
-    if (epi.av.mode == AMPV_FIXED && !(pro.mode == PRO_AMP && pro.av.mode == AMPV_FIXED)) shared += 1.0;
-  } else if (epi.mode == EPI_WEIGHT && epi.mask) {
-    shared += 1.0;
-  }
-  if (has_mid) shared += 1.0;
-  return e * (per * B + shared);
-}
-
-const char* row_name(int pm, bool mid, int es) {
-  static const char* names[2][4] = {
-      {"row_sweep_f32_1d", "row_sweep_f32_1d_metric", "row_sweep_f32_2d", "row_sweep_f32_3d"},
-      {"row_sweep_f64_1d", "row_sweep_f64_1d_metric", "row_sweep_f64_2d", "row_sweep_f64_3d"}};
-  const int t = es == 8 ? 1 : 0;
-  return pm == 1 ? names[t][mid ? 1 : 0] : names[t][pm];
 }
 
 template <typename T, int PM, bool MID>
@@ -293,6 +262,59 @@ int launch_col(const ColArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int
   return NRE_OK;
 }
 
+// ---- register-resident kernels (lines of 8..4096): instantiated per
+// (dtype, line length) in sweeps_inst.cu, declared in sweeps_launch.cuh.
+#define NRE_L_CASE(K, LL, ...) \
+  case K: {                      \
+    constexpr int L = LL;        \
+    __VA_ARGS__;                 \
+  }
+#define NRE_L_SWITCH(L2, ...)                \
+  switch (L2) {                              \
+    NRE_L_CASE(3, 8, __VA_ARGS__)            \
+    NRE_L_CASE(4, 16, __VA_ARGS__)           \
+    NRE_L_CASE(5, 32, __VA_ARGS__)           \
+    NRE_L_CASE(6, 64, __VA_ARGS__)           \
+    NRE_L_CASE(7, 128, __VA_ARGS__)          \
+    NRE_L_CASE(8, 256, __VA_ARGS__)          \
+    NRE_L_CASE(9, 512, __VA_ARGS__)          \
+    NRE_L_CASE(10, 1024, __VA_ARGS__)        \
+    NRE_L_CASE(11, 2048, __VA_ARGS__)        \
+    NRE_L_CASE(12, 4096, __VA_ARGS__)        \
+    default: break;                          \
+  }
+
+// Register-kernel sweeps.  *handled = false (nothing launched) when the line
+// length or the shared-memory budget needs the generic kernels.
+template <typename T>
+int row_sweep_reg(RowArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_t st, int64_t N,
+                  bool* handled) {
+  *handled = false;
+  dim3 grid;
+  size_t smem = 0;
+  NRE_L_SWITCH(a.log2L, {
+    if (row_reg_plan<T, L>(a, B, bins, &grid, &smem, nparts) != NRE_OK) return NRE_OK;
+    *handled = true;
+    return row_reg_L<T, L>(a, mid, grid, smem, st, N);
+  })
+  return NRE_OK;
+}
+
+template <typename T>
+int col_sweep_reg(ColArgs<T> a, int64_t outer, bool mid, int B, bool bins, int* nparts, cudaStream_t st,
+                  int64_t N, bool* handled) {
+  *handled = false;
+  NRE_L_SWITCH(a.log2L, {
+    if (ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0) > 200 * 1024) return NRE_OK;
+    a.W = ColShape<L>::W < a.inner ? ColShape<L>::W : (int)a.inner;
+    a.nblk = a.inner / a.W;
+    a.n_units = outer * a.nblk;
+    *handled = true;
+    return col_reg_L<T, L>(a, mid, B, bins, nparts, st, N);
+  })
+  return NRE_OK;
+}
+
 template <typename T>
 int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
               const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st) {
@@ -311,6 +333,11 @@ int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
   a.partials = partials;
   a.grows = p->grows.as<int>();
   a.gflags = p->gflags.as<int>();
+  const bool bins = epi.mode == EPI_AMP && epi.bins;
+  a.n_units = D == 1 ? (B + 1) / 2 : p->n_groups;
+  bool handled = false;
+  NRE_TRY(row_sweep_reg<T>(a, mid != nullptr, B, bins, nparts, st, p->N, &handled));
+  if (handled) return NRE_OK;
   const int nl = row_lines(a.L);
   dim3 grid;
   int nhist;
@@ -354,6 +381,15 @@ int col_sweep(const nre_cf_plan* p, int axis, int B, const Pro<T>& pro, const Ep
   for (int d = axis + 1; d < p->ndim; ++d) inner *= p->n[d];
   for (int d = 0; d < axis; ++d) outer *= p->n[d];
   a.inner = inner;
+  a.pro = pro;
+  a.epi = epi;
+  if (mid) a.mid = *mid;
+  a.nb = p->n_bins > 0 ? p->n_bins : 1;
+  a.partials = partials;
+  bool handled = false;
+  NRE_TRY(col_sweep_reg<T>(a, outer, mid != nullptr, B, epi.mode == EPI_AMP && epi.bins, nparts, st, p->N,
+                           &handled));
+  if (handled) return NRE_OK;
   a.W = col_width(a.L, inner, (int)sizeof(typename CplxT<T>::type));
   a.nblk = inner / a.W;
   a.n_units = outer * a.nblk;

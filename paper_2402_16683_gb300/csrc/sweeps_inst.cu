@@ -1,0 +1,129 @@
+// One (dtype, line length) instantiation of the register-resident sweep
+// kernels and their launchers.  The build compiles this file once per
+// combination with -DNRE_SWEEP_T=float|double -DNRE_SWEEP_L=8..4096; without
+// the defines it compiles to nothing.
+#include "sweeps_launch.cuh"
+
+#if defined(NRE_SWEEP_T) && defined(NRE_SWEEP_L)
+
+namespace nre {
+
+template <typename K>
+static int set_smem(K k, size_t smem) {
+  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return NRE_OK;
+}
+
+template <typename T, int L, int PM, bool MID, int PK, int EK>
+int launch_row_k(const RowArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+  NRE_TRY(set_smem(k_row_reg<T, L, PM, MID, PK, EK>, smem));
+  k_row_reg<T, L, PM, MID, PK, EK><<<grid, RowShape<L>::NT, smem, st>>>(a);
+  return NRE_OK;
+}
+
+template <typename T, int L, int PM>
+int launch_row_pm(const RowArgs<T>& a, int pk, int ek, dim3 grid, size_t smem, cudaStream_t st) {
+  if (pk == SK_TAB && ek == SK_BUF) return launch_row_k<T, L, PM, false, SK_TAB, SK_BUF>(a, grid, smem, st);
+  if (pk == SK_BUF && ek == SK_TAB) return launch_row_k<T, L, PM, false, SK_BUF, SK_TAB>(a, grid, smem, st);
+  if (pk == SK_BUF && ek == SK_BUF) return launch_row_k<T, L, PM, false, SK_BUF, SK_BUF>(a, grid, smem, st);
+  return launch_row_k<T, L, PM, false, SK_GEN, SK_GEN>(a, grid, smem, st);
+}
+
+template <typename T>
+int pro_kind(const Pro<T>& p) {
+  if (p.mode == PRO_BUF) return SK_BUF;
+  return (p.mode == PRO_AMP && p.av.mode == AMPV_PIX && p.av.bpix != nullptr) ? SK_TAB : SK_GEN;
+}
+template <typename T>
+int epi_kind(const Epi<T>& e) {
+  if (e.mode == EPI_BUF) return SK_BUF;
+  return (e.mode == EPI_AMP && e.av.mode == AMPV_PIX && e.av.bpix != nullptr) ? SK_TAB : SK_GEN;
+}
+
+template <typename T, int L>
+int row_reg_L(RowArgs<T> a, bool mid, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
+  const char* name = row_name(a.pm, mid, sizeof(T));
+  prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, mid, a.B, N), st);
+  int s;
+  if (a.pm == 1) {
+    s = mid ? launch_row_k<T, L, 1, true, SK_GEN, SK_GEN>(a, grid, smem, st)
+            : launch_row_k<T, L, 1, false, SK_GEN, SK_GEN>(a, grid, smem, st);
+  } else {
+    const int pk = pro_kind(a.pro), ek = epi_kind(a.epi);
+    s = a.pm == 2 ? launch_row_pm<T, L, 2>(a, pk, ek, grid, smem, st)
+                  : launch_row_pm<T, L, 3>(a, pk, ek, grid, smem, st);
+  }
+  prof_end(st);
+  NRE_TRY(s);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+// CTAs per sample of a persistent sweep: about kResidentCTAs in total, at least
+// one, at most one per unit group and at most kMaxGridX.
+inline int persistent_gx(int64_t groups, int B) {
+  int64_t gx = (kResidentCTAs + B - 1) / B;
+  if (gx > groups) gx = groups;
+  if (gx > kMaxGridX) gx = kMaxGridX;
+  return gx < 1 ? 1 : (int)gx;
+}
+
+template <typename T, int L>
+int row_reg_plan(RowArgs<T>& a, int B, bool bins, dim3* grid, size_t* smem, int* nparts) {
+  constexpr int NU = RowShape<L>::NU;
+  const bool sbase = a.epi.mode == EPI_AMP && a.epi.base != nullptr;
+  int nhist;
+  if (a.pm == 1) {
+    a.n_units = (B + 1) / 2;
+    *grid = dim3((a.n_units + NU - 1) / NU, 1);  // one group per CTA: histograms per sample
+    nhist = 2 * NU;
+    *nparts = 1;
+  } else {
+    const int gx = persistent_gx((a.n_units + NU - 1) / NU, B);
+    *grid = dim3(gx, B);
+    nhist = 1;
+    *nparts = gx;
+  }
+  a.nU = NU;
+  const int pm = a.pm;
+  *smem = pm == 1   ? RowSmem<T, L, 1>::bytes(sbase, a.nb, bins ? nhist * a.nb : 0)
+          : pm == 2 ? RowSmem<T, L, 2>::bytes(sbase, a.nb, bins ? a.nb : 0)
+                    : RowSmem<T, L, 3>::bytes(sbase, a.nb, bins ? a.nb : 0);
+  return *smem <= 200 * 1024 ? NRE_OK : NRE_EINVAL;
+}
+
+template <typename T, int L>
+int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_t st, int64_t N) {
+  constexpr int NT = ColShape<L>::NT;
+  const int gx = persistent_gx(a.n_units, B);
+  *nparts = gx;
+  const size_t smem = ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0);
+  if (smem > 200 * 1024) return set_error(NRE_EINVAL, "column sweep of length %d needs %zu bytes of shared memory", L, smem);
+  const dim3 grid((unsigned)gx, B);
+  const char* name = sizeof(T) == 8 ? (mid ? "col_sweep_f64_metric" : "col_sweep_f64")
+                                    : (mid ? "col_sweep_f32_metric" : "col_sweep_f32");
+  const bool buf = a.pro.mode == PRO_BUF && a.epi.mode == EPI_BUF;
+  if (mid && !buf) return set_error(NRE_EINVAL, "internal: the metric's column sweep reads and writes plain buffers");
+  prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, mid, B, N), st);
+  if (mid) {
+    NRE_TRY(set_smem(k_col_reg<T, L, true, SK_BUF, SK_BUF>, smem));
+    k_col_reg<T, L, true, SK_BUF, SK_BUF><<<grid, NT, smem, st>>>(a);
+  } else if (buf) {
+    NRE_TRY(set_smem(k_col_reg<T, L, false, SK_BUF, SK_BUF>, smem));
+    k_col_reg<T, L, false, SK_BUF, SK_BUF><<<grid, NT, smem, st>>>(a);
+  } else {
+    NRE_TRY(set_smem(k_col_reg<T, L, false, SK_GEN, SK_GEN>, smem));
+    k_col_reg<T, L, false, SK_GEN, SK_GEN><<<grid, NT, smem, st>>>(a);
+  }
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template int row_reg_plan<NRE_SWEEP_T, NRE_SWEEP_L>(RowArgs<NRE_SWEEP_T>&, int, bool, dim3*, size_t*, int*);
+template int row_reg_L<NRE_SWEEP_T, NRE_SWEEP_L>(RowArgs<NRE_SWEEP_T>, bool, dim3, size_t, cudaStream_t, int64_t);
+template int col_reg_L<NRE_SWEEP_T, NRE_SWEEP_L>(ColArgs<NRE_SWEEP_T>, bool, int, bool, int*, cudaStream_t, int64_t);
+
+}  // namespace nre
+
+#endif

@@ -1,0 +1,499 @@
+// Register-resident, pipelined Hartley sweeps (line lengths 8..4096).
+//
+// Row sweep: a unit is a reflection orbit of rows (D = 2: {i, -i}; D = 3:
+// {(+-i0, +-i1)}) or, for D = 1, a pair of samples.  Two real rows form one
+// complex line held by L/8 threads; each thread takes its 8 elements of both
+// rows into the first radix-8 butterfly, runs the transform in registers,
+// fetches the mirror elements X[-x] through shared memory, and applies the
+// Hartley unpack, the reflection combination P (D >= 2; for D = 3 a thread owns
+// both lines of its unit) and the epilogue in registers.  For D = 1 the
+// metric's t = w * y and the second transform follow directly.
+//
+// Column sweep: a unit is a tile of W adjacent grid columns (all L rows of one
+// outer index); columns 2p and 2p+1 form complex line p.  The tile is staged
+// into shared memory row by row, each line is transformed by L/8 consecutive
+// threads, and the results go back through a shared output tile so that global
+// stores cover whole 32-byte sectors.  The axis-0 sweep of the 2-D / 3-D
+// metric runs y = H_0 u, t = w * y and H_0 t back to back in registers, with
+// the w tile staged beside the input tile.
+//
+// Both kernels are persistent over their units: while a CTA transforms one
+// group, the inputs of its next group stream into the other half of a double
+// buffer with 16-byte cp.async copies, so HBM reads overlap the arithmetic.
+// The threads of one line synchronise with warp or named barriers only.
+// Per-bin amplitude tables (A and the tangent's dA) of the CTA's sample sit in
+// shared memory; only the int16 bin index is read per pixel.  Log-|k| bin sums
+// of the epilogue are reduced over runs of equal bins within each warp before
+// one shared-memory atomic per run.
+#pragma once
+
+#include "cf_internal.cuh"
+#include "regfft.cuh"
+
+namespace nre {
+
+template <int L>
+struct RowShape {
+  static constexpr int T8 = L / 8;
+  static constexpr int NT = T8 > 256 ? T8 : 256;
+  static constexpr int NU = NT / T8;  // units per CTA iteration
+};
+
+template <int L>
+struct ColShape {
+  static constexpr int T8 = L / 8;
+  static constexpr int NT = T8 > 256 ? T8 : 256;
+  static constexpr int NL = NT / T8;            // complex lines per tile
+  static constexpr int W = 2 * NL;              // grid columns per tile
+  static constexpr int WP = W + 4;              // padded tile row (16-byte multiple)
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* tw, const C* gtw, int L, int shift) {
+  for (int m = threadIdx.x; m < L; m += blockDim.x) tw[m] = gtw[m << shift];
+}
+
+// Barrier of the T8 threads of line `u` (consecutive threads).
+template <int T8>
+struct LineSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (T8 <= 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(T8) : "memory");
+    }
+  }
+};
+
+// Adds the contributions c[s] of slots with bins bn[s] (all into the same
+// histogram): slots sharing a bin are summed first, then each distinct bin is
+// reduced over the warp.  Must be called by all lanes of the warp.
+template <int S, typename V>
+__device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], double* hist) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    int key = bn[s];
+    V val = c[s];
+#pragma unroll
+    for (int s2 = 0; s2 < s; ++s2)
+      if (bn[s2] == bn[s]) key = -1;
+#pragma unroll
+    for (int s2 = s + 1; s2 < S; ++s2)
+      if (bn[s2] == bn[s]) val += c[s2];
+    if (s == 0 || __any_sync(0xffffffffu, key >= 0)) warp_run_add(key, val, hist);
+  }
+}
+
+// Per-bin tables of one sample in shared memory: A (from the per-bin model
+// amplitude) into sA and the tangent's dA into sdA.  Returns whether the
+// prologue / epilogue should read them (*use_dA: the dA table).  Called by all
+// threads; a barrier must follow before use.
+template <typename T>
+__device__ __forceinline__ bool load_tables(const Pro<T>& pro, const Epi<T>& epi, int b, T* sA, T* sdA, int nb,
+                                            bool* use_dA) {
+  const AmpView<T>& v = pro.mode == PRO_AMP ? pro.av : epi.av;
+  *use_dA = false;
+  if (v.abin == nullptr || (v.mode != AMPV_MODEL && v.mode != AMPV_PIX)) return false;
+  if (!(pro.mode == PRO_AMP || epi.mode == EPI_AMP)) return false;
+  const bool dA = pro.mode == PRO_AMP && pro.dA != nullptr;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    sA[i] = T(v.abin[b * v.astride + i]);
+    if (dA) sdA[i] = T(pro.dA[b * pro.nb + i]);
+  }
+  *use_dA = dA;
+  return true;
+}
+
+// Shared-memory plan of the row kernel (element counts in T).
+template <typename T, int L, int PM>
+struct RowSmem {
+  static constexpr int LPU = (PM == 3) ? 2 : 1;
+  static constexpr int SLOTS = 2 * LPU;
+  static constexpr int NU = RowShape<L>::NU;
+  static constexpr int XSZ = NU * SLOTS * L;              // staged input rows
+  static constexpr int LNSZ = NU * LPU * rline(L) * 2;    // exchange lines (complex)
+  static constexpr int STG = (XSZ > LNSZ ? XSZ : LNSZ);
+  static constexpr int STGA = (STG + 3) / 4 * 4;          // 16-byte multiple
+  static size_t bytes(bool base, int nb, int nhist_bins) {
+    return (size_t)2 * L * sizeof(T) + (size_t)2 * STGA * sizeof(T) + (base ? (size_t)2 * XSZ * sizeof(T) : 0) +
+           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
+  }
+};
+
+// Prologue / epilogue specialisations (compile time): GEN = the runtime
+// functor of the arguments, BUF = plain copy, TAB = the metric's amplitude with
+// per-pixel int16 bins and per-bin tables in shared memory.
+enum { SK_GEN = 0, SK_BUF = 1, SK_TAB = 2 };
+
+template <typename T, int L, int PM, bool MID, int PK, int EK>
+__global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM == 3 ? 2 : 3) : 1))
+    k_row_reg(RowArgs<T> a) {
+  typedef typename CplxT<T>::type C;
+  typedef RowSmem<T, L, PM> SM;
+  constexpr int T8 = L / 8, NU = SM::NU, LPU = SM::LPU, SLOTS = SM::SLOTS, LS = rline(L);
+  constexpr int CH = 16 / sizeof(T), CPR = L / CH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  T* stage = reinterpret_cast<T*>(tw + L);                  // [2][STGA]
+  const bool sbase = a.epi.mode == EPI_AMP && a.epi.base != nullptr;
+  T* bstage = stage + 2 * SM::STGA;                          // [2][XSZ] when staged
+  const int nbp = (a.nb + 3) / 4 * 4;
+  T* sA = bstage + (sbase ? 2 * SM::XSZ : 0);
+  T* sdA = sA + nbp;
+  double* hist = reinterpret_cast<double*>(sdA + nbp);
+  const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  const int nhist = (PM == 1) ? 2 * NU : 1;
+  const int bsample = (PM == 1) ? 0 : blockIdx.y;
+  const Pro<T>& pro = a.pro;
+  const Epi<T>& epi = a.epi;
+  load_twiddles(tw, a.tw, L, a.log2Lmax - a.log2L);
+  bool use_dA = false;
+  const bool use_tab = (PM != 1) && load_tables<T>(pro, epi, bsample, sA, sdA, a.nb, &use_dA);
+  const T* stab = use_tab ? sA : nullptr;
+  const T* stdA = use_dA ? sdA : nullptr;
+  if (bins)
+    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = 0.0;
+  const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
+  const LineSync<T8> sync{1 + u};
+
+  // slot sl of unit `unit`: sample and row, or false if absent
+  auto slot_of = [&](int unit, int sl, int& samp, int& row) -> bool {
+    samp = 0;
+    row = 0;
+    if (unit >= a.n_units) return false;
+    if (PM == 1) {
+      samp = 2 * unit + sl;
+      return samp < a.B;
+    }
+    samp = bsample;
+    row = a.grows[unit * SLOTS + sl];
+    return true;
+  };
+  auto issue = [&](int ug, int buf) {
+    T* dst = stage + buf * SM::STGA;
+    T* bdst = bstage + buf * SM::XSZ;
+    for (int c = threadIdx.x; c < NU * SLOTS * CPR; c += blockDim.x) {
+      const int rr = c / CPR, j = c - rr * CPR;
+      const int uu = rr / SLOTS, sl = rr - uu * SLOTS;
+      int samp, row;
+      if (!slot_of(ug + uu, sl, samp, row)) continue;
+      const int64_t g = (int64_t)row * L + j * CH;
+      cp_async16(dst + rr * L + j * CH, a.pro.x + samp * a.pro.xs + g);
+      if (sbase) cp_async16(bdst + rr * L + j * CH, a.epi.base + samp * a.epi.bs + g);
+    }
+  };
+
+  const int ustride = gridDim.x * NU;
+  int u0 = blockIdx.x * NU;
+  if (u0 < a.n_units) issue(u0, 0);
+  cp_commit();
+  for (int it = 0; u0 < a.n_units; u0 += ustride, ++it) {
+    const int cur = it & 1;
+    if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    const int unit = u0 + u;
+    int row[SLOTS], samp[SLOTS];
+    bool sval[SLOTS];
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) sval[sl] = slot_of(unit, sl, samp[sl], row[sl]);
+    const bool valid = sval[0];
+    const T* X = stage + cur * SM::STGA + u * SLOTS * L;
+    C v[LPU][8];
+    if constexpr (PK == SK_GEN) {
+#pragma unroll
+      for (int q = 0; q < LPU; ++q)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int x = t + T8 * s;
+          const T re =
+              sval[2 * q] ? pro.apply(samp[2 * q], (int64_t)row[2 * q] * L + x, X[(2 * q) * L + x], stab, stdA) : T(0);
+          const T im = sval[2 * q + 1] ? pro.apply(samp[2 * q + 1], (int64_t)row[2 * q + 1] * L + x,
+                                                   X[(2 * q + 1) * L + x], stab, stdA)
+                                       : T(0);
+          v[q][s] = cmake<C>(re, im);
+        }
+    } else if constexpr (PK == SK_BUF) {
+#pragma unroll
+      for (int q = 0; q < LPU; ++q)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int x = t + T8 * s;
+          v[q][s] = cmake<C>(sval[2 * q] ? X[(2 * q) * L + x] : T(0), sval[2 * q + 1] ? X[(2 * q + 1) * L + x] : T(0));
+        }
+    } else {
+      // u = A[bin] v + dA[bin] xi_p (bins per pixel, tables in shared memory)
+      const int16_t* bp = pro.av.bpix;
+      const T* xp = pro.xi_p + (int64_t)bsample * pro.ps;
+      const T a0 = pro.av.a0t;
+#pragma unroll
+      for (int q = 0; q < LPU; ++q)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int x = t + T8 * s;
+          T e[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int f = row[2 * q + h] * L + x;
+            const int bn = __ldg(&bp[f]);
+            T val = (bn < 0 ? a0 : sA[bn]) * X[(2 * q + h) * L + x];
+            if (stdA != nullptr && bn >= 0) val += sdA[bn] * __ldg(&xp[f]);
+            e[h] = sval[2 * q + h] ? val : T(0);
+          }
+          v[q][s] = cmake<C>(e[0], e[1]);
+        }
+    }
+    __syncthreads();  // the stage half becomes the exchange buffer
+    C* sm[LPU];
+#pragma unroll
+    for (int q = 0; q < LPU; ++q) sm[q] = reinterpret_cast<C*>(stage + cur * SM::STGA) + (u * LPU + q) * LS;
+    C* const* smc = sm;
+    reg_fft<C, L, LPU>(v, smc, tw, t, sync);
+    C zm[LPU][8];
+    if constexpr (MID) {
+      reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int x = t + T8 * s;
+        T ha[2], hb[2];
+        hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+        const T w = a.mid.w[x];
+        v[0][s] = cmake<C>(w * ha[0], w * hb[0]);
+      }
+      reg_fft<C, L, LPU>(v, smc, tw, t, sync);
+    }
+    reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
+    const T* BV = bstage + cur * SM::XSZ + u * SLOTS * L;
+    // output of slot value `val` at row `rw`, column x of sample `sp`
+    auto put = [&](int sp, int rw, int x, T val, T bval, int& bn, T& c) {
+      if constexpr (EK == SK_BUF) {
+        epi.y[(int64_t)sp * epi.ys + rw * L + x] = val;
+        bn = -1;
+        c = T(0);
+      } else if constexpr (EK == SK_TAB) {
+        const int f = rw * L + x;
+        bn = __ldg(&epi.av.bpix[f]);
+        epi.y[(int64_t)sp * epi.ys + f] = (bn < 0 ? epi.av.a0t : sA[bn]) * val + bval;
+        c = (bins && bn >= 0) ? __ldg(&epi.xi_p[(int64_t)sp * epi.ps + f]) * val : T(0);
+        if (!bins) bn = -1;
+      } else {
+        epi.store_b(sp, (int64_t)rw * L + x, val, bval, bn, c, stab);
+      }
+    };
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int x = t + T8 * s;
+      if (PM == 1) {
+        T ha[2], hb[2];
+        hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+        int bn[2] = {-1, -1};
+        T c[2] = {T(0), T(0)};
+        if (sval[0]) put(samp[0], 0, x, ha[0], sbase ? BV[x] : T(0), bn[0], c[0]);
+        if (sval[1]) put(samp[1], 0, x, hb[0], sbase ? BV[L + x] : T(0), bn[1], c[1]);
+        if (bins) {
+          warp_run_add(bn[0] >= 0 ? (2 * u) * a.nb + bn[0] : -1, c[0], hist);
+          if (__any_sync(0xffffffffu, bn[1] >= 0))
+            warp_run_add(bn[1] >= 0 ? (2 * u + 1) * a.nb + bn[1] : -1, c[1], hist);
+        }
+      } else if (PM == 2) {
+        T R[2][2];
+        hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+        const bool f0 = valid && (a.gflags[unit] & 1);
+        const T half = T(0.5);
+        int bn[2] = {-1, -1};
+        T c[2] = {T(0), T(0)};
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          const int s0 = f0 ? 1 - sl : sl;
+          const T val = half * (R[sl][0] + R[s0][0] + R[sl][1] - R[s0][1]);
+          if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
+        }
+        if (bins) add_slots<2, T>(bn, c, hist);
+      } else {
+        T R[4][2];
+        hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+        hartley_unpack<T>(v[1][s], zm[1][s], R[2], R[3]);
+        const int fl = valid ? a.gflags[unit] : 0;
+        const bool f0 = fl & 1, f1 = fl & 2;
+        const T half = T(0.5);
+        int bn[4] = {-1, -1, -1, -1};
+        T c[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+          const int s0 = f0 ? (sl ^ 1) : sl;
+          const int s1 = f1 ? (sl ^ 2) : sl;
+          const int s01 = f1 ? (s0 ^ 2) : s0;
+          const T val = half * (R[s0][0] + R[s1][0] + R[sl][1] - R[s01][1]);
+          if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
+        }
+        if (bins) add_slots<4, T>(bn, c, hist);
+      }
+    }
+    __syncthreads();  // this half is refilled two iterations later
+  }
+  cp_wait<0>();
+  if (bins) {
+    __syncthreads();
+    if (PM == 1) {
+      for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
+        const int hs = i / a.nb, bn = i - hs * a.nb;
+        const int sample = 2 * (blockIdx.x * NU) + hs;
+        if (sample < a.B) a.partials[(int64_t)sample * a.nb + bn] = hist[i];
+      }
+    } else {
+      double* dst = a.partials + ((int64_t)bsample * gridDim.x + blockIdx.x) * a.nb;
+      for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+    }
+  }
+}
+
+// Shared-memory plan of the column kernel (element counts in T).
+template <typename T, int L>
+struct ColSmem {
+  static constexpr int XS = L * ColShape<L>::WP;                     // one staged tile
+  static constexpr int LNSZ = ColShape<L>::NL * rline(L) * 2;       // exchange lines
+  static size_t bytes(int nb, int nhist_bins) {
+    return (size_t)2 * L * sizeof(T) + (size_t)2 * XS * sizeof(T) + (size_t)LNSZ * sizeof(T) +
+           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
+  }
+};
+
+template <typename T, int L, bool MID, int PK, int EK>
+__global__ void __launch_bounds__(ColShape<L>::NT, (ColShape<L>::NT <= 256 ? 3 : 1)) k_col_reg(ColArgs<T> a) {
+  typedef typename CplxT<T>::type C;
+  typedef ColSmem<T, L> SM;
+  constexpr int T8 = L / 8, NL = ColShape<L>::NL, WP = ColShape<L>::WP;
+  constexpr int LS = rline(L), CH = 16 / sizeof(T);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  T* xin = reinterpret_cast<T*>(tw + L);      // [2][XS]; the current half is also the output tile
+  C* lines = reinterpret_cast<C*>(xin + 2 * SM::XS);
+  const int nbp = (a.nb + 3) / 4 * 4;
+  T* sA = reinterpret_cast<T*>(lines + NL * LS);
+  T* sdA = sA + nbp;
+  double* hist = reinterpret_cast<double*>(sdA + nbp);
+  const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  const int b = blockIdx.y;
+  const Pro<T>& pro = a.pro;
+  const Epi<T>& epi = a.epi;
+  load_twiddles(tw, a.tw, L, a.log2Lmax - a.log2L);
+  bool use_dA = false;
+  const bool use_tab = load_tables<T>(pro, epi, b, sA, sdA, a.nb, &use_dA);
+  const T* stab = use_tab ? sA : nullptr;
+  const T* stdA = use_dA ? sdA : nullptr;
+  if (bins)
+    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = 0.0;
+  const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
+  const LineSync<T8> sync{1 + u};
+  const int W = a.W, CPR = W / CH;
+  const bool lval = 2 * u < W;
+
+  auto tile_base = [&](int64_t unit) -> int64_t {
+    const int64_t o = unit / a.nblk;
+    return o * L * a.inner + (unit - o * a.nblk) * W;
+  };
+  auto issue = [&](int64_t unit, int buf) {
+    const T* src = a.pro.x + b * a.pro.xs + tile_base(unit);
+    T* dst = xin + buf * SM::XS;
+    for (int c = threadIdx.x; c < L * CPR; c += blockDim.x) {
+      const int l = c / CPR, j = c - l * CPR;
+      cp_async16(dst + l * WP + j * CH, src + (int64_t)l * a.inner + j * CH);
+    }
+  };
+
+  int64_t unit = blockIdx.x;
+  if (unit < a.n_units) issue(unit, 0);
+  cp_commit();
+  for (int it = 0; unit < a.n_units; unit += gridDim.x, ++it) {
+    const int cur = it & 1;
+    if (unit + gridDim.x < a.n_units) issue(unit + gridDim.x, cur ^ 1);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    const int64_t base = tile_base(unit);
+    T* X = xin + cur * SM::XS;
+    C v[1][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int l = t + T8 * s;
+      if (lval) {
+        const C raw = *reinterpret_cast<const C*>(X + l * WP + 2 * u);
+        if constexpr (PK == SK_BUF) {
+          v[0][s] = raw;
+        } else {
+          const int64_t flat = base + (int64_t)l * a.inner + 2 * u;
+          v[0][s] = cmake<C>(pro.apply(b, flat, raw.x, stab, stdA), pro.apply(b, flat + 1, raw.y, stab, stdA));
+        }
+      } else {
+        v[0][s] = cmake<C>(T(0), T(0));
+      }
+    }
+    C* sm[1] = {lines + u * LS};
+    C* const* smc = sm;
+    reg_fft<C, L, 1>(v, smc, tw, t, sync);
+    C zm[1][8];
+    if constexpr (MID) {
+      reg_mirror<C, L, 1>(v, zm, smc, t, sync);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        T ha[2], hb[2];
+        hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+        const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
+        v[0][s] = lval ? a.mid.apply2(flat, ha[0], hb[0]) : cmake<C>(T(0), T(0));
+      }
+      reg_fft<C, L, 1>(v, smc, tw, t, sync);
+    }
+    reg_mirror<C, L, 1>(v, zm, smc, t, sync);
+    __syncthreads();  // every line has read the input tile: reuse it for the output
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      T ha[2], hb[2];
+      hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+      if (lval) *reinterpret_cast<C*>(X + (t + T8 * s) * WP + 2 * u) = cmake<C>(ha[0], hb[0]);
+    }
+    __syncthreads();
+    // write the tile back row by row (CH consecutive columns per thread); the
+    // loop is uniform over the block so the warp reductions see full warps
+    for (int c0 = 0; c0 < L * CPR; c0 += blockDim.x) {
+      const int c = c0 + threadIdx.x;
+      const bool act = c < L * CPR;
+      const int l = act ? c / CPR : 0, j = act ? c - l * CPR : 0;
+      const int64_t flat = base + (int64_t)l * a.inner + j * CH;
+      const T* src = X + l * WP + j * CH;
+      if constexpr (EK == SK_BUF) {
+        if (act) *reinterpret_cast<uint4*>(epi.y + b * epi.ys + flat) = *reinterpret_cast<const uint4*>(src);
+      } else {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+          int bn = -1;
+          T cc = T(0);
+          if (act)
+            epi.store_b(b, flat + e, src[e],
+                        (epi.mode == EPI_AMP && epi.base) ? epi.base[b * epi.bs + flat + e] : T(0), bn, cc, stab);
+          if (bins) warp_run_add(bn, cc, hist);
+        }
+      }
+    }
+    __syncthreads();  // tiles of this half are refilled two iterations later
+  }
+  cp_wait<0>();
+  if (bins) {
+    __syncthreads();
+    double* dst = a.partials + ((int64_t)b * gridDim.x + blockIdx.x) * a.nb;
+    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+  }
+}
+
+}  // namespace nre
