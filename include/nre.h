@@ -122,6 +122,23 @@ int cf_jvp(nre_cf_plan *plan, const void *xi_p, const void *v, void *jv,
 int cf_vjp(nre_cf_plan *plan, const void *xi_p, const void *ct, void *g,
            int batch, nre_stream_t stream);
 
+/* cf_forward without any device allocation (the paper has no counterpart: this
+ * is an interface for callers that cannot allocate).  cf_forward may grow the
+ * plan's workspaces with cudaMalloc, which can synchronise the device and take
+ * unpredictable time, and some host runtimes hand out device memory only
+ * through their own pool; this variant instead keeps the transform's
+ * intermediates (and the amplitude-model state) in one fixed 16 MiB device
+ * array that every GPU loading the library holds until the process exits.
+ * Same arguments and results as cf_forward.  Returns NRE_EINVAL, before any
+ * work is enqueued, if `batch` needs more than 16 MiB of intermediates (about
+ * batch * N * sizeof(dtype) per intermediate: one for 2-D grids, two for 3-D).
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, or
+ * unordered host threads) race on it. */
+int cf_forward_noalloc(nre_cf_plan *plan, const void *xi, void *s, int batch,
+                       nre_stream_t stream);
+
 /* Host-only helper (no GPU needed): log-|k| bin of every harmonic pixel as the
  * POWER_MODEL uses it (-1 at k = 0), C order, into host array out[N]. */
 int cf_bin_map(int ndim, const int64_t *shape, const double *spacing,

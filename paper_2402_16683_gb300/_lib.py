@@ -60,6 +60,7 @@ SIGNATURES = {
     "cf_forward": [_P, _P, _P, C.c_int, _P],
     "cf_jvp": [_P, _P, _P, _P, C.c_int, _P],
     "cf_vjp": [_P, _P, _P, _P, C.c_int, _P],
+    "cf_forward_noalloc": [_P, _P, _P, C.c_int, _P],
     "cf_bin_map": [C.c_int, _I64P, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int32)],
     "icr_create": [C.POINTER(_P), C.POINTER(ICRChartParams), C.POINTER(ICRKernelParams), C.c_int, C.c_int],
     "icr_destroy": [_P],
