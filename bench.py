@@ -44,12 +44,21 @@ WORKLOAD = "cf2d_512x512_power_poisson_mgvi_cg100"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-metric-grids", action="store_true",
+                    help="skip the metric-product roofline leg on 2-D 1024^2 and 3-D 256^3")
+    ap.add_argument("--metric-batch", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests of the serving stream (0: skip the serving leg)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-plain-cap-s", type=float, default=120.0,
+                    help="stop the sequential FP64 arm after this many seconds")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     return ap.parse_args()
 
 
@@ -84,7 +93,7 @@ class Clocks:
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -187,6 +196,10 @@ def run_ours(args, rank, world):
     import paper_2402_16683_gb300 as nre
     from paper_2402_16683_gb300 import _lib
 
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serve": run_serve(args)}), flush=True)
+        return
     lib = _lib.load()
     lib.nre_launch_count.restype = C.c_ulonglong
     lib.nre_launch_count.argtypes = []
@@ -222,25 +235,31 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def timed(n):
+        ev = []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = step()
+            e1.record(stream)
+            ev.append((e0, e1))
+        barrier()
+        return sum(a.elapsed_time(b_) for a, b_ in ev), its
+
     clocks = Clocks(torch.cuda.current_device())
     barrier()
     clocks.start()
-    lib.nre_prof_enable(1)
     n0 = lib.nre_launch_count()
-    ev = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        its = step()
-        e1.record(stream)
-        ev.append((e0, e1))
-    barrier()
+    ms, its = timed(args.steps)
     launches = lib.nre_launch_count() - n0
-    lib.nre_prof_enable(0)
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    # per-kernel device times from a separate traced pass (the events that
+    # bracket every launch are kept out of the timed steps above)
+    lib.nre_prof_enable(1)
+    timed(max(1, min(args.steps, 5)))
+    lib.nre_prof_enable(0)
     buf = C.create_string_buffer(1 << 16)
     _lib.check(lib.nre_prof_report(buf, len(buf)))
     kern = json.loads(buf.value.decode())
@@ -268,6 +287,12 @@ def run_ours(args, rank, world):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier)
+    grids = None
+    if not args.no_metric_grids:
+        grids = run_metric_grids(args, lib)
+    serve = None
+    if args.serve_requests > 0 and world == 1:
+        serve = run_serve(args)
     if rank != 0:
         return
     cb = None
@@ -279,6 +304,10 @@ def run_ours(args, rank, world):
            "config": config(B), "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
            "cg_iterations": its[:1]}
+    if grids is not None:
+        out["metric_grids"] = grids
+    if serve is not None:
+        out["serve"] = serve
     print(json.dumps(out), flush=True)
 
 
@@ -326,6 +355,246 @@ def run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier):
     return {"value": world * e_steps * B * CG_ITERS / e_t, "unit": UNIT,
             "h2d_bytes_per_step": int(h_xi.numel() * 4 + h_eta.numel() * 4),
             "d2h_bytes_per_step": int(h_x.numel() * 4)}
+
+
+# ----------------------------------------------------------------- metric roofline leg
+METRIC_GRIDS = [((1024, 1024), "poisson"), ((256, 256, 256), "gauss_mask10")]
+
+
+def run_metric_grids(args, lib):
+    """Metric-vector products alone (no CG) at B=8 on the 2-D 1024^2 Poisson
+    and the 3-D 256^3 Gaussian (sigma 0.05, 10% mask) fields: products/s and
+    the HBM roofline of the whole product (algorithmic bytes of all its
+    kernels over their device time) and of each kernel."""
+    import ctypes as C
+
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+    from paper_2402_16683_gb300 import _lib
+
+    peak, _ = peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    B = args.metric_batch
+    out = {}
+    for shape, kind in METRIC_GRIDS:
+        plan = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float32)
+        if kind == "poisson":
+            lik = nre.Likelihood("poisson", scale=10.0)
+        else:
+            lik = nre.Likelihood("gauss", sigma=0.05, mask=synth.mask_fraction(synth.SEED_MASK, plan.n_field),
+                                 n_data=plan.n_field)
+        xi_p = torch.tensor(synth.normal(synth.SEED_POS, plan.latent_size), dtype=torch.float32, device=dev)
+        M = nre.Metric(plan, lik, plan.pad(xi_p[None])[0], max_batch=B)
+        g = np.random.default_rng(synth.SEED_TANGENT)
+        v = plan.pad(torch.tensor(g.standard_normal((B, plan.latent_size)), dtype=torch.float32, device=dev))
+        o = torch.empty_like(v)
+        for _ in range(3):
+            M.apply(v, out=o)
+        torch.cuda.synchronize()
+
+        def timed(n):
+            ev = []
+            for _ in range(n):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                M.apply(v, out=o)
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            return sum(a.elapsed_time(b_) for a, b_ in ev) / n
+
+        n = max(5, args.steps)
+        ms = timed(n)
+        lib.nre_prof_enable(1)
+        timed(n)
+        lib.nre_prof_enable(0)
+        buf = C.create_string_buffer(1 << 16)
+        _lib.check(lib.nre_prof_report(buf, len(buf)))
+        kern = json.loads(buf.value.decode())
+        kms = sum(x[1] for x in kern.values())
+        kbytes = sum(x[2] for x in kern.values())
+        name = "x".join(str(d) for d in shape)
+        out[f"{len(shape)}d_{name}"] = {
+            "likelihood": kind, "batch": B, "products_per_s": B / (ms / 1e3), "ms_per_apply": ms,
+            "bytes_per_apply": kbytes / n, "achieved_GBps": kbytes / (kms / 1e3) / 1e9,
+            "frac": kbytes / (kms / 1e3) / 1e9 / peak,
+            "kernels": {k: {"us_per_launch": 1e3 * x[1] / x[0], "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None,
+                            "frac": (x[2] / (x[1] / 1e3) / 1e9 / peak) if x[1] else None}
+                        for k, x in kern.items()}}
+        del M, v, o
+        torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------- serving leg
+SERVE_SAMPLES = 8
+SERVE_RTOL = 1e-5
+SERVE_MAXITER = 2000
+# Gaussian requests observe the field itself (sigma 0.1, every pixel); Poisson
+# requests count at rate 10 exp(cf)
+SERVE_RESPONSE = {"gauss": "identity", "poisson": "exp"}
+
+
+def _pctl(v, q):
+    return float(np.percentile(np.asarray(v), q)) if v else None
+
+
+def run_serve(args):
+    """The request stream (Poisson arrivals at 50/s, grids drawn uniformly from
+    1-D 4096, 2-D 256^2, 2-D 1024^2, 3-D 128^3, Gaussian (sigma 0.1 on cf,
+    every pixel) / Poisson (rate 10 exp(cf)) 50/50, 8 sample systems per
+    request to 1e-5 relative residual) through
+
+    * the FP32 server: continuous batching, one stream per admitted request,
+      CG chunks replayed as CUDA graphs, admission by HBM footprint;
+    * the plain sequential FP64 path: requests first in first out, one
+      system at a time (batch 1), through Metric / cg, nothing overlapped.
+
+    Both use the harmonic preconditioner and the same inputs (a pool of two
+    input sets per grid, reused round-robin; expansion points with N(0, 1)
+    field and offset excitations and the power-spectrum excitations at the
+    prior median).  Latency = result in host memory
+    minus arrival.  One request per grid is served first, untimed, so that plans
+    (and the server's slot objects) exist before the stream starts."""
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+
+    reqs = synth.request_stream(synth.SEED_STREAM, n=args.serve_requests, rate=50.0)
+    pool = 2
+    inputs = {}
+    for si, shape in enumerate(synth.SERVE_SHAPES):
+        N = int(np.prod(shape))
+        lat = N + 4 + 2 * 255
+        sets = []
+        for k in range(pool):
+            g = np.random.default_rng(9000 + 10 * si + k)
+            xv = g.standard_normal(lat)
+            xv[N:] = 0.0  # power-spectrum excitations at the prior median
+            xi = torch.tensor(xv, dtype=torch.float32).pin_memory()
+            b = torch.tensor(g.standard_normal((SERVE_SAMPLES, lat)), dtype=torch.float32).pin_memory()
+            sets.append((xi, b))
+        inputs[shape] = sets
+    free = {shape: [] for shape in synth.SERVE_SHAPES}
+    lock = threading.Lock()
+
+    def take_out(shape):
+        with lock:
+            if free[shape]:
+                return free[shape].pop()
+        return torch.empty_like(inputs[shape][0][1]).pin_memory()
+
+    # ---- FP32 server
+    srv = nre.Server(max_slots=args.serve_slots, dtype=torch.float32, chunk_iters=8, use_graphs=True)
+    for shape in synth.SERVE_SHAPES:
+        for lik in ("gauss", "poisson"):
+            xi, b = inputs[shape][0]
+            out = take_out(shape)
+            r = srv.poll(srv.submit(shape, xi, b, out, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
+                                    response=SERVE_RESPONSE[lik]), -1)
+            free[shape].append(out)
+    results = [None] * len(reqs)
+    ids = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def poller():
+        for i in range(len(reqs)):
+            ready.acquire()
+            r = srv.poll(ids[i][0], -1)
+            results[i] = r
+            with lock:
+                free[reqs[i][1]].append(ids[i][1])
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.monotonic()
+    for i, (ta, shape, lik) in enumerate(reqs):
+        dt = t0 + ta - time.monotonic()
+        if dt > 0:
+            time.sleep(dt)
+        xi, b = inputs[shape][i % pool]
+        out = take_out(shape)
+        ids[i] = (srv.submit(shape, xi, b, out, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
+                             response=SERVE_RESPONSE[lik]), out)
+        ready.release()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat32 = [1e3 * (r["t_done"] - (t0 + reqs[i][0])) for i, r in enumerate(results)]
+    ok32 = sum(1 for r in results if r["status"] == 0)
+    end32 = max(r["t_done"] for r in results)
+    its32 = [max(r["iters"][:SERVE_SAMPLES]) for r in results]
+    fp32 = {"p50_ms": _pctl(lat32, 50), "p99_ms": _pctl(lat32, 99), "mean_ms": float(np.mean(lat32)),
+            "solves_per_s": SERVE_SAMPLES * len(reqs) / (end32 - t0), "converged": ok32,
+            "mean_iters": float(np.mean(its32)), "max_relres": max(max(r["relres"][:SERVE_SAMPLES]) for r in results),
+            "slots": args.serve_slots, "graph_replays": st["graph_replays"], "chunks": st["chunks"],
+            "slot_objects_created": st["created"], "reused": st["reused"],
+            "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9}
+
+    # ---- plain sequential FP64 path
+    plans = {shape: nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR),
+                                        dtype=torch.float64) for shape in synth.SERVE_SHAPES}
+    liks = {"gauss": nre.Likelihood("gauss", sigma=0.1, response=SERVE_RESPONSE["gauss"]),
+            "poisson": nre.Likelihood("poisson", scale=10.0)}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    inp64 = {shape: [(xi.double().pin_memory(), b.double().pin_memory()) for (xi, b) in sets]
+             for shape, sets in inputs.items()}
+
+    def plain(shape, lik, k):
+        plan = plans[shape]
+        xi, b = inp64[shape][k]
+        xp = torch.zeros(plan.stride, dtype=torch.float64, device=dev)
+        xp[:plan.latent_size].copy_(xi, non_blocking=True)
+        M = nre.Metric(plan, liks[lik], xp, max_batch=1)
+        M.set_precond("harmonic")
+        bd = torch.zeros(1, plan.stride, dtype=torch.float64, device=dev)
+        xd = torch.zeros_like(bd)
+        out = torch.empty_like(b).pin_memory()
+        its, rels, sts = [], [], []
+        for s_ in range(SERVE_SAMPLES):
+            bd[0, :plan.latent_size].copy_(b[s_], non_blocking=True)
+            _, it, rel, st_ = M.cg(bd, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER, x=xd)
+            out[s_].copy_(xd[0, :plan.latent_size])
+            its.append(it[0])
+            rels.append(rel[0])
+            sts.append(st_)
+        torch.cuda.synchronize()
+        return max(its), max(rels), all(v == 0 for v in sts)
+
+    for shape in synth.SERVE_SHAPES:
+        plain(shape, "gauss", 0)
+    lat64, its64, ok64, rel64 = [], [], 0, 0.0
+    t0 = time.monotonic()
+    truncated = False
+    for i, (ta, shape, lik) in enumerate(reqs):
+        dt = t0 + ta - time.monotonic()
+        if dt > 0:
+            time.sleep(dt)
+        it, rel, ok = plain(shape, lik, i % pool)
+        lat64.append(1e3 * (time.monotonic() - (t0 + ta)))
+        its64.append(it)
+        rel64 = max(rel64, rel)
+        ok64 += int(ok)
+        if time.monotonic() - t0 > args.serve_plain_cap_s:
+            truncated = i + 1 < len(reqs)
+            break
+    end64 = time.monotonic()
+    n64 = len(lat64)
+    fp64 = {"p50_ms": _pctl(lat64, 50), "p99_ms": _pctl(lat64, 99), "mean_ms": float(np.mean(lat64)),
+            "solves_per_s": SERVE_SAMPLES * n64 / (end64 - t0), "converged": ok64, "requests_served": n64,
+            "mean_iters": float(np.mean(its64)), "max_relres": rel64,
+            "truncated_at_s": args.serve_plain_cap_s if truncated else None}
+    return {"requests": len(reqs), "rate_hz": 50.0, "samples_per_request": SERVE_SAMPLES, "rtol": SERVE_RTOL,
+            "grids": [list(s) for s in synth.SERVE_SHAPES], "precond": "harmonic",
+            "likelihoods": {"gauss": "sigma 0.1, identity response", "poisson": "rate 10 exp(cf)"},
+            "fp32_batched": fp32, "fp64_sequential": fp64,
+            "p50_speedup": fp64["p50_ms"] / fp32["p50_ms"], "p99_speedup": fp64["p99_ms"] / fp32["p99_ms"],
+            "throughput_ratio": fp32["solves_per_s"] / fp64["solves_per_s"]}
 
 
 def main():

@@ -259,6 +259,99 @@ int nre_prof_report(char *buf, size_t len);
 enum { NRE_PRECOND_NONE = 0, NRE_PRECOND_HARMONIC = 1 };
 int metric_set_precond(nre_metric *m, int kind, nre_stream_t stream);
 
+/* Device bytes currently held by the library's own allocations (plans,
+ * metrics, CG workspaces, servers), summed over all devices. */
+int nre_device_bytes(int64_t *bytes);
+
+/* ================================================================ serving
+ * A request loop for sampling solves: each request is one expansion point of
+ * a correlated-field model (Sec. "Variational Inference": MGVI draws each
+ * posterior sample by a CG solve of the metric at the current point) with
+ * n_samples right-hand sides solved to a relative residual.  Requests of
+ * different grids and likelihoods are served at once: a request is admitted
+ * when a slot is free and its device footprint fits the HBM budget (first in,
+ * first out), its CG state stays on the device until it converges, every
+ * admitted request runs on its own CUDA stream (optionally replaying its CG
+ * iterations as a CUDA graph), and the convergence of all of them is polled
+ * without blocking.  Nothing here is in the paper: it serves the paper's
+ * sampling step to many callers.
+ *
+ * Threads: serve_create starts prep_threads admission / set-up threads, one
+ * CG-launch thread and one completion thread.  serve_submit and serve_poll may be called
+ * from any thread.  serve_destroy waits for admitted work, fails queued
+ * requests with NRE_EBUSY and joins the threads. */
+typedef struct nre_server nre_server;
+
+typedef struct {
+  uint64_t hbm_budget_bytes; /* device bytes the server may hold; 0: half of
+                                the free device memory at create            */
+  int max_slots;             /* requests on the device at once (1..256)     */
+  int dtype;                 /* NRE_F32 or NRE_F64 for every solve          */
+  int chunk_iters;           /* CG iterations between convergence polls
+                                (0: 8)                                      */
+  int use_graphs;            /* 1: capture each slot's chunk of iterations
+                                once as a CUDA graph and replay it          */
+  int prep_threads;          /* admission / set-up threads (0: 8)           */
+} nre_serve_cfg;
+
+typedef struct {
+  int ndim;                  /* 1..3                                        */
+  int64_t shape[3];          /* powers of two in [8, 4096]; spacing 1/shape */
+  nre_cf_amp_params amp;     /* amplitude model (POWER_MODEL or MATERN_FIXED;
+                                copied at submit)                           */
+  int lik_kind;              /* NRE_LIK_GAUSS (every pixel observed, sigma)
+                                or NRE_LIK_POISSON (rate scale exp(cf))    */
+  int response;              /* Gaussian: NRE_RESP_EXP or NRE_RESP_IDENTITY;
+                                Poisson: NRE_RESP_EXP                       */
+  double sigma_or_scale;
+  int precond;               /* NRE_PRECOND_* of the solves                 */
+  int n_samples;             /* right-hand sides, 1..64                     */
+  double rtol;               /* > 0: stop at ||r|| <= rtol ||b||            */
+  int maxiter;               /* >= 1                                        */
+  /* HOST arrays in the server's dtype, C order, latent = cf_latent_size of
+   * the grid.  They are read after serve_submit returns, up to the moment the
+   * request starts, and x_out is written just before it completes: all must
+   * stay valid until serve_poll has returned NRE_OK for the request.  Page-
+   * locked memory makes the copies asynchronous. */
+  const void *xi_p;          /* [latent] expansion point                    */
+  const void *b;             /* [n_samples][latent] right-hand sides, or the
+                                latent draws xi' when eta is given          */
+  const void *eta;           /* NULL, or [n_samples][N] data-space draws:
+                                the right-hand sides become the MGVI
+                                b = xi' + J^T (sqrt(w) eta)                 */
+  void *x_out;               /* [n_samples][latent] solutions               */
+} nre_serve_req;
+
+typedef struct {
+  int status;                /* NRE_OK, NRE_ENOTCONV or the error of the solve */
+  int iters[64];             /* CG iterations per sample                    */
+  double relres[64];         /* recursive ||r|| / ||b|| per sample          */
+  double t_submit, t_start, t_done; /* CLOCK_MONOTONIC seconds: submit,
+                                admission, result copied to x_out           */
+  uint64_t device_bytes;     /* footprint charged against the budget        */
+  char error[192];           /* message when status != NRE_OK               */
+} nre_serve_result;
+
+typedef struct {
+  uint64_t budget, reserved, peak_reserved; /* bytes (reserved includes idle
+                                slot objects kept for reuse)                */
+  int active, queued, idle_objects;
+  uint64_t completed, reused, created, evicted, graph_replays, chunks;
+} nre_serve_stats;
+
+int serve_create(nre_server **srv, const nre_serve_cfg *cfg);
+/* Queues a request and returns its id.  NRE_EINVAL for a malformed request,
+ * NRE_EBUSY if its footprint exceeds the whole budget (it could never run). */
+int serve_submit(nre_server *srv, const nre_serve_req *req, uint64_t *id);
+/* Waits up to timeout_ms (0: do not wait, < 0: forever) for request id.
+ * NRE_OK: done, *res filled and the id released; NRE_EAGAIN: still pending;
+ * NRE_EINVAL: unknown or already collected id. */
+int serve_poll(nre_server *srv, uint64_t id, nre_serve_result *res, int timeout_ms);
+/* Device bytes a request would be charged (its footprint estimate). */
+int serve_footprint(const nre_serve_req *req, int dtype, uint64_t *bytes);
+int serve_stats(nre_server *srv, nre_serve_stats *st);
+int serve_destroy(nre_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,32 @@ class ICRKernelParams(C.Structure):
     _fields_ = [("rho", C.c_double), ("var", C.c_double)]
 
 
+class ServeCfg(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_int), ("dtype", C.c_int),
+                ("chunk_iters", C.c_int), ("use_graphs", C.c_int), ("prep_threads", C.c_int)]
+
+
+class ServeReq(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("shape", C.c_int64 * 3), ("amp", CFAmpParams),
+                ("lik_kind", C.c_int), ("response", C.c_int), ("sigma_or_scale", C.c_double),
+                ("precond", C.c_int),
+                ("n_samples", C.c_int), ("rtol", C.c_double), ("maxiter", C.c_int),
+                ("xi_p", C.c_void_p), ("b", C.c_void_p), ("eta", C.c_void_p), ("x_out", C.c_void_p)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int * 64), ("relres", C.c_double * 64),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("device_bytes", C.c_uint64), ("error", C.c_char * 192)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("budget", C.c_uint64), ("reserved", C.c_uint64), ("peak_reserved", C.c_uint64),
+                ("active", C.c_int), ("queued", C.c_int), ("idle_objects", C.c_int),
+                ("completed", C.c_uint64), ("reused", C.c_uint64), ("created", C.c_uint64),
+                ("evicted", C.c_uint64), ("graph_replays", C.c_uint64), ("chunks", C.c_uint64)]
+
+
 _P = C.c_void_p
 _I64P = C.POINTER(C.c_int64)
 
@@ -77,6 +103,13 @@ SIGNATURES = {
     "cg_solve": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                  C.POINTER(C.c_double), _P],
     "metric_set_precond": [_P, C.c_int, _P],
+    "nre_device_bytes": [_I64P],
+    "serve_create": [C.POINTER(_P), C.POINTER(ServeCfg)],
+    "serve_submit": [_P, C.POINTER(ServeReq), C.POINTER(C.c_uint64)],
+    "serve_poll": [_P, C.c_uint64, C.POINTER(ServeResult), C.c_int],
+    "serve_footprint": [C.POINTER(ServeReq), C.c_int, C.POINTER(C.c_uint64)],
+    "serve_stats": [_P, C.POINTER(ServeStats)],
+    "serve_destroy": [_P],
     "nre_prof_enable": [C.c_int],
     "nre_prof_report": [C.c_char_p, C.c_size_t],
 }

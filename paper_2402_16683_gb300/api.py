@@ -45,6 +45,38 @@ def bin_map(shape, spacing, n_bins=256):
     return out.reshape(shape)
 
 
+def _amp_params(amplitude="power", prior=None, matern=None, offset_mean=0.0):
+    """nre_cf_amp_params of an amplitude choice (see CorrelatedField); returns
+    (params, array kept alive for NRE_AMP_ARRAY or None)."""
+    a = L.CFAmpParams()
+    arr = None
+    if isinstance(amplitude, np.ndarray):
+        a.kind = L.NRE_AMP_ARRAY
+        arr = np.ascontiguousarray(amplitude, dtype=np.float64).ravel()
+        a.amp_array = arr.ctypes.data_as(C.POINTER(C.c_double))
+        a.offset_mean = offset_mean
+    elif amplitude == "matern":
+        m = dict(k0=8.0, gamma=1.5, variance=1.0, zero_mode=0.0)
+        m.update(matern or {})
+        a.kind = L.NRE_AMP_MATERN_FIXED
+        a.k0, a.gamma, a.variance, a.zero_mode = m["k0"], m["gamma"], m["variance"], m["zero_mode"]
+        a.offset_mean = offset_mean
+    elif amplitude == "power":
+        pr = dict(fluct=(1.0, 0.5), slope=(-3.0, 0.5), flex=(1.0, 0.5), asp=(0.1, 0.05),
+                  offset_mean=0.0, offset_std=1.0, n_bins=256)
+        pr.update(prior or {})
+        a.kind = L.NRE_AMP_POWER_MODEL
+        a.fluct_mean, a.fluct_std = pr["fluct"]
+        a.slope_mean, a.slope_std = pr["slope"]
+        a.flex_mean, a.flex_std = pr["flex"]
+        a.asp_mean, a.asp_std = pr["asp"]
+        a.offset_mean, a.offset_std = pr["offset_mean"], pr["offset_std"]
+        a.n_bins = pr["n_bins"]
+    else:
+        raise ValueError(f"unknown amplitude {amplitude!r}")
+    return a, arr
+
+
 class CorrelatedField:
     """Correlated-field plan (cf_create).
 
@@ -60,32 +92,7 @@ class CorrelatedField:
         self.shape = tuple(int(s) for s in shape)
         self.spacing = tuple(float(s) for s in (spacing or [1.0 / s for s in self.shape]))
         self.dtype = dtype
-        a = L.CFAmpParams()
-        self._arr = None
-        if isinstance(amplitude, np.ndarray):
-            a.kind = L.NRE_AMP_ARRAY
-            self._arr = np.ascontiguousarray(amplitude, dtype=np.float64).ravel()
-            a.amp_array = self._arr.ctypes.data_as(C.POINTER(C.c_double))
-            a.offset_mean = offset_mean
-        elif amplitude == "matern":
-            m = dict(k0=8.0, gamma=1.5, variance=1.0, zero_mode=0.0)
-            m.update(matern or {})
-            a.kind = L.NRE_AMP_MATERN_FIXED
-            a.k0, a.gamma, a.variance, a.zero_mode = m["k0"], m["gamma"], m["variance"], m["zero_mode"]
-            a.offset_mean = offset_mean
-        elif amplitude == "power":
-            pr = dict(fluct=(1.0, 0.5), slope=(-3.0, 0.5), flex=(1.0, 0.5), asp=(0.1, 0.05),
-                      offset_mean=0.0, offset_std=1.0, n_bins=256)
-            pr.update(prior or {})
-            a.kind = L.NRE_AMP_POWER_MODEL
-            a.fluct_mean, a.fluct_std = pr["fluct"]
-            a.slope_mean, a.slope_std = pr["slope"]
-            a.flex_mean, a.flex_std = pr["flex"]
-            a.asp_mean, a.asp_std = pr["asp"]
-            a.offset_mean, a.offset_std = pr["offset_mean"], pr["offset_std"]
-            a.n_bins = pr["n_bins"]
-        else:
-            raise ValueError(f"unknown amplitude {amplitude!r}")
+        a, self._arr = _amp_params(amplitude, prior, matern, offset_mean)
         h = C.c_void_p()
         shp = (C.c_int64 * len(self.shape))(*self.shape)
         sp = (C.c_double * len(self.shape))(*self.spacing)
@@ -297,3 +304,116 @@ class Metric:
         if st != L.NRE_OK and (st != L.NRE_ENOTCONV or raise_on_notconv):
             check(st)
         return x, list(it), list(rr), st
+
+
+def _host_ptr(a, dtype, n, name):
+    """Address of a contiguous host array (numpy or CPU tensor) of n entries."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != dtype or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{name}: need a contiguous CPU tensor of {n} {dtype}")
+        return a.data_ptr()
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    if not isinstance(a, np.ndarray) or a.dtype != npdt or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"{name}: need a C-contiguous numpy array of {n} {npdt.__name__}")
+    return a.ctypes.data
+
+
+class Server:
+    """Request loop for sampling solves (serve_*): continuous batching of
+    correlated-field CG solves of different grids on one device.
+
+    Inputs and outputs are HOST arrays in the server dtype (page-locked CPU
+    tensors give asynchronous copies); the server reads / writes them until the
+    request is polled, and this object keeps them referenced until then.
+    """
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=8, dtype=torch.float32, chunk_iters=8,
+                 use_graphs=True, prep_threads=8):
+        lib = L.load()
+        cfg = L.ServeCfg(int(hbm_budget_bytes), int(max_slots), _DT[dtype], int(chunk_iters),
+                         1 if use_graphs else 0, int(prep_threads))
+        h = C.c_void_p()
+        check(lib.serve_create(C.byref(h), C.byref(cfg)))
+        self.handle = h
+        self.dtype = dtype
+        self._keep = {}
+
+    def _request(self, shape, xi_p, b, x_out, lik, sigma, scale, amplitude, prior, matern, precond,
+                 rtol, maxiter, eta, n_samples, check_arrays=True, response="exp"):
+        r = L.ServeReq()
+        r.ndim = len(shape)
+        for d, n in enumerate(shape):
+            r.shape[d] = int(n)
+        r.amp, _ = _amp_params(amplitude, prior, matern)
+        r.lik_kind = L.NRE_LIK_GAUSS if lik == "gauss" else L.NRE_LIK_POISSON
+        r.response = L.NRE_RESP_IDENTITY if response == "identity" else L.NRE_RESP_EXP
+        r.sigma_or_scale = float(sigma if lik == "gauss" else scale)
+        r.precond = L.NRE_PRECOND_HARMONIC if precond == "harmonic" else L.NRE_PRECOND_NONE
+        r.n_samples = int(n_samples)
+        r.rtol = float(rtol)
+        r.maxiter = int(maxiter)
+        if check_arrays:
+            N = int(np.prod(shape))
+            lat = N + (4 + 2 * (r.amp.n_bins - 1) if r.amp.kind == L.NRE_AMP_POWER_MODEL else 0)
+            r.xi_p = _host_ptr(xi_p, self.dtype, lat, "xi_p")
+            r.b = _host_ptr(b, self.dtype, n_samples * lat, "b")
+            r.x_out = _host_ptr(x_out, self.dtype, n_samples * lat, "x_out")
+            r.eta = _host_ptr(eta, self.dtype, n_samples * N, "eta") if eta is not None else None
+        return r
+
+    def submit(self, shape, xi_p, b, x_out, lik="gauss", sigma=0.1, scale=10.0, amplitude="power",
+               prior=None, matern=None, precond="harmonic", rtol=1e-5, maxiter=1000, eta=None,
+               response="exp"):
+        """Queue one request (b: [n_samples, latent], x_out likewise); returns its id."""
+        n = int(np.prod(b.shape[:-1])) if len(b.shape) > 1 else 1
+        r = self._request(shape, xi_p, b, x_out, lik, sigma, scale, amplitude, prior, matern, precond,
+                          rtol, maxiter, eta, n, response=response)
+        rid = C.c_uint64()
+        check(L.load().serve_submit(self.handle, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = (xi_p, b, x_out, eta)
+        return rid.value
+
+    def footprint(self, shape, n_samples=8, lik="gauss", amplitude="power", prior=None, matern=None,
+                  precond="harmonic", mgvi=False):
+        """Device bytes a request of this kind is charged."""
+        r = self._request(shape, None, None, None, lik, 0.1, 10.0, amplitude, prior, matern, precond, 1e-5,
+                          1, None, n_samples, check_arrays=False)
+        if mgvi:
+            r.eta = 1
+        out = C.c_uint64()
+        check(L.load().serve_footprint(C.byref(r), _DT[self.dtype], C.byref(out)))
+        return out.value
+
+    def poll(self, rid, timeout_ms=-1):
+        """Result dict of a finished request, or None while it is pending."""
+        res = L.ServeResult()
+        st = L.load().serve_poll(self.handle, C.c_uint64(rid), C.byref(res), int(timeout_ms))
+        if st == L.NRE_EAGAIN:
+            return None
+        check(st)
+        self._keep.pop(rid, None)
+        n = 64
+        return dict(status=res.status, iters=list(res.iters[:n]), relres=list(res.relres[:n]),
+                    t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done,
+                    device_bytes=res.device_bytes, error=res.error.decode(errors="replace"))
+
+    def stats(self):
+        s = L.ServeStats()
+        check(L.load().serve_stats(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+
+def device_bytes():
+    """Device bytes held by the library's own allocations."""
+    v = C.c_int64()
+    check(L.load().nre_device_bytes(C.byref(v)))
+    return v.value

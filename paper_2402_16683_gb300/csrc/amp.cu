@@ -18,32 +18,58 @@ namespace nre {
 
 namespace {
 
-__device__ double scan_incl(double v, double* buf) {
-  const int i = threadIdx.x;
-  __syncthreads();
-  buf[i] = v;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const double t = (i >= o) ? buf[i - o] : 0.0;
-    __syncthreads();
-    buf[i] += t;
-    __syncthreads();
+// Block-wide inclusive prefix / suffix sums of one double per thread
+// (blockDim.x a multiple of 32): shuffle scans within each warp, then a scan of
+// the warp totals.  The result is also left in buf[threadIdx.x] for the
+// neighbour reads of the callers.
+__device__ __forceinline__ double warp_prefix(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
   }
-  return buf[i];
+  return v;
+}
+
+__device__ __forceinline__ double warp_suffix(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += t;
+  }
+  return v;
+}
+
+__device__ double scan_incl(double v, double* buf) {
+  __shared__ double wt[32];
+  const int i = threadIdx.x, lane = i & 31, w = i >> 5, nw = blockDim.x >> 5;
+  double x = warp_prefix(v);
+  __syncthreads();  // earlier readers of buf / wt are done
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) wt[lane] = warp_prefix(lane < nw ? wt[lane] : 0.0);
+  __syncthreads();
+  if (w > 0) x += wt[w - 1];
+  buf[i] = x;
+  __syncthreads();
+  return x;
 }
 
 __device__ double scan_suffix(double v, double* buf) {
-  const int i = threadIdx.x, n = blockDim.x;
+  __shared__ double wt[32];
+  const int i = threadIdx.x, lane = i & 31, w = i >> 5, nw = blockDim.x >> 5;
+  double x = warp_suffix(v);
   __syncthreads();
-  buf[i] = v;
+  if (lane == 0) wt[w] = x;
   __syncthreads();
-  for (int o = 1; o < n; o <<= 1) {
-    const double t = (i + o < n) ? buf[i + o] : 0.0;
-    __syncthreads();
-    buf[i] += t;
-    __syncthreads();
-  }
-  return buf[i];
+  if (w == 0) wt[lane] = warp_suffix(lane < nw ? wt[lane] : 0.0);
+  __syncthreads();
+  if (w + 1 < nw) x += wt[w + 1];
+  buf[i] = x;
+  __syncthreads();
+  return x;
 }
 
 struct Th {
@@ -139,7 +165,7 @@ __global__ void k_amp_jvp(AmpPrior pr, const double* state, int64_t ss, const T*
 
 template <typename T>
 __global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const double* partials,
-                          int nparts, const T* base, int64_t bhs, T* out, int64_t ohs) {
+                          int nparts, const T* base, int64_t bhs, T* out, int64_t ohs, double* dot) {
   __shared__ double buf[1024];
   __shared__ double red[32];
   const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
@@ -187,15 +213,26 @@ __global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const do
   const double g_thas = block_sum(p_as, red);
   T* o = out + b * ohs;
   const T* bb = base ? base + b * bhs : nullptr;
+  double dsum = 0.0;  // sum(base * out) over the hyper entries (fused inner product)
   if (act && i >= 1) {
     const int j1 = 4 + i - 1, j2 = 4 + nb - 1 + i - 1;
-    o[j1] = T((bb ? double(bb[j1]) : 0.0) + g_xi1);
-    o[j2] = T((bb ? double(bb[j2]) : 0.0) + g_xi2);
+    const T o1 = T((bb ? double(bb[j1]) : 0.0) + g_xi1), o2 = T((bb ? double(bb[j2]) : 0.0) + g_xi2);
+    o[j1] = o1;
+    o[j2] = o2;
+    if (bb) dsum += double(bb[j1] * o1) + double(bb[j2] * o2);
   }
   if (i == 0) {
     const double g4[4] = {g_thfl * th_fl * pr.s_fl, g_thsl * pr.sl_s, g_thfx * th_fx * pr.s_fx,
                           g_thas * th_as * pr.s_as};
-    for (int j = 0; j < 4; ++j) o[j] = T((bb ? double(bb[j]) : 0.0) + g4[j]);
+    for (int j = 0; j < 4; ++j) {
+      const T oj = T((bb ? double(bb[j]) : 0.0) + g4[j]);
+      o[j] = oj;
+      if (bb) dsum += double(bb[j] * oj);
+    }
+  }
+  if (dot != nullptr) {
+    const double t = block_sum(dsum, red);
+    if (i == 0) dot[(int64_t)b * kDotStride + kDotStride - 1] = t;
   }
 }
 
@@ -241,11 +278,11 @@ int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, in
 template <typename T>
 int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* partials,
             int nparts, const T* base_h, int64_t bhs, T* out_h, int64_t ohs, int B,
-            cudaStream_t st) {
+            cudaStream_t st, double* dot) {
   prof_begin("amp_vjp", (double)B * pr.nb * (8.0 * nparts + (base_h ? 4 : 2) * sizeof(T)) +
                             (ss ? B : 1) * pr.nb * 40.0, st);
   k_amp_vjp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, partials, nparts, base_h, bhs,
-                                                  out_h, ohs);
+                                                  out_h, ohs, dot);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -256,7 +293,7 @@ int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* p
   template int amp_jvp<T>(const AmpPrior&, const double*, int64_t, const T*, int64_t, double*,   \
                           int, cudaStream_t);                                                    \
   template int amp_vjp<T>(const AmpPrior&, const double*, int64_t, const double*, int, const T*, \
-                          int64_t, T*, int64_t, int, cudaStream_t);
+                          int64_t, T*, int64_t, int, cudaStream_t, double*);
 NRE_INST(float)
 NRE_INST(double)
 #undef NRE_INST

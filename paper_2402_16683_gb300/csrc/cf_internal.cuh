@@ -118,6 +118,10 @@ struct Pro {
 enum { EPI_BUF = 0, EPI_OFFSET = 1, EPI_WEIGHT = 2, EPI_AMP = 3 };
 
 // Consumer of the last transform's output at (sample b, pixel flat).
+// Partials of the fused metric-product inner product per sample: one per CTA
+// of the last sweep (at most 128) and the hyper-parameter part in the last.
+constexpr int kDotStride = 129;
+
 template <typename T>
 struct Epi {
   int mode;
@@ -135,6 +139,10 @@ struct Epi {
   int64_t ps;
   int bins;           // accumulate the per-bin sums
   AmpView<T> av;
+  // EPI_AMP with base, last sweep of a metric product: per-CTA partials of
+  // sum(base * y) at dot[b * kDotStride + cta] (row sweeps of 2-D / 3-D grids;
+  // other sweeps leave them to a separate reduction)
+  double* dot;
 
   // Writes the output of pixel `flat` of sample b.  EPI_AMP with bins also
   // returns the pixel's contribution xi_p * value to its log-|k| bin (bn = -1:
@@ -143,14 +151,17 @@ struct Epi {
     store_b(b, flat, val, (mode == EPI_AMP && base != nullptr) ? base[b * bs + flat] : T(0), bn_out, contrib);
   }
   // As store, with the EPI_AMP base value already loaded.
-  __device__ __forceinline__ void store_b(int b, int64_t flat, T val, T bval, int& bn_out, T& contrib,
-                                          const T* stab = nullptr) const {
+  // Returns the value written.
+  __device__ __forceinline__ T store_b(int b, int64_t flat, T val, T bval, int& bn_out, T& contrib,
+                                       const T* stab = nullptr) const {
     bn_out = -1;
     contrib = T(0);
     if (mode == EPI_BUF) {
       y[b * ys + flat] = val;
+      return val;
     } else if (mode == EPI_OFFSET) {
       y[b * ys + flat] = T(offset) + val;
+      return T(offset) + val;
     } else if (mode == EPI_WEIGHT) {
       const T cf = T(offset) + val;
       T w;
@@ -167,6 +178,7 @@ struct Epi {
         if (mask != nullptr) w *= __ldg(&mask[flat]);
       }
       y[b * ys + flat] = w;
+      return w;
     } else {
       const int bn = av.binned() ? av.bin(flat) : -1;
       const T o = av.amp_t(b, flat, bn, stab) * val + bval;
@@ -175,6 +187,7 @@ struct Epi {
         bn_out = bn;
         contrib = xi_p[b * ps + flat] * val;
       }
+      return o;
     }
   }
   // Outputs at flat and flat + 1 (flat even).
@@ -286,10 +299,11 @@ template <typename T>
 int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
             double* dA, int B, cudaStream_t st);
 // out_h[b] = base_h[b] (optional) + VJP at state of gA[b] = sum_c partials[b][c][:].
+// With `dot` (and a base): dot[b * kDotStride + kDotStride - 1] = sum(base_h * out_h).
 template <typename T>
 int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* partials,
             int nparts, const T* base_h, int64_t bhs, T* out_h, int64_t ohs, int B,
-            cudaStream_t st);
+            cudaStream_t st, double* dot = nullptr);
 
 // Sweep chains (sweeps.cu).  Runs one Hartley transform (mid == nullptr) or the
 // metric's transform pair with t = w * y between them (mid != nullptr) over a

@@ -17,7 +17,8 @@ using namespace nre;
 namespace {
 
 constexpr int CG_THREADS = 256;
-enum { SC_RR = 0, SC_BB = 1, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = 4, SC_ITERS = 5, SC_N = 8 };
+enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
+       SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
 // Blocks per system of the vector kernels.
 int cg_blocks(int64_t n) {
@@ -154,14 +155,23 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, i
 // x += alpha p, r -= alpha q; then (last block) beta = r'.r' / r.r, the
 // iteration count and the convergence test.  A system that has converged
 // keeps beta = 0 and its x, r frozen.
+// With pq (the fused p.q partials of the metric product, kDotStride per
+// system) every block forms alpha = r.r / p.q itself; the last block of the
+// system, which alone rewrites r.r, starts only after every block has read it.
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_update(T* x, T* r, const T* p, const T* q, int64_t n,
                                                          int64_t S, double* sc, double* rr_part,
-                                                         unsigned* counter, double rtol) {
+                                                         unsigned* counter, double rtol, const double* pq) {
   const int b = blockIdx.y;
   double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
-  const T alpha = T(c[SC_ALPHA]);
+  T alpha;
+  if (pq != nullptr) {
+    const double s = block_sum_array(pq + (int64_t)b * kDotStride, kDotStride);
+    alpha = T(active && s != 0.0 ? c[SC_RR] / s : 0.0);
+  } else {
+    alpha = T(c[SC_ALPHA]);
+  }
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
   for_vec<T>(n, [&](int64_t i, int w) {
@@ -229,9 +239,32 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_pupdate(T* p, const T* r, int
   });
 }
 
+// Device pointers of the CG workspace of a batch of B systems.
 template <typename T>
-int cg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* iters_out,
-         double* relres_out, cudaStream_t st) {
+struct CGWork {
+  T *r, *p, *q;
+  double *sc, *part_a, *part_b;
+  unsigned* counter;
+  int nblk;
+};
+
+template <typename T>
+CGWork<T> cg_work(nre_metric* m, int B) {
+  CGWork<T> w;
+  w.nblk = cg_blocks(m->latent);
+  w.r = m->cg_r.as<T>();
+  w.p = m->cg_p.as<T>();
+  w.q = m->cg_q.as<T>();
+  w.sc = m->cg_sc.as<double>();
+  w.part_a = m->cg_part.as<double>();
+  w.part_b = w.part_a + (size_t)B * w.nblk;
+  w.counter = reinterpret_cast<unsigned*>(w.part_b + (size_t)B * w.nblk);
+  return w;
+}
+
+// Workspace, x = 0, r = p = b and the initial scalars; enqueue only.
+template <typename T>
+int cg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_t st) {
   const int64_t n = m->latent, S = m->stride;
   NRE_TRY(ensure(m->cg_r, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_p, (size_t)B * S * sizeof(T)));
@@ -239,62 +272,108 @@ int cg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* 
   NRE_TRY(ensure(m->cg_sc, (size_t)B * SC_N * sizeof(double)));
   const int nblk = cg_blocks(n);
   NRE_TRY(ensure(m->cg_part, (size_t)2 * B * nblk * sizeof(double) + (size_t)B * sizeof(unsigned)));
-  T* r = m->cg_r.as<T>();
-  T* p = m->cg_p.as<T>();
-  T* q = m->cg_q.as<T>();
-  double* sc = m->cg_sc.as<double>();
-  double* part_a = m->cg_part.as<double>();
-  double* part_b = part_a + (size_t)B * nblk;
-  unsigned* counter = reinterpret_cast<unsigned*>(part_b + (size_t)B * nblk);
-  NRE_TRY_CUDA(cudaMemsetAsync(counter, 0, (size_t)B * sizeof(unsigned), st));
+  if (m->model_kind == NRE_MODEL_CF) NRE_TRY(ensure(m->cg_dot, (size_t)B * kDotStride * sizeof(double)));
+  const CGWork<T> w = cg_work<T>(m, B);
+  NRE_TRY_CUDA(cudaMemsetAsync(w.counter, 0, (size_t)B * sizeof(unsigned), st));
   const dim3 grid(nblk, B);
   const double vb = (double)B * n * sizeof(T);
   prof_begin("cg_init", 4 * vb, st);
-  k_cg_init<T><<<grid, CG_THREADS, 0, st>>>(b, x, r, p, n, S, part_a);
+  k_cg_init<T><<<grid, CG_THREADS, 0, st>>>(b, x, w.r, w.p, n, S, w.part_a);
   prof_end(st);
   prof_begin("cg_scalars", 0.0, st);
-  k_cg_start<<<B, 32, 0, st>>>(sc, part_a, nblk, rtol);
+  k_cg_start<<<B, 32, 0, st>>>(w.sc, w.part_a, nblk, rtol);
   prof_end(st);
   NRE_CHECK_LAUNCH();
-  m->cg_host.resize((size_t)B * SC_N);
-  const int check_every = 8;
-  for (int it = 0; it < maxiter; ++it) {
-    NRE_TRY(metric_apply_impl(m, p, q, B, st));
-    prof_begin("cg_dot", 2 * vb, st);
-    k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(p, q, n, S, part_a, counter, sc);
-    prof_end(st);
-    prof_begin("cg_update", 6 * vb, st);
-    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, r, p, q, n, S, sc, part_b, counter, rtol);
-    prof_end(st);
-    prof_begin("cg_pupdate", 3 * vb, st);
-    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(p, r, n, S, sc);
-    prof_end(st);
-    NRE_CHECK_LAUNCH();
-    if (rtol > 0.0 && (it + 1) % check_every == 0 && it + 1 < maxiter) {
-      NRE_TRY_CUDA(cudaMemcpyAsync(m->cg_host.data(), sc, (size_t)B * SC_N * sizeof(double),
-                                   cudaMemcpyDeviceToHost, st));
-      NRE_TRY_CUDA(cudaStreamSynchronize(st));
-      bool any = false;
-      for (int i = 0; i < B; ++i) any |= m->cg_host[(size_t)i * SC_N + SC_ACTIVE] != 0.0;
-      if (!any) break;
-    }
-  }
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->cg_host.data(), sc, (size_t)B * SC_N * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-  NRE_TRY_CUDA(cudaStreamSynchronize(st));
-  bool conv = true;
-  for (int i = 0; i < B; ++i) {
-    const double* c = &m->cg_host[(size_t)i * SC_N];
-    const double rel = c[SC_BB] > 0 ? std::sqrt(c[SC_RR] / c[SC_BB]) : 0.0;
-    if (iters_out) iters_out[i] = (int)c[SC_ITERS];
-    if (relres_out) relres_out[i] = rel;
-    if (rtol > 0.0 && rel > rtol) conv = false;
-  }
-  if (!conv) return set_error(NRE_ENOTCONV, "CG: some system missed rtol=%g within maxiter=%d", rtol, maxiter);
   return NRE_OK;
 }
 
+// `iters` iterations on the state left by cg_begin_t; enqueue only.
+template <typename T>
+int cg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t st) {
+  const int64_t n = m->latent, S = m->stride;
+  const CGWork<T> w = cg_work<T>(m, B);
+  const dim3 grid(w.nblk, B);
+  const double vb = (double)B * n * sizeof(T);
+  // correlated field: p.q comes fused with the metric product
+  double* pq = m->model_kind == NRE_MODEL_CF ? m->cg_dot.as<double>() : nullptr;
+  for (int it = 0; it < iters; ++it) {
+    NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, pq));
+    if (!pq) {
+      prof_begin("cg_dot", 2 * vb, st);
+      k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.q, n, S, w.part_a, w.counter, w.sc);
+      prof_end(st);
+    }
+    prof_begin("cg_update", 6 * vb, st);
+    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, w.r, w.p, w.q, n, S, w.sc, w.part_b, w.counter, rtol, pq);
+    prof_end(st);
+    prof_begin("cg_pupdate", 3 * vb, st);
+    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.r, n, S, w.sc);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+  }
+  return NRE_OK;
+}
+
+template <typename T>
+int cg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* iters_out,
+         double* relres_out, cudaStream_t st) {
+  NRE_TRY(cg_begin_t<T>(m, b, x, B, rtol, st));
+  const int check_every = 8;
+  for (int it = 0; it < maxiter; it += check_every) {
+    const int k = maxiter - it < check_every ? maxiter - it : check_every;
+    NRE_TRY(cg_iter_t<T>(m, x, B, k, rtol, st));
+    if (rtol > 0.0 && it + k < maxiter) {
+      NRE_TRY(cg_read_scalars(m, B, st));
+      if (!cg_any_active(m, B)) break;
+    }
+  }
+  NRE_TRY(cg_read_scalars(m, B, st));
+  return cg_report(m, B, rtol, maxiter, iters_out, relres_out, "CG");
+}
+
 }  // namespace
+
+namespace nre {
+int cg_read_scalars(nre_metric* m, int B, cudaStream_t st) {
+  m->cg_host.resize((size_t)B * CG_SC_N);
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->cg_host.data(), m->cg_sc.p, (size_t)B * CG_SC_N * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+  NRE_TRY_CUDA(cudaStreamSynchronize(st));
+  return NRE_OK;
+}
+
+bool cg_any_active(const nre_metric* m, int B) {
+  for (int i = 0; i < B; ++i)
+    if (m->cg_host[(size_t)i * CG_SC_N + CG_SC_ACTIVE] != 0.0) return true;
+  return false;
+}
+
+int cg_report(const nre_metric* m, int B, double rtol, int maxiter, int* iters_out, double* relres_out,
+              const char* what) {
+  bool conv = true;
+  for (int i = 0; i < B; ++i) {
+    const double* c = &m->cg_host[(size_t)i * CG_SC_N];
+    const double rel = c[CG_SC_BB] > 0 ? std::sqrt(c[CG_SC_RR] / c[CG_SC_BB]) : 0.0;
+    if (iters_out) iters_out[i] = (int)c[CG_SC_ITERS];
+    if (relres_out) relres_out[i] = rel;
+    if (rtol > 0.0 && rel > rtol) conv = false;
+  }
+  if (!conv) return set_error(NRE_ENOTCONV, "%s: some system missed rtol=%g within maxiter=%d", what, rtol, maxiter);
+  return NRE_OK;
+}
+
+int cg_begin(nre_metric* m, const void* b, void* x, int B, double rtol, cudaStream_t st) {
+  if (m->precond != NRE_PRECOND_NONE) return pcg_begin(m, b, x, B, rtol, st);
+  if (m->dtype == NRE_F64) return cg_begin_t<double>(m, (const double*)b, (double*)x, B, rtol, st);
+  return cg_begin_t<float>(m, (const float*)b, (float*)x, B, rtol, st);
+}
+
+int cg_iterate(nre_metric* m, void* x, int B, int iters, double rtol, cudaStream_t st) {
+  if (m->precond != NRE_PRECOND_NONE) return pcg_iterate(m, x, B, iters, rtol, st);
+  if (m->dtype == NRE_F64) return cg_iter_t<double>(m, (double*)x, B, iters, rtol, st);
+  return cg_iter_t<float>(m, (float*)x, B, iters, rtol, st);
+}
+}  // namespace nre
 
 extern "C" int cg_solve(nre_metric* m, const void* b, void* x, int batch, double rtol, int maxiter,
                         int* iters_out, double* relres_out, nre_stream_t stream) {

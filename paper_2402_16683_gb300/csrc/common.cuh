@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -44,6 +45,11 @@ void prof_end(cudaStream_t st);
                               cudaGetErrorString(e_), __FILE__, __LINE__);     \
   } while (0)
 
+// Device bytes held by DevBufs of this process (prof.cu).
+std::atomic<long long>& dev_bytes();
+// Kernels launched outside prof_begin (graph replays): adds to the launch count.
+void prof_add_launches(unsigned long long n);
+
 // Owning device allocation (freed in the destructor).
 struct DevBuf {
   void* p = nullptr;
@@ -53,7 +59,10 @@ struct DevBuf {
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      dev_bytes().fetch_sub((long long)bytes);
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -67,6 +76,7 @@ struct DevBuf {
       return set_error(NRE_ENOMEM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
     }
     bytes = n;
+    dev_bytes().fetch_add((long long)n);
     return NRE_OK;
   }
   int upload(const void* h, size_t n) {
@@ -111,6 +121,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int i = 0; i < nw; ++i) t += red[i];
   __syncthreads();
   return t;
+}
+
+// Sum of n doubles p[0..n) by the first warp of the block in a fixed order
+// (lane-strided runs, then a shuffle tree); every thread gets the result.
+// Must be called by all threads of the block.
+__device__ __forceinline__ double block_sum_array(const double* p, int n) {
+  __shared__ double res;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += p[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) res = s;
+  }
+  __syncthreads();
+  const double r = res;
+  __syncthreads();
+  return r;
 }
 
 }  // namespace nre

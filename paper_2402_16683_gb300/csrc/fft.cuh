@@ -154,4 +154,18 @@ __device__ __forceinline__ void hartley_unpack(C z, C zm, T* ha, T* hb) {
   hb[1] = half * (zm.x - z.x + zm.y + z.y);
 }
 
+// R[s ^ m] of the reflection-orbit values of one column with s known at
+// compile time (unrolled loops) and the mask m = f0 + 2 f1 known only at run
+// time, written as selects so that R stays in registers.
+template <typename T>
+__device__ __forceinline__ T pick2(const T (&R)[2][2], int s, bool f0, int c) {
+  return f0 ? R[s ^ 1][c] : R[s][c];
+}
+template <typename T>
+__device__ __forceinline__ T pick4(const T (&R)[4][2], int s, bool f0, bool f1, int c) {
+  const T a = f0 ? R[s ^ 1][c] : R[s][c];
+  const T b = f0 ? R[s ^ 3][c] : R[s ^ 2][c];
+  return f1 ? b : a;
+}
+
 }  // namespace nre

@@ -53,15 +53,17 @@ template <typename T>
 int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   nre_cf_plan* p = m->cf;
   const int64_t N = p->N;
-  NRE_TRY(m->xi_p.alloc(p->stride * sizeof(T)));
+  NRE_TRY(ensure(m->xi_p, p->stride * sizeof(T)));
   NRE_TRY_CUDA(cudaMemcpyAsync(m->xi_p.p, xi_p_in, p->latent * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  NRE_TRY(m->w.alloc(N * sizeof(T)));
+  NRE_TRY(ensure(m->w, N * sizeof(T)));
   if (!m->lik.mask.empty()) {
-    std::vector<T> mk(m->lik.mask.begin(), m->lik.mask.end());
-    NRE_TRY(m->mask.upload(mk.data(), mk.size() * sizeof(T)));
+    if (!m->mask.p) {
+      std::vector<T> mk(m->lik.mask.begin(), m->lik.mask.end());
+      NRE_TRY(m->mask.upload(mk.data(), mk.size() * sizeof(T)));
+    }
   }
-  NRE_TRY(m->tmp0.alloc((size_t)m->max_batch * N * sizeof(T)));
-  NRE_TRY(m->tmp1.alloc((size_t)m->max_batch * N * sizeof(T)));
+  NRE_TRY(ensure(m->tmp0, (size_t)m->max_batch * N * sizeof(T)));
+  NRE_TRY(ensure(m->tmp1, (size_t)m->max_batch * N * sizeof(T)));
   const T* xp = m->xi_p.as<T>();
   Pro<T> pro{};
   pro.mode = PRO_AMP;
@@ -78,13 +80,13 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   epi.mask = m->mask.p ? m->mask.as<T>() : nullptr;
   if (p->amp_kind == NRE_AMP_POWER_MODEL) {
     const int nb = p->n_bins;
-    NRE_TRY(m->state.alloc(amp_state_size(nb) * sizeof(double)));
-    NRE_TRY(m->dA.alloc((size_t)m->max_batch * nb * sizeof(double)));
-    NRE_TRY(m->part.alloc((size_t)m->max_batch * max_parts(p) * nb * sizeof(double)));
+    NRE_TRY(ensure(m->state, amp_state_size(nb) * sizeof(double)));
+    NRE_TRY(ensure(m->dA, (size_t)m->max_batch * nb * sizeof(double)));
+    NRE_TRY(ensure(m->part, (size_t)m->max_batch * max_parts(p) * nb * sizeof(double)));
     NRE_TRY(amp_forward<T>(amp_prior_of(p), xp + N, 0, m->state.as<double>(), 1, st));
     pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
-    NRE_TRY(m->apix.alloc(N * sizeof(T)));
-    NRE_TRY(m->bpix.alloc(N * sizeof(int16_t)));
+    NRE_TRY(ensure(m->apix, N * sizeof(T)));
+    NRE_TRY(ensure(m->bpix, N * sizeof(int16_t)));
     prof_begin("pix_tables", (double)N * (sizeof(T) + 2), st);
     k_pix_tables<T><<<304, 256, 0, st>>>(pro.av, m->apix.as<T>(), m->bpix.as<int16_t>(), N);
     prof_end(st);
@@ -97,7 +99,7 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
 }
 
 template <typename T>
-int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
+int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, double* dot) {
   nre_cf_plan* p = m->cf;
   const int64_t N = p->N, S = p->stride;
   const T* xp = m->xi_p.as<T>();
@@ -111,6 +113,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
   epi.ys = S;
   epi.base = v;
   epi.bs = S;
+  epi.dot = dot;
   Mid<T> mid{m->w.as<T>()};
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   const int nb = p->n_bins;
@@ -135,7 +138,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st) {
                          model ? m->part.as<double>() : nullptr, &np, st));
   if (model)
     NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,
-                       B, st));
+                       B, st, dot));
   return NRE_OK;
 }
 
@@ -177,10 +180,15 @@ int cf_mgvi_rhs(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cud
 }  // namespace
 
 namespace nre {
-int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st) {
+int metric_relinearize(nre_metric* m, const void* xi_p, cudaStream_t st) {
+  if (m->model_kind != NRE_MODEL_CF) return set_error(NRE_EINVAL, "relinearisation is implemented for the correlated field");
+  return m->dtype == NRE_F64 ? cf_metric_setup<double>(m, xi_p, st) : cf_metric_setup<float>(m, xi_p, st);
+}
+
+int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st, double* dot) {
   if (m->model_kind == NRE_MODEL_ICR) return icr_metric_apply(m, v, out, batch, st);
-  if (m->dtype == NRE_F64) return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st);
-  return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st);
+  if (m->dtype == NRE_F64) return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st, dot);
+  return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st, dot);
 }
 }  // namespace nre
 

@@ -32,6 +32,7 @@ struct nre_metric {
   nre::DevBuf tmp0, tmp1, part;
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;
+  nre::DevBuf cg_dot;  // [max batch][kDotStride] fused p.q partials
   std::vector<double> cg_host;
   // preconditioner (metric_set_precond)
   int precond = 0;
@@ -40,6 +41,9 @@ struct nre_metric {
   nre::DevBuf pc_G;       // float [n_hyper][n_bins]: dA_b / dh at xi_p
   nre::DevBuf pc_Sinv;    // float [n_hyper][n_hyper]: inverse Schur complement
   nre::DevBuf cg_z, pc_gz, pc_part;
+  nre::DevBuf pc_tmp, pc_eye, pc_dG;  // preconditioner set-up scratch
+  nre::DevBuf pc_invD, pc_e;          // per pixel: 1 / D and A xi_p / D
+  nre::DevBuf pc_Gt;                  // float [n_bins][n_hyper]: G transposed
 };
 
 namespace nre {
@@ -47,8 +51,11 @@ namespace nre {
 // power model, the plan's per-pixel spectrum for the fixed kinds.
 template <typename T>
 AmpView<T> metric_view(const nre_metric* m);
-// out = v + J^T (w * J v) for a batch (dtype-dispatched inside).
-int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st);
+// out = v + J^T (w * J v) for a batch (dtype-dispatched inside).  With `dot`
+// (correlated field only) also the inner products v . out as partials
+// dot[b * kDotStride + i], whose sum over i is the product of system b.
+int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st,
+                      double* dot = nullptr);
 // ICR model hooks (icr.cu).
 int icr_metric_setup(nre_metric* m, cudaStream_t st);
 int icr_metric_apply(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st);
@@ -58,4 +65,25 @@ int icr_layout(const nre_icr_plan* p, int64_t* n_out, int64_t* latent, int64_t* 
 // Preconditioned CG (pcg.cu), used by cg_solve when m->precond != NRE_PRECOND_NONE.
 int pcg_solve_impl(nre_metric* m, const void* b, void* x, int batch, double rtol, int maxiter,
                    int* iters_out, double* relres_out, cudaStream_t st);
+
+// CG in pieces (cg.cu / pcg.cu), for callers that advance many solves at once
+// without waiting on each: cg_begin enqueues x = 0, r = b and the initial
+// scalars; cg_iterate enqueues `iters` iterations; neither synchronises.  The
+// per-system scalars live on the device in m->cg_sc, CG_SC_N doubles per
+// system, with the entries below (rr = r.r, bb = b.b, active = 1 while the
+// system runs, iters = iterations taken).  cg_read_scalars copies them to
+// m->cg_host and waits; cg_report turns them into iterations / relres and
+// the NRE_ENOTCONV status.
+enum { CG_SC_RR = 0, CG_SC_BB = 1, CG_SC_ACTIVE = 4, CG_SC_ITERS = 5, CG_SC_N = 8 };
+int cg_begin(nre_metric* m, const void* b, void* x, int batch, double rtol, cudaStream_t st);
+int cg_iterate(nre_metric* m, void* x, int batch, int iters, double rtol, cudaStream_t st);
+int pcg_begin(nre_metric* m, const void* b, void* x, int batch, double rtol, cudaStream_t st);
+int pcg_iterate(nre_metric* m, void* x, int batch, int iters, double rtol, cudaStream_t st);
+int cg_read_scalars(nre_metric* m, int batch, cudaStream_t st);
+bool cg_any_active(const nre_metric* m, int batch);
+int cg_report(const nre_metric* m, int batch, double rtol, int maxiter, int* iters_out, double* relres_out,
+              const char* what);
+// Recompute the metric's expansion-point data (w, amplitude state, per-pixel
+// tables) at a new xi_p (device, [latent]) in the buffers it already owns.
+int metric_relinearize(nre_metric* m, const void* xi_p, cudaStream_t st);
 }  // namespace nre

@@ -20,13 +20,15 @@
 #include <vector>
 
 #include "metric_internal.cuh"
+#include "regfft.cuh"
 
 using namespace nre;
 
 namespace {
 
 constexpr int PC_THREADS = 256;
-enum { SC_RR = 0, SC_BB = 1, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = 4, SC_ITERS = 5, SC_N = 8 };
+enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
+       SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
 int pc_blocks(int64_t n) {
   int64_t nb = (n + PC_THREADS * 8 - 1) / (PC_THREADS * 8);
@@ -37,13 +39,16 @@ int pc_blocks(int64_t n) {
 
 template <typename T>
 struct PCArgs {
-  int64_t N;          // field entries (the rest of the latent vector is hyper)
-  double c;           // N * mean(w)
-  AmpView<T> av;      // amplitude at the expansion point
-  const T* xi_p;      // expansion point (field)
-  int nb;             // bins (0: fixed amplitude, no hyper block)
-  double* bin_part;   // [B][gridDim.x][nb] partial sums t_b
-  const double* gz;   // [B][nb]
+  int64_t N;            // field entries (the rest of the latent vector is hyper)
+  double c;             // N * mean(w)
+  AmpView<T> av;        // amplitude at the expansion point (set-up only)
+  const T* xi_p;        // expansion point (set-up only)
+  const T* invD;        // [N] 1 / D_k = 1 / (1 + c A_k^2)
+  const T* e;           // [N] A_k xi_p[k] / D_k (nb > 0)
+  const int16_t* bpix;  // [N] log-|k| bin (nb > 0)
+  int nb;               // bins (0: fixed amplitude, no hyper block)
+  double* bin_part;     // [B][gridDim.x][nb] partial sums t_b
+  const double* gz;     // [B][nb]
 };
 
 __device__ void partial_out(double acc, double* part) {
@@ -52,93 +57,165 @@ __device__ void partial_out(double acc, double* part) {
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
-// Bins t_b += A_k xi_p[k] r_k / D_k of the field entries of r (per-CTA
-// histogram in shared memory, one partial per CTA).
+// 16-byte vector of T.
 template <typename T>
-__device__ void bins_of(const PCArgs<T>& pc, int b, const T* r, int64_t S, double* hist) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pc.N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int bn = pc.av.bin(i);
-    if (bn < 0) continue;
-    const T A = pc.av.amp(0, i, bn);
-    const T D = T(1) + T(pc.c) * A * A;
-    atomicAdd(&hist[bn], double(A * pc.xi_p[i] * r[b * S + i] / D));
+struct alignas(16) PV {
+  static constexpr int W = 16 / sizeof(T);
+  T e[W];
+};
+template <typename T>
+__device__ __forceinline__ PV<T> ldp(const T* p) { return *reinterpret_cast<const PV<T>*>(p); }
+template <typename T>
+__device__ __forceinline__ void stp(T* p, const PV<T>& v) { *reinterpret_cast<PV<T>*>(p) = v; }
+
+// Grid-stride loop of the CTAs of system blockIdx.y over the n entries in
+// vectors of W = 16 / sizeof(T); the trip count is uniform over the block
+// (the warp reductions of the bins need whole warps).  f(i, full) handles
+// entries i .. i+W-1 (full) or the entries i.. below n (tail; i may be >= n).
+template <typename T, class F>
+__device__ __forceinline__ void for_pv(int64_t n, F f) {
+  constexpr int W = PV<T>::W;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * W;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * W; base < n; base += step) {
+    const int64_t i = base + (int64_t)threadIdx.x * W;
+    f(i, i + W <= n);
   }
 }
 
+// t_b += e_k v_k for the W entries from i (field entries only: N is a multiple
+// of W, so a vector is all field or all hyper).  Called by every lane.
+template <typename T>
+__device__ __forceinline__ void bins_add(const PCArgs<T>& pc, int64_t i, const T (&v)[PV<T>::W], double* hist) {
+  constexpr int W = PV<T>::W;
+  int key[W];
+  T val[W];
+  const bool in = i + W <= pc.N;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    key[k] = in ? (int)__ldg(&pc.bpix[i + k]) : -1;
+    val[k] = in ? __ldg(&pc.e[i + k]) * v[k] : T(0);
+  }
+  add_slots<W, T>(key, val, hist);
+}
+
+template <typename T>
+__device__ __forceinline__ void bins_out(const PCArgs<T>& pc, int b, const double* hist) {
+  __syncthreads();
+  double* dst = pc.bin_part + ((int64_t)b * gridDim.x + blockIdx.x) * pc.nb;
+  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) dst[i] = hist[i];
+}
+
+// x = 0, r = b; partials of r.r and of the bins of r.
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T* r, int64_t n, int64_t S,
                                                         double* rr_part, PCArgs<T> pc) {
   extern __shared__ double hist[];
+  constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
   for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T v = bsrc[off + i];
-    x[off + i] = T(0);
-    r[off + i] = v;
-    acc += double(v * v);
-  }
-  if (pc.nb > 0) bins_of(pc, b, bsrc, S, hist);
+  for_pv<T>(n, [&](int64_t i, bool full) {
+    T v[W];
+    T run = T(0);
+    if (full) {
+      const PV<T> bv = ldp(bsrc + off + i);
+      PV<T> z;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        v[k] = bv.e[k];
+        z.e[k] = T(0);
+        run += v[k] * v[k];
+      }
+      stp(x + off + i, z);
+      stp(r + off + i, bv);
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        v[k] = T(0);
+        if (i + k < n) {
+          v[k] = bsrc[off + i + k];
+          x[off + i + k] = T(0);
+          r[off + i + k] = v[k];
+          run += v[k] * v[k];
+        }
+      }
+    }
+    acc += double(run);
+    if (pc.nb > 0) bins_add(pc, i, v, hist);
+  });
   partial_out(acc, rr_part);
-  __syncthreads();
-  if (pc.nb > 0) {
-    double* dst = pc.bin_part + ((int64_t)b * gridDim.x + blockIdx.x) * pc.nb;
-    for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) dst[i] = hist[i];
-  }
+  if (pc.nb > 0) bins_out(pc, b, hist);
 }
 
-// alpha = r.z / p.q; x += alpha p; r -= alpha q; partials of r.r and of the bins.
+// alpha = r.z / p.q (p.q from npq partials per system); x += alpha p;
+// r -= alpha q; partials of r.r and of the bins of r.
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* p, const T* q, int64_t n,
                                                           int64_t S, const double* sc, const double* pq_part,
-                                                          double* rr_part, PCArgs<T> pc) {
+                                                          int npq, double* rr_part, PCArgs<T> pc) {
   extern __shared__ double hist[];
-  const int b = blockIdx.y, nblk = gridDim.x;
+  constexpr int W = PV<T>::W;
+  const int b = blockIdx.y;
   for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
   const double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
-  double pq = 0.0;
-  for (int i = 0; i < nblk; ++i) pq += pq_part[b * nblk + i];
+  const double pq = block_sum_array(pq_part + (int64_t)b * npq, npq);
   const T alpha = T(active && pq != 0.0 ? c[SC_RZ] / pq : 0.0);
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
-  T run = T(0);
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = r[off + i];
-    if (active) {
-      x[off + i] += alpha * p[off + i];
-      ri -= alpha * q[off + i];
-      r[off + i] = ri;
+  for_pv<T>(n, [&](int64_t i, bool full) {
+    T v[W];
+    T run = T(0);
+    if (full) {
+      PV<T> ri = ldp(r + off + i);
+      if (active) {
+        PV<T> xi = ldp(x + off + i);
+        const PV<T> pi = ldp(p + off + i), qi = ldp(q + off + i);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          xi.e[k] += alpha * pi.e[k];
+          ri.e[k] -= alpha * qi.e[k];
+        }
+        stp(x + off + i, xi);
+        stp(r + off + i, ri);
+      }
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        v[k] = ri.e[k];
+        run += v[k] * v[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        v[k] = T(0);
+        if (i + k < n) {
+          T ri = r[off + i + k];
+          if (active) {
+            x[off + i + k] += alpha * p[off + i + k];
+            ri -= alpha * q[off + i + k];
+            r[off + i + k] = ri;
+          }
+          v[k] = ri;
+          run += ri * ri;
+        }
+      }
     }
-    run += ri * ri;
-    if (++cnt == 8) {
-      acc += double(run);
-      run = T(0);
-      cnt = 0;
-    }
-  }
-  acc += double(run);
-  __syncthreads();
-  if (pc.nb > 0) bins_of(pc, b, r, S, hist);
+    acc += double(run);
+    if (pc.nb > 0) bins_add(pc, i, v, hist);
+  });
   partial_out(acc, rr_part);
-  __syncthreads();
-  if (pc.nb > 0) {
-    double* dst = pc.bin_part + ((int64_t)b * gridDim.x + blockIdx.x) * pc.nb;
-    for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) dst[i] = hist[i];
-  }
+  if (pc.nb > 0) bins_out(pc, b, hist);
 }
 
 // Hyper block of the preconditioner, one CTA per system:
-// z_h = S^-1 (r_h - c G^T t), g = G z_h.
+// z_h = S^-1 (r_h - c G t), gz = G^T z_h  (G [nh][nb], Gt = G^T [nb][nh]).
 template <typename T>
 __global__ void k_pcg_hyper(const T* r, T* z, int64_t S, int64_t N, int nh, int nb, double c,
-                            const float* G, const float* Sinv, const double* bin_part, int nparts,
-                            double* gz) {
+                            const float* G, const float* Gt, const float* Sinv, const double* bin_part,
+                            int nparts, double* gz) {
   extern __shared__ float sh[];
   float* t = sh;        // [nb]
   float* u = t + nb;    // [nh]
@@ -153,53 +230,97 @@ __global__ void k_pcg_hyper(const T* r, T* z, int64_t S, int64_t N, int nh, int 
   __syncthreads();
   const T* rh = r + (int64_t)b * S + N;
   for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-    float s = 0.f;
-    const float* g = G + (int64_t)h * nb;
-    for (int i = 0; i < nb; ++i) s += g[i] * t[i];
-    u[h] = float(rh[h]) - float(c) * s;
+    float s0 = 0.f, s1 = 0.f;
+    int i = 0;
+    for (; i + 1 < nb; i += 2) {
+      s0 += __ldg(&Gt[(int64_t)i * nh + h]) * t[i];
+      s1 += __ldg(&Gt[(int64_t)(i + 1) * nh + h]) * t[i + 1];
+    }
+    if (i < nb) s0 += __ldg(&Gt[(int64_t)i * nh + h]) * t[i];
+    u[h] = float(rh[h]) - float(c) * (s0 + s1);
   }
   __syncthreads();
   T* zo = z + (int64_t)b * S + N;
   for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nh; ++k) s += Sinv[(int64_t)k * nh + h] * u[k];  // S^-1 symmetric
-    zh[h] = s;
-    zo[h] = T(s);
+    float s0 = 0.f, s1 = 0.f;
+    int k = 0;
+    for (; k + 1 < nh; k += 2) {  // S^-1 symmetric: column h read as row h
+      s0 += __ldg(&Sinv[(int64_t)k * nh + h]) * u[k];
+      s1 += __ldg(&Sinv[(int64_t)(k + 1) * nh + h]) * u[k + 1];
+    }
+    if (k < nh) s0 += __ldg(&Sinv[(int64_t)k * nh + h]) * u[k];
+    zh[h] = s0 + s1;
+    zo[h] = T(s0 + s1);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    float s = 0.f;
-    for (int h = 0; h < nh; ++h) s += G[(int64_t)h * nb + i] * zh[h];
-    gz[(int64_t)b * nb + i] = s;
+    float s0 = 0.f, s1 = 0.f;
+    int h = 0;
+    for (; h + 1 < nh; h += 2) {
+      s0 += __ldg(&G[(int64_t)h * nb + i]) * zh[h];
+      s1 += __ldg(&G[(int64_t)(h + 1) * nb + i]) * zh[h + 1];
+    }
+    if (h < nh) s0 += __ldg(&G[(int64_t)h * nb + i]) * zh[h];
+    gz[(int64_t)b * nb + i] = s0 + s1;
   }
 }
 
-// Field block z_f = (r_f - c A xi_p g_bin) / D; partials of r.z over the whole
+// Field block z_f = r_f / D - c e gz[bin] ; partials of r.z over the whole
 // latent vector (the hyper part of z was written by k_pcg_hyper).  With
 // `init`, also p = z.
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_pcg_z(const T* r, T* z, T* p, int64_t n, int64_t S,
                                                      double* rz_part, PCArgs<T> pc, int init) {
+  __shared__ float sgz[1024];
+  constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
+  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) sgz[i] = float(pc.c * pc.gz[(int64_t)b * pc.nb + i]);
+  __syncthreads();
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T ri = r[off + i];
-    T zi;
-    if (i < pc.N) {
-      const int bn = pc.av.binned() ? pc.av.bin(i) : -1;
-      const T A = pc.av.amp(0, i, bn);
-      const T D = T(1) + T(pc.c) * A * A;
-      T num = ri;
-      if (bn >= 0 && pc.nb > 0) num -= T(pc.c) * A * pc.xi_p[i] * T(pc.gz[(int64_t)b * pc.nb + bn]);
-      zi = num / D;
-      z[off + i] = zi;
+  for_pv<T>(n, [&](int64_t i, bool full) {
+    T run = T(0);
+    if (full && i + W <= pc.N) {
+      const PV<T> ri = ldp(r + off + i), id = ldp(pc.invD + i);
+      PV<T> zi;
+      if (pc.nb > 0) {
+        const PV<T> ei = ldp(pc.e + i);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const int bn = __ldg(&pc.bpix[i + k]);
+          zi.e[k] = ri.e[k] * id.e[k] - (bn >= 0 ? ei.e[k] * T(sgz[bn]) : T(0));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) zi.e[k] = ri.e[k] * id.e[k];
+      }
+      stp(z + off + i, zi);
+      if (init) stp(p + off + i, zi);
+#pragma unroll
+      for (int k = 0; k < W; ++k) run += ri.e[k] * zi.e[k];
     } else {
-      zi = z[off + i];
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const int64_t j = i + k;
+        if (j >= n) continue;
+        const T ri = r[off + j];
+        T zi;
+        if (j < pc.N) {
+          zi = ri * pc.invD[j];
+          if (pc.nb > 0) {
+            const int bn = pc.bpix[j];
+            if (bn >= 0) zi -= pc.e[j] * T(sgz[bn]);
+          }
+          z[off + j] = zi;
+        } else {
+          zi = z[off + j];
+        }
+        if (init) p[off + j] = zi;
+        run += ri * zi;
+      }
     }
-    if (init) p[off + i] = zi;
-    acc += double(ri * zi);
-  }
+    acc += double(run);
+  });
   partial_out(acc, rz_part);
 }
 
@@ -225,15 +346,25 @@ __global__ void k_pcg_start(double* sc, const double* rr_part, const double* rz_
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_pcg_pupdate(T* p, const T* z, int64_t n, int64_t S,
                                                            const double* sc, const double* rz_part, int nblk) {
+  constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
   if (c[SC_ACTIVE] == 0.0) return;
-  double rz = 0.0;
-  for (int i = 0; i < nblk; ++i) rz += rz_part[b * nblk + i];
+  const double rz = block_sum_array(rz_part + (int64_t)b * nblk, nblk);
   const T beta = T(rz / c[SC_RZ]);
   const int64_t off = (int64_t)b * S;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[off + i] = z[off + i] + beta * p[off + i];
+  for_pv<T>(n, [&](int64_t i, bool full) {
+    if (full) {
+      const PV<T> zi = ldp(z + off + i);
+      PV<T> pi = ldp(p + off + i);
+#pragma unroll
+      for (int k = 0; k < W; ++k) pi.e[k] = zi.e[k] + beta * pi.e[k];
+      stp(p + off + i, pi);
+    } else {
+      for (int k = 0; k < W; ++k)
+        if (i + k < n) p[off + i + k] = z[off + i + k] + beta * p[off + i + k];
+    }
+  });
 }
 
 __global__ void k_pcg_finish(double* sc, const double* rr_part, const double* rz_part, int nblk, double rtol) {
@@ -253,22 +384,37 @@ __global__ void k_pcg_finish(double* sc, const double* rr_part, const double* rz
   if (rtol > 0.0 && sqrt(rr) <= rtol * sqrt(c[SC_BB])) c[SC_ACTIVE] = 0.0;
 }
 
+// Partials of p.q.
 template <typename T>
-__global__ void k_dot_p(const T* a, const T* q, int64_t n, int64_t S, double* part) {
+__global__ void __launch_bounds__(PC_THREADS) k_dot_p(const T* a, const T* q, int64_t n, int64_t S, double* part) {
+  constexpr int W = PV<T>::W;
   const int64_t off = (int64_t)blockIdx.y * S;
   double acc = 0.0;
-  T run = T(0);
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    run += a[off + i] * q[off + i];
-    if (++cnt == 8) {
-      acc += double(run);
-      run = T(0);
-      cnt = 0;
+  for_pv<T>(n, [&](int64_t i, bool full) {
+    T run = T(0);
+    if (full) {
+      const PV<T> u = ldp(a + off + i), v = ldp(q + off + i);
+#pragma unroll
+      for (int k = 0; k < W; ++k) run += u.e[k] * v.e[k];
+    } else {
+      for (int k = 0; k < W; ++k)
+        if (i + k < n) run += a[off + i + k] * q[off + i + k];
     }
-  }
-  acc += double(run);
+    acc += double(run);
+  });
   partial_out(acc, part);
+}
+
+// Per-pixel preconditioner coefficients at the expansion point.
+template <typename T>
+__global__ void k_pc_pix(PCArgs<T> pc, T* invD, T* e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pc.N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int bn = pc.av.binned() ? pc.av.bin(i) : -1;
+    const double A = double(pc.av.amp(0, i, bn));
+    const double D = 1.0 + pc.c * A * A;
+    invD[i] = T(1.0 / D);
+    if (e) e[i] = (bn >= 0 && pc.nb > 0) ? T(A * double(pc.xi_p[i]) / D) : T(0);
+  }
 }
 
 // U_b = sum_{k in b} xi_p[k]^2 / D_k (bins of the expansion point), and
@@ -308,6 +454,9 @@ PCArgs<T> pc_args(nre_metric* m) {
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   a.av = metric_view<T>(m);
   a.nb = model ? p->n_bins : 0;
+  a.invD = m->pc_invD.as<T>();
+  a.e = model ? m->pc_e.as<T>() : nullptr;
+  a.bpix = model ? m->bpix.as<int16_t>() : nullptr;
   return a;
 }
 
@@ -326,18 +475,24 @@ bool spd_inverse(std::vector<double>& A, int n, std::vector<double>& inv) {
       L[(size_t)i * n + j] = t / d;
     }
   }
+  std::vector<double> Lt((size_t)n * n);  // L^T, so both substitutions read rows
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k <= i; ++k) Lt[(size_t)k * n + i] = L[(size_t)i * n + k];
   inv.assign((size_t)n * n, 0.0);
   std::vector<double> col(n);
   for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < c; ++i) col[i] = 0.0;  // L^-1 e_c vanishes above c
+    for (int i = c; i < n; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * col[k];
-      col[i] = s / L[(size_t)i * n + i];
+      const double* Li = &L[(size_t)i * n];
+      for (int k = c; k < i; ++k) s -= Li[k] * col[k];
+      col[i] = s / Li[i];
     }
     for (int i = n - 1; i >= 0; --i) {
       double s = col[i];
-      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * col[k];
-      col[i] = s / L[(size_t)i * n + i];
+      const double* Lti = &Lt[(size_t)i * n];
+      for (int k = i + 1; k < n; ++k) s -= Lti[k] * col[k];
+      col[i] = s / Lti[i];
     }
     for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = col[i];
   }
@@ -350,8 +505,8 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   const int64_t N = p->N;
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   const int nb = model ? p->n_bins : 0, nh = model ? p->n_hyper : 0;
-  DevBuf dbuf;
-  NRE_TRY(dbuf.alloc((size_t)(1 + nb) * sizeof(double)));
+  DevBuf& dbuf = m->pc_tmp;  // metric-owned, so a re-setup allocates nothing
+  NRE_TRY(ensure(dbuf, (size_t)(1 + nb) * sizeof(double)));
   NRE_TRY_CUDA(cudaMemsetAsync(dbuf.p, 0, (size_t)(1 + nb) * sizeof(double), st));
   // pass 1: mean weight
   PCArgs<T> a = pc_args<T>(m);
@@ -366,6 +521,14 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   NRE_TRY_CUDA(cudaStreamSynchronize(st));
   m->pc_c = wsum;  // N * mean(w) = sum(w)
   m->pc_nh = nh;
+  // per-pixel coefficients 1 / D and A xi_p / D
+  NRE_TRY(ensure(m->pc_invD, (size_t)N * sizeof(T)));
+  if (model) NRE_TRY(ensure(m->pc_e, (size_t)N * sizeof(T)));
+  a.c = m->pc_c;
+  prof_begin("pc_setup", (double)N * 3 * sizeof(T), st);
+  k_pc_pix<T><<<304, PC_THREADS, 0, st>>>(a, m->pc_invD.as<T>(), model ? m->pc_e.as<T>() : nullptr);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
   if (!model) return NRE_OK;
   // pass 2: U_b with the final c
   NRE_TRY_CUDA(cudaMemsetAsync(dbuf.p, 0, (size_t)(1 + nb) * sizeof(double), st));
@@ -378,36 +541,101 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   // amplitude Jacobian G[h][b] = dA_b / dh: JVPs along the unit vectors
   std::vector<T> eye((size_t)nh * nh, T(0));
   for (int h = 0; h < nh; ++h) eye[(size_t)h * nh + h] = T(1);
-  DevBuf deye, dG;
-  NRE_TRY(deye.upload(eye.data(), eye.size() * sizeof(T)));
-  NRE_TRY(dG.alloc((size_t)nh * nb * sizeof(double)));
+  DevBuf& deye = m->pc_eye;
+  DevBuf& dG = m->pc_dG;
+  NRE_TRY(ensure(deye, eye.size() * sizeof(T)));
+  NRE_TRY_CUDA(cudaMemcpyAsync(deye.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  NRE_TRY(ensure(dG, (size_t)nh * nb * sizeof(double)));
   NRE_TRY(amp_jvp<T>(amp_prior_of(p), m->state.as<double>(), 0, deye.as<T>(), nh, dG.as<double>(), nh, st));
   std::vector<double> G((size_t)nh * nb), U(nb);
   NRE_TRY_CUDA(cudaMemcpyAsync(G.data(), dG.p, G.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   NRE_TRY_CUDA(cudaMemcpyAsync(U.data(), dbuf.as<double>() + 1, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   NRE_TRY_CUDA(cudaStreamSynchronize(st));
   // S = I + c G diag(U) G^T (G stored [h][b])
-  std::vector<double> S((size_t)nh * nh), Sinv;
+  std::vector<double> S((size_t)nh * nh), Sinv, GU((size_t)nh * nb);
   const double c = m->pc_c;
-  for (int i = 0; i < nh; ++i)
+  for (size_t i = 0; i < GU.size(); ++i) GU[i] = G[i] * U[i % nb];
+  for (int i = 0; i < nh; ++i) {
+    const double* gi = &GU[(size_t)i * nb];
     for (int j = 0; j <= i; ++j) {
+      const double* gj = &G[(size_t)j * nb];
       double s = 0.0;
-      for (int k = 0; k < nb; ++k) s += G[(size_t)i * nb + k] * U[k] * G[(size_t)j * nb + k];
+      for (int k = 0; k < nb; ++k) s += gi[k] * gj[k];
       S[(size_t)i * nh + j] = S[(size_t)j * nh + i] = c * s + (i == j ? 1.0 : 0.0);
     }
+  }
   if (!spd_inverse(S, nh, Sinv)) return set_error(NRE_EINVAL, "preconditioner Schur block is not positive definite");
-  std::vector<float> Gf(G.begin(), G.end()), Sf(Sinv.begin(), Sinv.end());
-  NRE_TRY(m->pc_G.upload(Gf.data(), Gf.size() * sizeof(float)));
-  NRE_TRY(m->pc_Sinv.upload(Sf.data(), Sf.size() * sizeof(float)));
+  std::vector<float> Gf(G.begin(), G.end()), Sf(Sinv.begin(), Sinv.end()), Gtf((size_t)nb * nh);
+  for (int h = 0; h < nh; ++h)
+    for (int k = 0; k < nb; ++k) Gtf[(size_t)k * nh + h] = Gf[(size_t)h * nb + k];
+  NRE_TRY(ensure(m->pc_G, Gf.size() * sizeof(float)));
+  NRE_TRY(ensure(m->pc_Gt, Gtf.size() * sizeof(float)));
+  NRE_TRY(ensure(m->pc_Sinv, Sf.size() * sizeof(float)));
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_G.p, Gf.data(), Gf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_Gt.p, Gtf.data(), Gtf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_Sinv.p, Sf.data(), Sf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  NRE_TRY_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  return NRE_OK;
+}
+
+// Workspace pointers and launch shapes of a preconditioned solve of B systems.
+template <typename T>
+struct PCGWork {
+  T *r, *p, *q, *z;
+  double *sc, *part_pq, *part_rr, *part_rz;
+  PCArgs<T> pc;
+  int nb, nh, nblk;
+  size_t hsm, hyp_sm;
+};
+
+template <typename T>
+PCGWork<T> pcg_work(nre_metric* m, int B) {
+  PCGWork<T> w;
+  nre_cf_plan* p = m->cf;
+  w.nb = m->pc_nh > 0 ? p->n_bins : 0;
+  w.nh = m->pc_nh;
+  w.nblk = pc_blocks(m->latent);
+  w.r = m->cg_r.as<T>();
+  w.p = m->cg_p.as<T>();
+  w.q = m->cg_q.as<T>();
+  w.z = m->cg_z.as<T>();
+  w.sc = m->cg_sc.as<double>();
+  w.part_pq = m->cg_part.as<double>();
+  w.part_rr = w.part_pq + (size_t)B * w.nblk;
+  w.part_rz = w.part_rr + (size_t)B * w.nblk;
+  w.pc = pc_args<T>(m);
+  w.pc.nb = w.nb;
+  w.pc.bin_part = w.nb > 0 ? m->pc_part.as<double>() : nullptr;
+  w.pc.gz = w.nb > 0 ? m->pc_gz.as<double>() : nullptr;
+  w.hsm = (size_t)(w.nb > 0 ? w.nb : 1) * sizeof(double);
+  w.hyp_sm = (size_t)(w.nb + 2 * w.nh) * sizeof(float);
+  return w;
+}
+
+// z = P r (and p = z on the first call).
+template <typename T>
+int pcg_precondition(nre_metric* m, const PCGWork<T>& w, int B, int init, cudaStream_t st) {
+  const int64_t n = m->latent, S = m->stride, N = m->cf->N;
+  const double vb = (double)B * n * sizeof(T);
+  if (w.nb > 0) {
+    prof_begin("pcg_hyper", (double)B * w.nh * sizeof(T) * 2, st);
+    k_pcg_hyper<T><<<B, 512, w.hyp_sm, st>>>(w.r, w.z, S, N, w.nh, w.nb, m->pc_c, m->pc_G.as<float>(),
+                                              m->pc_Gt.as<float>(), m->pc_Sinv.as<float>(), w.pc.bin_part,
+                                              w.nblk, m->pc_gz.as<double>());
+    prof_end(st);
+  }
+  prof_begin("pcg_z", (init ? 3.0 : 2.0) * vb + (double)N * sizeof(T), st);
+  k_pcg_z<T><<<dim3(w.nblk, B), PC_THREADS, 0, st>>>(w.r, w.z, w.p, n, S, w.part_rz, w.pc, init);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
   return NRE_OK;
 }
 
 template <typename T>
-int pcg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* iters_out,
-          double* relres_out, cudaStream_t st) {
+int pcg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_t st) {
   const int64_t n = m->latent, S = m->stride;
   nre_cf_plan* p = m->cf;
-  const int nb = m->pc_nh > 0 ? p->n_bins : 0, nh = m->pc_nh;
+  const int nb = m->pc_nh > 0 ? p->n_bins : 0;
   NRE_TRY(ensure(m->cg_r, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_p, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_q, (size_t)B * S * sizeof(T)));
@@ -415,93 +643,81 @@ int pcg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int*
   NRE_TRY(ensure(m->cg_sc, (size_t)B * SC_N * sizeof(double)));
   const int nblk = pc_blocks(n);
   NRE_TRY(ensure(m->cg_part, (size_t)3 * B * nblk * sizeof(double)));
+  NRE_TRY(ensure(m->cg_dot, (size_t)B * kDotStride * sizeof(double)));
   if (nb > 0) {
     NRE_TRY(ensure(m->pc_part, (size_t)B * nblk * nb * sizeof(double)));
     NRE_TRY(ensure(m->pc_gz, (size_t)B * nb * sizeof(double)));
   }
-  T* r = m->cg_r.as<T>();
-  T* pp = m->cg_p.as<T>();
-  T* q = m->cg_q.as<T>();
-  T* z = m->cg_z.as<T>();
-  double* sc = m->cg_sc.as<double>();
-  double* part_pq = m->cg_part.as<double>();
-  double* part_rr = part_pq + (size_t)B * nblk;
-  double* part_rz = part_rr + (size_t)B * nblk;
-  PCArgs<T> pc = pc_args<T>(m);
-  pc.nb = nb;
-  pc.bin_part = nb > 0 ? m->pc_part.as<double>() : nullptr;
-  pc.gz = nb > 0 ? m->pc_gz.as<double>() : nullptr;
-  const dim3 grid(nblk, B);
-  const size_t hsm = (size_t)(nb > 0 ? nb : 1) * sizeof(double);
-  const size_t hyp_sm = (size_t)(nb + 2 * nh) * sizeof(float);
+  const PCGWork<T> w = pcg_work<T>(m, B);
   const double vb = (double)B * n * sizeof(T);
-  auto precondition = [&](int init) -> int {
-    if (nb > 0) {
-      prof_begin("pcg_hyper", (double)B * nh * sizeof(T) * 2, st);
-      k_pcg_hyper<T><<<B, 256, hyp_sm, st>>>(r, z, S, p->N, nh, nb, m->pc_c, m->pc_G.as<float>(),
-                                             m->pc_Sinv.as<float>(), pc.bin_part, nblk, m->pc_gz.as<double>());
-      prof_end(st);
-    }
-    prof_begin("pcg_z", (init ? 3.0 : 2.0) * vb + (double)p->N * sizeof(T), st);
-    k_pcg_z<T><<<grid, PC_THREADS, 0, st>>>(r, z, pp, n, S, part_rz, pc, init);
-    prof_end(st);
-    NRE_CHECK_LAUNCH();
-    return NRE_OK;
-  };
   prof_begin("pcg_init", 3.0 * vb, st);
-  k_pcg_init<T><<<grid, PC_THREADS, hsm, st>>>(b, x, r, n, S, part_rr, pc);
+  k_pcg_init<T><<<dim3(nblk, B), PC_THREADS, w.hsm, st>>>(b, x, w.r, n, S, w.part_rr, w.pc);
   prof_end(st);
   NRE_CHECK_LAUNCH();
-  NRE_TRY(precondition(1));
+  NRE_TRY(pcg_precondition<T>(m, w, B, 1, st));
   prof_begin("cg_scalars", 0.0, st);
-  k_pcg_start<<<B, 32, 0, st>>>(sc, part_rr, part_rz, nblk, rtol);
+  k_pcg_start<<<B, 32, 0, st>>>(w.sc, w.part_rr, w.part_rz, nblk, rtol);
   prof_end(st);
-  m->cg_host.resize((size_t)B * SC_N);
-  const int check_every = 8;
-  for (int it = 0; it < maxiter; ++it) {
-    NRE_TRY(metric_apply_impl(m, pp, q, B, st));
-    prof_begin("cg_dot", 2 * vb, st);
-    k_dot_p<T><<<grid, PC_THREADS, 0, st>>>(pp, q, n, S, part_pq);
-    prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int pcg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t st) {
+  const int64_t n = m->latent, S = m->stride;
+  const PCGWork<T> w = pcg_work<T>(m, B);
+  const dim3 grid(w.nblk, B);
+  const double vb = (double)B * n * sizeof(T);
+  for (int it = 0; it < iters; ++it) {
+    // p.q comes fused with the metric product (kDotStride partials per system)
+    NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, m->cg_dot.as<double>()));
     prof_begin("pcg_update", 6 * vb, st);
-    k_pcg_update<T><<<grid, PC_THREADS, hsm, st>>>(x, r, pp, q, n, S, sc, part_pq, part_rr, pc);
+    k_pcg_update<T><<<grid, PC_THREADS, w.hsm, st>>>(x, w.r, w.p, w.q, n, S, w.sc, m->cg_dot.as<double>(),
+                                                      kDotStride, w.part_rr, w.pc);
     prof_end(st);
     NRE_CHECK_LAUNCH();
-    NRE_TRY(precondition(0));
+    NRE_TRY(pcg_precondition<T>(m, w, B, 0, st));
     prof_begin("cg_pupdate", 3 * vb, st);
-    k_pcg_pupdate<T><<<grid, PC_THREADS, 0, st>>>(pp, z, n, S, sc, part_rz, nblk);
+    k_pcg_pupdate<T><<<grid, PC_THREADS, 0, st>>>(w.p, w.z, n, S, w.sc, w.part_rz, w.nblk);
     prof_end(st);
     prof_begin("cg_scalars", 0.0, st);
-    k_pcg_finish<<<B, 32, 0, st>>>(sc, part_rr, part_rz, nblk, rtol);
+    k_pcg_finish<<<B, 32, 0, st>>>(w.sc, w.part_rr, w.part_rz, w.nblk, rtol);
     prof_end(st);
     NRE_CHECK_LAUNCH();
-    if (rtol > 0.0 && (it + 1) % check_every == 0 && it + 1 < maxiter) {
-      NRE_TRY_CUDA(cudaMemcpyAsync(m->cg_host.data(), sc, (size_t)B * SC_N * sizeof(double),
-                                   cudaMemcpyDeviceToHost, st));
-      NRE_TRY_CUDA(cudaStreamSynchronize(st));
-      bool any = false;
-      for (int i = 0; i < B; ++i) any |= m->cg_host[(size_t)i * SC_N + SC_ACTIVE] != 0.0;
-      if (!any) break;
+  }
+  return NRE_OK;
+}
+
+template <typename T>
+int pcg_t(nre_metric* m, const T* b, T* x, int B, double rtol, int maxiter, int* iters_out,
+          double* relres_out, cudaStream_t st) {
+  NRE_TRY(pcg_begin_t<T>(m, b, x, B, rtol, st));
+  const int check_every = 8;
+  for (int it = 0; it < maxiter; it += check_every) {
+    const int k = maxiter - it < check_every ? maxiter - it : check_every;
+    NRE_TRY(pcg_iter_t<T>(m, x, B, k, rtol, st));
+    if (rtol > 0.0 && it + k < maxiter) {
+      NRE_TRY(cg_read_scalars(m, B, st));
+      if (!cg_any_active(m, B)) break;
     }
   }
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->cg_host.data(), sc, (size_t)B * SC_N * sizeof(double),
-                               cudaMemcpyDeviceToHost, st));
-  NRE_TRY_CUDA(cudaStreamSynchronize(st));
-  bool conv = true;
-  for (int i = 0; i < B; ++i) {
-    const double* c = &m->cg_host[(size_t)i * SC_N];
-    const double rel = c[SC_BB] > 0 ? std::sqrt(c[SC_RR] / c[SC_BB]) : 0.0;
-    if (iters_out) iters_out[i] = (int)c[SC_ITERS];
-    if (relres_out) relres_out[i] = rel;
-    if (rtol > 0.0 && rel > rtol) conv = false;
-  }
-  if (!conv) return set_error(NRE_ENOTCONV, "PCG: some system missed rtol=%g within maxiter=%d", rtol, maxiter);
-  return NRE_OK;
+  NRE_TRY(cg_read_scalars(m, B, st));
+  return cg_report(m, B, rtol, maxiter, iters_out, relres_out, "PCG");
 }
 
 }  // namespace
 
 namespace nre {
+int pcg_begin(nre_metric* m, const void* b, void* x, int B, double rtol, cudaStream_t st) {
+  if (m->dtype == NRE_F64) return pcg_begin_t<double>(m, (const double*)b, (double*)x, B, rtol, st);
+  return pcg_begin_t<float>(m, (const float*)b, (float*)x, B, rtol, st);
+}
+
+int pcg_iterate(nre_metric* m, void* x, int B, int iters, double rtol, cudaStream_t st) {
+  if (m->dtype == NRE_F64) return pcg_iter_t<double>(m, (double*)x, B, iters, rtol, st);
+  return pcg_iter_t<float>(m, (float*)x, B, iters, rtol, st);
+}
+
 int pcg_solve_impl(nre_metric* m, const void* b, void* x, int batch, double rtol, int maxiter,
                    int* iters_out, double* relres_out, cudaStream_t st) {
   if (m->dtype == NRE_F64)

@@ -40,6 +40,13 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+std::atomic<long long>& dev_bytes() {
+  static std::atomic<long long> b{0};
+  return b;
+}
+
+void prof_add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void prof_begin(const char* name, double bytes, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
@@ -64,6 +71,12 @@ using namespace nre;
 extern "C" {
 
 unsigned long long nre_launch_count(void) { return g_launches.load(); }
+
+int nre_device_bytes(int64_t* bytes) {
+  if (!bytes) return set_error(NRE_EINVAL, "bytes must not be NULL");
+  *bytes = (int64_t)dev_bytes().load();
+  return NRE_OK;
+}
 
 int nre_prof_enable(int on) {
   g_on.store(on ? 1 : 0);

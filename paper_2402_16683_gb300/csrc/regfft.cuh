@@ -151,4 +151,23 @@ __device__ __forceinline__ void warp_run_add(int key, V val, double* hist) {
   if (tail && key >= 0) atomicAdd(&hist[key], double(val));
 }
 
+// Adds the contributions c[s] of slots with bins bn[s] (all into the same
+// histogram): slots sharing a bin are summed first, then each distinct bin is
+// reduced over the warp.  Must be called by all lanes of the warp.
+template <int S, typename V>
+__device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], double* hist) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    int key = bn[s];
+    V val = c[s];
+#pragma unroll
+    for (int s2 = 0; s2 < s; ++s2)
+      if (bn[s2] == bn[s]) key = -1;
+#pragma unroll
+    for (int s2 = s + 1; s2 < S; ++s2)
+      if (bn[s2] == bn[s]) val += c[s2];
+    if (s == 0 || __any_sync(0xffffffffu, key >= 0)) warp_run_add(key, val, hist);
+  }
+}
+
 }  // namespace nre

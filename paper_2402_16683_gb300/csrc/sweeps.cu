@@ -102,10 +102,9 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
         T V[2][2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const int s0 = f0 ? 1 - s : s;
 #pragma unroll
           for (int p = 0; p < 2; ++p)
-            V[s][p] = half * (R[s][p] + R[s0][p] + R[s][1 - p] - R[s0][1 - p]);
+            V[s][p] = half * (R[s][p] + pick2(R, s, f0, p) + R[s][1 - p] - pick2(R, s, f0, 1 - p));
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -123,12 +122,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
         T V[4][2];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          const int s0 = f0 ? (s ^ 1) : s;
-          const int s1 = f1 ? (s ^ 2) : s;
-          const int s01 = f1 ? (s0 ^ 2) : s0;
 #pragma unroll
           for (int p = 0; p < 2; ++p)
-            V[s][p] = half * (R[s0][p] + R[s1][p] + R[s][1 - p] - R[s01][1 - p]);
+            V[s][p] = half * (pick4(R, s, f0, false, p) + pick4(R, s, false, f1, p) + R[s][1 - p] -
+                              pick4(R, s, f0, f1, 1 - p));
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -315,9 +312,31 @@ int col_sweep_reg(ColArgs<T> a, int64_t outer, bool mid, int B, bool bins, int* 
   return NRE_OK;
 }
 
+// Partials of sum(base * y) over the N outputs of each sample (the fused inner
+// product when the row kernel cannot produce it), in the Epi::dot layout.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_fallback(const T* base, int64_t bs, const T* y, int64_t ys,
+                                                     int64_t N, double* dot) {
+  const int b = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    acc += double(base[b * bs + i] * y[b * ys + i]);
+  __shared__ double red[8];
+  const double t = block_sum(acc, red);
+  double* dp = dot + (int64_t)b * kDotStride;
+  if (threadIdx.x == 0) dp[blockIdx.x] = t;
+  if (blockIdx.x == 0)
+    for (int i = gridDim.x + threadIdx.x; i < kDotStride; i += blockDim.x) dp[i] = 0.0;
+}
+
+template <typename T>
+int row_sweep_dot(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
+                  const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st);
+
 template <typename T>
 int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
               const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st) {
+  if (epi.dot != nullptr) return row_sweep_dot<T>(p, B, pro, epi, mid, partials, nparts, st);
   RowArgs<T> a{};
   const int D = p->ndim;
   a.L = p->n[D - 1];
@@ -421,6 +440,47 @@ Epi<T> epi_buf(T* y, int64_t ys) {
   r.y = y;
   r.ys = ys;
   return r;
+}
+
+// row_sweep with the fused inner product: the register kernel of a 2-D / 3-D
+// grid accumulates it in its epilogue; otherwise a separate reduction follows.
+template <typename T>
+int row_sweep_dot(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
+                  const Mid<T>* mid, double* partials, int* nparts, cudaStream_t st) {
+  Epi<T> e = epi;
+  double* dot = e.dot;
+  const int64_t N = p->N;
+  bool fused = false;
+  if (p->ndim >= 2) {
+    RowArgs<T> a{};
+    const int D = p->ndim;
+    a.L = p->n[D - 1];
+    a.log2L = p->l2[D - 1];
+    a.log2Lmax = p->log2Lmax;
+    a.tw = p->tw.as<typename CplxT<T>::type>();
+    a.pm = D;
+    a.B = B;
+    a.pro = pro;
+    a.epi = e;
+    if (mid) a.mid = *mid;
+    a.nb = p->n_bins > 0 ? p->n_bins : 1;
+    a.partials = partials;
+    a.grows = p->grows.as<int>();
+    a.gflags = p->gflags.as<int>();
+    a.n_units = p->n_groups;
+    NRE_TRY(row_sweep_reg<T>(a, mid != nullptr, B, e.mode == EPI_AMP && e.bins, nparts, st, N, &fused));
+  }
+  if (!fused) {
+    e.dot = nullptr;
+    NRE_TRY(row_sweep<T>(p, B, pro, e, mid, partials, nparts, st));
+    int64_t gx = (N + 256 * 8 - 1) / (256 * 8);
+    if (gx > kMaxGridX) gx = kMaxGridX;
+    prof_begin("dot_fallback", (double)B * N * 2 * sizeof(T), st);
+    k_dot_fallback<T><<<dim3((unsigned)gx, B), 256, 0, st>>>(e.base, e.bs, e.y, e.ys, N, dot);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+  }
+  return NRE_OK;
 }
 
 }  // namespace

@@ -76,25 +76,6 @@ struct LineSync {
   }
 };
 
-// Adds the contributions c[s] of slots with bins bn[s] (all into the same
-// histogram): slots sharing a bin are summed first, then each distinct bin is
-// reduced over the warp.  Must be called by all lanes of the warp.
-template <int S, typename V>
-__device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], double* hist) {
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    int key = bn[s];
-    V val = c[s];
-#pragma unroll
-    for (int s2 = 0; s2 < s; ++s2)
-      if (bn[s2] == bn[s]) key = -1;
-#pragma unroll
-    for (int s2 = s + 1; s2 < S; ++s2)
-      if (bn[s2] == bn[s]) val += c[s2];
-    if (s == 0 || __any_sync(0xffffffffu, key >= 0)) warp_run_add(key, val, hist);
-  }
-}
-
 // Per-bin tables of one sample in shared memory: A (from the per-bin model
 // amplitude) into sA and the tangent's dA into sdA.  Returns whether the
 // prologue / epilogue should read them (*use_dA: the dA table).  Called by all
@@ -167,33 +148,26 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
 
-  // slot sl of unit `unit`: sample and row, or false if absent
-  auto slot_of = [&](int unit, int sl, int& samp, int& row) -> bool {
-    samp = 0;
-    row = 0;
-    if (unit >= a.n_units) return false;
-    if (PM == 1) {
-      samp = 2 * unit + sl;
-      return samp < a.B;
-    }
-    samp = bsample;
-    row = a.grows[unit * SLOTS + sl];
-    return true;
-  };
   auto issue = [&](int ug, int buf) {
     T* dst = stage + buf * SM::STGA;
     T* bdst = bstage + buf * SM::XSZ;
     for (int c = threadIdx.x; c < NU * SLOTS * CPR; c += blockDim.x) {
       const int rr = c / CPR, j = c - rr * CPR;
       const int uu = rr / SLOTS, sl = rr - uu * SLOTS;
-      int samp, row;
-      if (!slot_of(ug + uu, sl, samp, row)) continue;
+      const int un = ug + uu;
+      if (un >= a.n_units) continue;
+      const int samp = PM == 1 ? 2 * un + sl : bsample;
+      if (PM == 1 && samp >= a.B) continue;
+      const int row = PM == 1 ? 0 : __ldg(&a.grows[un * SLOTS + sl]);
       const int64_t g = (int64_t)row * L + j * CH;
       cp_async16(dst + rr * L + j * CH, a.pro.x + samp * a.pro.xs + g);
       if (sbase) cp_async16(bdst + rr * L + j * CH, a.epi.base + samp * a.epi.bs + g);
     }
   };
 
+  // fused inner product sum(base * y) of a metric product (see Epi::dot)
+  const bool dot = PM >= 2 && epi.dot != nullptr;
+  double dacc = 0.0;
   const int ustride = gridDim.x * NU;
   int u0 = blockIdx.x * NU;
   if (u0 < a.n_units) issue(u0, 0);
@@ -205,11 +179,21 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
     cp_wait<1>();
     __syncthreads();
     const int unit = u0 + u;
+    const bool valid = unit < a.n_units;
     int row[SLOTS], samp[SLOTS];
     bool sval[SLOTS];
 #pragma unroll
-    for (int sl = 0; sl < SLOTS; ++sl) sval[sl] = slot_of(unit, sl, samp[sl], row[sl]);
-    const bool valid = sval[0];
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      if (PM == 1) {
+        samp[sl] = 2 * unit + sl;
+        row[sl] = 0;
+        sval[sl] = valid && samp[sl] < a.B;
+      } else {
+        samp[sl] = bsample;
+        row[sl] = valid ? __ldg(&a.grows[unit * SLOTS + sl]) : 0;
+        sval[sl] = valid;
+      }
+    }
     const T* X = stage + cur * SM::STGA + u * SLOTS * L;
     C v[LPU][8];
     if constexpr (PK == SK_GEN) {
@@ -276,6 +260,73 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
     }
     reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
     const T* BV = bstage + cur * SM::XSZ + u * SLOTS * L;
+    if constexpr (EK == SK_TAB && PM >= 2) {
+      // The metric's epilogue in two phases so the per-pixel loads (bins,
+      // expansion point) are all in flight before they are used:
+      // A) loads and the P combination, B) stores and bin reductions.
+      const int16_t* bp = epi.av.bpix;
+      const T* xp = epi.xi_p + (int64_t)bsample * epi.ps;
+      T* yo = epi.y + (int64_t)bsample * epi.ys;
+      const int fl = valid ? __ldg(&a.gflags[unit]) : 0;
+      const bool f0 = fl & 1, f1 = fl & 2;
+      const T half = T(0.5), a0 = epi.av.a0t;
+      T dsum = T(0);
+      constexpr int CH = 2;  // columns per load/store phase pair (register budget)
+#pragma unroll
+      for (int c0 = 0; c0 < 8; c0 += CH) {
+        int bn[CH][SLOTS];
+        T xv[CH][SLOTS], val[CH][SLOTS];
+#pragma unroll
+        for (int s = 0; s < CH; ++s)
+#pragma unroll
+          for (int sl = 0; sl < SLOTS; ++sl) {
+            const int f = row[sl] * L + t + T8 * (c0 + s);
+            bn[s][sl] = valid ? (int)__ldg(&bp[f]) : -1;
+            xv[s][sl] = (valid && bins) ? __ldg(&xp[f]) : T(0);
+          }
+#pragma unroll
+        for (int s = 0; s < CH; ++s) {
+          if constexpr (PM == 2) {
+            T R[2][2];
+            hartley_unpack<T>(v[0][c0 + s], zm[0][c0 + s], R[0], R[1]);
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+              val[s][sl] = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
+            }
+          } else {
+            T R[4][2];
+            hartley_unpack<T>(v[0][c0 + s], zm[0][c0 + s], R[0], R[1]);
+            hartley_unpack<T>(v[1][c0 + s], zm[1][c0 + s], R[2], R[3]);
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+              val[s][sl] = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
+                                   pick4(R, sl, f0, f1, 1));
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < CH; ++s) {
+          const int x = t + T8 * (c0 + s);
+          T c[SLOTS];
+          int kb[SLOTS];
+#pragma unroll
+          for (int sl = 0; sl < SLOTS; ++sl) {
+            const int b_ = bn[s][sl];
+            const T bv = sbase ? BV[sl * L + x] : T(0);
+            const T o = (b_ < 0 ? a0 : sA[b_]) * val[s][sl] + bv;
+            if (valid) {
+              yo[row[sl] * L + x] = o;
+              dsum += bv * o;
+            }
+            c[sl] = xv[s][sl] * val[s][sl];
+            kb[sl] = (bins && b_ >= 0) ? b_ : -1;
+          }
+          if (bins) add_slots<SLOTS, T>(kb, c, hist);
+        }
+      }
+      if (dot) dacc += double(dsum);
+    } else {
+    T dsum = T(0);
     // output of slot value `val` at row `rw`, column x of sample `sp`
     auto put = [&](int sp, int rw, int x, T val, T bval, int& bn, T& c) {
       if constexpr (EK == SK_BUF) {
@@ -289,7 +340,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
         c = (bins && bn >= 0) ? __ldg(&epi.xi_p[(int64_t)sp * epi.ps + f]) * val : T(0);
         if (!bins) bn = -1;
       } else {
-        epi.store_b(sp, (int64_t)rw * L + x, val, bval, bn, c, stab);
+        const T o = epi.store_b(sp, (int64_t)rw * L + x, val, bval, bn, c, stab);
+        dsum += bval * o;
       }
     };
 #pragma unroll
@@ -316,8 +368,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
         T c[2] = {T(0), T(0)};
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl) {
-          const int s0 = f0 ? 1 - sl : sl;
-          const T val = half * (R[sl][0] + R[s0][0] + R[sl][1] - R[s0][1]);
+          const T val = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
           if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
         }
         if (bins) add_slots<2, T>(bn, c, hist);
@@ -332,18 +383,26 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
         T c[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int sl = 0; sl < 4; ++sl) {
-          const int s0 = f0 ? (sl ^ 1) : sl;
-          const int s1 = f1 ? (sl ^ 2) : sl;
-          const int s01 = f1 ? (s0 ^ 2) : s0;
-          const T val = half * (R[s0][0] + R[s1][0] + R[sl][1] - R[s01][1]);
+          const T val = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
+                                pick4(R, sl, f0, f1, 1));
           if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
         }
         if (bins) add_slots<4, T>(bn, c, hist);
       }
     }
+    if (dot) dacc += double(dsum);
+    }  // generic epilogue
     __syncthreads();  // this half is refilled two iterations later
   }
   cp_wait<0>();
+  if (dot) {
+    __shared__ double dred[32];
+    const double tot = block_sum(dacc, dred);
+    double* dp = epi.dot + (int64_t)blockIdx.y * kDotStride;
+    if (threadIdx.x == 0) dp[blockIdx.x] = tot;
+    if (blockIdx.x == 0)
+      for (int i = gridDim.x + threadIdx.x; i < kDotStride; i += blockDim.x) dp[i] = 0.0;
+  }
   if (bins) {
     __syncthreads();
     if (PM == 1) {

@@ -92,3 +92,72 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.icr_create(C.byref(p), C.byref(ch), C.byref(kp), 3, L.NRE_F32) == L.NRE_EINVAL
     assert lib.metric_apply(None, None, None, 1, None) == L.NRE_EINVAL
     assert lib.cg_solve(None, None, None, 1, 0.0, 1, None, None, None) == L.NRE_EINVAL
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the header's structs have the C sizes and offsets."""
+    import shutil
+    import subprocess
+    from paper_2402_16683_gb300 import _lib as L
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"nre_cf_amp_params": L.CFAmpParams, "nre_serve_cfg": L.ServeCfg, "nre_serve_req": L.ServeReq,
+               "nre_serve_result": L.ServeResult, "nre_serve_stats": L.ServeStats,
+               "icr_chart_params": L.ICRChartParams, "icr_kernel_params": L.ICRKernelParams}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nre.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_serve_host_side_checks(lib):
+    from paper_2402_16683_gb300 import _lib as L
+    r = L.ServeReq()
+    r.ndim = 2
+    r.shape[0], r.shape[1] = 256, 256
+    r.amp.kind = L.NRE_AMP_POWER_MODEL
+    r.amp.n_bins = 256
+    r.n_samples = 8
+    r.precond = L.NRE_PRECOND_HARMONIC
+    r.response = L.NRE_RESP_EXP
+    out = C.c_uint64()
+    assert lib.serve_footprint(C.byref(r), L.NRE_F32, C.byref(out)) == L.NRE_OK
+    f32 = out.value
+    N, lat = 256 * 256, 256 * 256 + 514
+    # at least x, b, r, p, q, z of 8 samples and the two sweep intermediates
+    assert f32 >= (6 * 8 * lat + 2 * 8 * N) * 4
+    assert lib.serve_footprint(C.byref(r), L.NRE_F64, C.byref(out)) == L.NRE_OK
+    assert out.value > 1.6 * f32
+    r.n_samples = 16
+    assert lib.serve_footprint(C.byref(r), L.NRE_F32, C.byref(out)) == L.NRE_OK and out.value > 1.6 * f32
+    r.shape[1] = 100
+    assert lib.serve_footprint(C.byref(r), L.NRE_F32, C.byref(out)) == L.NRE_EINVAL
+    r.shape[1] = 256
+    r.n_samples = 65
+    assert lib.serve_footprint(C.byref(r), L.NRE_F32, C.byref(out)) == L.NRE_EINVAL
+    r.n_samples = 8
+    r.amp.kind = L.NRE_AMP_ARRAY
+    assert lib.serve_footprint(C.byref(r), L.NRE_F32, C.byref(out)) == L.NRE_EINVAL
+    h = C.c_void_p()
+    cfg = L.ServeCfg(0, 0, L.NRE_F32, 8, 1, 0)
+    assert lib.serve_create(C.byref(h), C.byref(cfg)) == L.NRE_EINVAL  # max_slots 0
+    cfg = L.ServeCfg(0, 4, 5, 8, 1, 0)
+    assert lib.serve_create(C.byref(h), C.byref(cfg)) == L.NRE_EINVAL  # dtype
+    assert lib.serve_submit(None, None, None) == L.NRE_EINVAL
+    assert lib.serve_poll(None, 1, None, 0) == L.NRE_EINVAL
+    assert lib.serve_destroy(None) == L.NRE_OK
