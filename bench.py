@@ -53,10 +53,10 @@ def parse():
     ap.add_argument("--no-metric-grids", action="store_true",
                     help="skip the metric-product roofline leg on 2-D 1024^2 and 3-D 256^3")
     ap.add_argument("--metric-batch", type=int, default=8)
-    ap.add_argument("--serve-requests", type=int, default=0,
+    ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-plain-cap-s", type=float, default=120.0,
+    ap.add_argument("--serve-plain-cap-s", type=float, default=90.0,
                     help="stop the sequential FP64 arm after this many seconds")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     return ap.parse_args()
@@ -529,12 +529,23 @@ def run_serve(args):
     ok32 = sum(1 for r in results if r["status"] == 0)
     end32 = max(r["t_done"] for r in results)
     its32 = [max(r["iters"][:SERVE_SAMPLES]) for r in results]
+    by_class = {}
+    for i, r in enumerate(results):
+        key = "x".join(str(d) for d in reqs[i][1]) + "_" + reqs[i][2]
+        c = by_class.setdefault(key, {"n": 0, "converged": 0, "iters": [], "lat": []})
+        c["n"] += 1
+        c["converged"] += int(r["status"] == 0)
+        c["iters"].append(max(r["iters"][:SERVE_SAMPLES]))
+        c["lat"].append(lat32[i])
+    by_class = {k: {"n": v["n"], "converged": v["converged"], "mean_iters": float(np.mean(v["iters"])),
+                    "p50_ms": _pctl(v["lat"], 50)} for k, v in sorted(by_class.items())}
     fp32 = {"p50_ms": _pctl(lat32, 50), "p99_ms": _pctl(lat32, 99), "mean_ms": float(np.mean(lat32)),
             "solves_per_s": SERVE_SAMPLES * len(reqs) / (end32 - t0), "converged": ok32,
             "mean_iters": float(np.mean(its32)), "max_relres": max(max(r["relres"][:SERVE_SAMPLES]) for r in results),
             "slots": args.serve_slots, "graph_replays": st["graph_replays"], "chunks": st["chunks"],
             "slot_objects_created": st["created"], "reused": st["reused"],
-            "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9}
+            "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9,
+            "by_class": by_class}
 
     # ---- plain sequential FP64 path
     plans = {shape: nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR),

@@ -171,11 +171,7 @@ __global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const do
   const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
   const double* st = state + b * ss;
   const bool act = i < nb;
-  double gA = 0.0;
-  if (act) {
-    const double* pp = partials + (int64_t)b * nparts * nb + i;
-    for (int c = 0; c < nparts; ++c) gA += pp[(int64_t)c * nb];
-  }
+  const double gA = act ? sum_strided(partials + (int64_t)b * nparts * nb + i, nparts, nb) : 0.0;
   const double th_fl = st[AS_THFL], th_fx = st[AS_THFX], th_as = st[AS_THAS], S = st[AS_S];
   const double rs = 1.0 / sqrt(S);
   const double a = act ? st[as_a(nb) + i] : 0.0;
@@ -232,7 +228,103 @@ __global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const do
   }
   if (dot != nullptr) {
     const double t = block_sum(dsum, red);
-    if (i == 0) dot[(int64_t)b * kDotStride + kDotStride - 1] = t;
+    if (i == 0) dot[(int64_t)b * kDotStride + kDotHyper] = t;
+  }
+}
+
+// Linearised amplitude model: the Jacobian at the expansion point,
+// Jt[h][i] = dA_i / dh (FP64, from the JVP along the unit vectors, so the
+// cumulative integration stays FP64), stored in FP32 both ways for the FP32
+// path:  dA = J dh  and  g_h = J^T gA, in FP32 (a warp per output: lane runs
+// of at most 17 products, then a shuffle tree).
+template <typename T>
+__global__ void k_eye(T* e, int n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)n * n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    e[k] = (k / n == k % n) ? T(1) : T(0);
+}
+
+__global__ void k_jac_store(const double* Jt, int nh, int nb, float* G, float* Gt) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nh * nb;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(k / nb), i = (int)(k % nb);
+    const float v = float(Jt[k]);
+    Gt[k] = v;                     // [nh][nb]
+    G[(int64_t)i * nh + h] = v;    // [nb][nh]
+  }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// dA[b][i] = sum_h G[i][h] dh[b][h]; one warp per output.
+template <typename T>
+__global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs,
+                                                    double* dA) {
+  const int b = blockIdx.y, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nb) return;
+  const float* g = G + (int64_t)i * nh;
+  const T* d = dh + b * dhs;
+  // eight independent loads per lane in flight per round
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int h0 = 0; h0 < nh; h0 += 256) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int h = h0 + lane + 32 * k;
+      if (h < nh) acc[k] += __ldg(&g[h]) * float(d[h]);
+    }
+  }
+  const float t = warp_sum_f(((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+  if (lane == 0) dA[(int64_t)b * nb + i] = double(t);
+}
+
+// out_h[b] = base_h[b] + G^T gA[b], gA[b] = sum_c partials[b][c][:]; CTAs of
+// 32 outputs (8 warps, 4 outputs each: 32 loads per lane in flight); with
+// `dot`, also the CTA's share of sum(base_h * out_h) at dot[b][kDotHyper + cta].
+template <typename T>
+__global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials,
+                                                    int nparts, const T* base, int64_t bhs, T* out, int64_t ohs,
+                                                    double* dot) {
+  __shared__ float gA[1024];
+  __shared__ double red[8];
+  const int b = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    gA[i] = float(sum_strided(partials + (int64_t)b * nparts * nb + i, nparts, nb));
+  __syncthreads();
+  const T* bb = base ? base + b * bhs : nullptr;
+  T* o = out + b * ohs;
+  double dsum = 0.0;
+  const int h0 = blockIdx.x * 32 + w * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int i0 = 0; i0 < nb; i0 += 256) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = i0 + lane + 32 * k;
+      if (i < nb) {
+        const float a = gA[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (h0 + q < nh) acc[q] += __ldg(&Gt[(int64_t)(h0 + q) * nb + i]) * a;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float t = warp_sum_f(acc[q]);
+    const int h = h0 + q;
+    if (lane == 0 && h < nh) {
+      const T v = T((bb ? float(bb[h]) : 0.f) + t);
+      o[h] = v;
+      if (bb) dsum += double(bb[h] * v);
+    }
+  }
+  if (dot != nullptr) {
+    const double tot = block_sum(dsum, red);
+    if (threadIdx.x == 0) dot[(int64_t)b * kDotStride + kDotHyper + blockIdx.x] = tot;
   }
 }
 
@@ -288,12 +380,53 @@ int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* p
   return NRE_OK;
 }
 
+template <typename T>
+int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double* Jt, float* G, float* Gt,
+                 cudaStream_t st) {
+  prof_begin("amp_jacobian", (double)nh * nh * sizeof(T), st);
+  k_eye<T><<<304, 256, 0, st>>>(eye, nh);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  NRE_TRY(amp_jvp<T>(pr, state, 0, eye, nh, Jt, nh, st));
+  prof_begin("amp_jacobian", (double)nh * pr.nb * 16.0, st);
+  k_jac_store<<<304, 256, 0, st>>>(Jt, nh, pr.nb, G, Gt);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st) {
+  prof_begin("amp_jvp", (double)nb * nh * 4 + (double)B * (nh * sizeof(T) + nb * 8), st);
+  k_amp_jvp_lin<T><<<dim3((nb + 7) / 8, B), 256, 0, st>>>(G, nb, nh, dh, dhs, dA);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
+template <typename T>
+int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int nparts, const T* base_h,
+                int64_t bhs, T* out_h, int64_t ohs, int B, cudaStream_t st, double* dot) {
+  prof_begin("amp_vjp", (double)nb * nh * 4 + (double)B * (8.0 * nparts * nb + (base_h ? 2 : 1) * nh * sizeof(T)),
+             st);
+  k_amp_vjp_lin<T><<<dim3((nh + 31) / 32, B), 256, 0, st>>>(Gt, nb, nh, partials, nparts, base_h, bhs, out_h,
+                                                             ohs, dot);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}
+
 #define NRE_INST(T)                                                                              \
   template int amp_forward<T>(const AmpPrior&, const T*, int64_t, double*, int, cudaStream_t);   \
   template int amp_jvp<T>(const AmpPrior&, const double*, int64_t, const T*, int64_t, double*,   \
                           int, cudaStream_t);                                                    \
   template int amp_vjp<T>(const AmpPrior&, const double*, int64_t, const double*, int, const T*, \
-                          int64_t, T*, int64_t, int, cudaStream_t, double*);
+                          int64_t, T*, int64_t, int, cudaStream_t, double*);                      \
+  template int amp_jacobian<T>(const AmpPrior&, const double*, int, T*, double*, float*, float*,       \
+                               cudaStream_t);                                                          \
+  template int amp_jvp_lin<T>(const float*, int, int, const T*, int64_t, double*, int, cudaStream_t);   \
+  template int amp_vjp_lin<T>(const float*, int, int, const double*, int, const T*, int64_t, T*,        \
+                              int64_t, int, cudaStream_t, double*);
 NRE_INST(float)
 NRE_INST(double)
 #undef NRE_INST

@@ -119,8 +119,10 @@ enum { EPI_BUF = 0, EPI_OFFSET = 1, EPI_WEIGHT = 2, EPI_AMP = 3 };
 
 // Consumer of the last transform's output at (sample b, pixel flat).
 // Partials of the fused metric-product inner product per sample: one per CTA
-// of the last sweep (at most 128) and the hyper-parameter part in the last.
-constexpr int kDotStride = 129;
+// of the last sweep (at most 128) at [0, 128), the hyper-parameter part at
+// [128, 160) (one per CTA of the amplitude VJP; unused entries are zero).
+constexpr int kDotStride = 160;
+constexpr int kDotHyper = 128;
 
 template <typename T>
 struct Epi {
@@ -299,11 +301,24 @@ template <typename T>
 int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
             double* dA, int B, cudaStream_t st);
 // out_h[b] = base_h[b] (optional) + VJP at state of gA[b] = sum_c partials[b][c][:].
-// With `dot` (and a base): dot[b * kDotStride + kDotStride - 1] = sum(base_h * out_h).
+// With `dot` (and a base): dot[b * kDotStride + kDotHyper] = sum(base_h * out_h).
 template <typename T>
 int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* partials,
             int nparts, const T* base_h, int64_t bhs, T* out_h, int64_t ohs, int B,
             cudaStream_t st, double* dot = nullptr);
+
+// Linearised amplitude model at an expansion point (FP32 path): the Jacobian
+// from nh JVPs along the unit vectors (eye: [nh][nh] scratch, Jt: [nh][nb] FP64
+// scratch), stored as G [nb][nh] and Gt [nh][nb] floats; then dA = G dh and
+// out_h = base_h + Gt^T-contractions of the per-bin sums (as amp_jvp / amp_vjp).
+template <typename T>
+int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double* Jt, float* G, float* Gt,
+                 cudaStream_t st);
+template <typename T>
+int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st);
+template <typename T>
+int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int nparts, const T* base_h,
+                int64_t bhs, T* out_h, int64_t ohs, int B, cudaStream_t st, double* dot = nullptr);
 
 // Sweep chains (sweeps.cu).  Runs one Hartley transform (mid == nullptr) or the
 // metric's transform pair with t = w * y between them (mid != nullptr) over a

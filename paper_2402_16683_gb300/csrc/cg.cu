@@ -20,9 +20,13 @@ constexpr int CG_THREADS = 256;
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
        SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
-// Blocks per system of the vector kernels.
-int cg_blocks(int64_t n) {
-  int64_t nb = (n + CG_THREADS * 8 - 1) / (CG_THREADS * 8);
+// Blocks per system of the vector kernels: about four waves of the 152 SMs
+// over the whole batch (enough loads in flight, few partials to fold), at
+// least 4 vectors per thread and at most 64 blocks.
+int cg_blocks(int64_t n, int B) {
+  int64_t nb = (4 * 152 + B - 1) / B;
+  const int64_t cap = (n + CG_THREADS * 16 - 1) / (CG_THREADS * 16);
+  if (nb > cap) nb = cap;
   if (nb > 64) nb = 64;
   if (nb < 1) nb = 1;
   return (int)nb;
@@ -251,7 +255,7 @@ struct CGWork {
 template <typename T>
 CGWork<T> cg_work(nre_metric* m, int B) {
   CGWork<T> w;
-  w.nblk = cg_blocks(m->latent);
+  w.nblk = cg_blocks(m->latent, B);
   w.r = m->cg_r.as<T>();
   w.p = m->cg_p.as<T>();
   w.q = m->cg_q.as<T>();
@@ -270,7 +274,7 @@ int cg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_t
   NRE_TRY(ensure(m->cg_p, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_q, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_sc, (size_t)B * SC_N * sizeof(double)));
-  const int nblk = cg_blocks(n);
+  const int nblk = cg_blocks(n, B);
   NRE_TRY(ensure(m->cg_part, (size_t)2 * B * nblk * sizeof(double) + (size_t)B * sizeof(unsigned)));
   if (m->model_kind == NRE_MODEL_CF) NRE_TRY(ensure(m->cg_dot, (size_t)B * kDotStride * sizeof(double)));
   const CGWork<T> w = cg_work<T>(m, B);

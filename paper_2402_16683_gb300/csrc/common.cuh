@@ -123,6 +123,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// sum_{c < n} p[c * stride] by one thread, fixed order, eight loads in flight
+// (the partial-sum loops are otherwise a serial chain of L2 round trips).
+__device__ __forceinline__ double sum_strided(const double* p, int n, int64_t stride) {
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int c = 0;
+  for (; c + 8 <= n; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = p[(int64_t)(c + k) * stride];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] += v[k];
+  }
+  for (int k = 0; c < n; ++c, ++k) acc[k] += p[(int64_t)c * stride];
+  return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
 // Sum of n doubles p[0..n) by the first warp of the block in a fixed order
 // (lane-strided runs, then a shuffle tree); every thread gets the result.
 // Must be called by all threads of the block.

@@ -84,6 +84,18 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
     NRE_TRY(ensure(m->dA, (size_t)m->max_batch * nb * sizeof(double)));
     NRE_TRY(ensure(m->part, (size_t)m->max_batch * max_parts(p) * nb * sizeof(double)));
     NRE_TRY(amp_forward<T>(amp_prior_of(p), xp + N, 0, m->state.as<double>(), 1, st));
+    if (sizeof(T) == 4 && p->n_hyper <= 1024) {
+      // FP32 products: the amplitude JVP / VJP become products with the
+      // Jacobian at xi_p, formed once here from FP64 JVPs
+      const int nh = p->n_hyper;
+      NRE_TRY(ensure(m->amp_G, (size_t)nb * nh * sizeof(float)));
+      NRE_TRY(ensure(m->amp_Gt, (size_t)nb * nh * sizeof(float)));
+      NRE_TRY(ensure(m->amp_eye, (size_t)nh * nh * sizeof(T)));
+      NRE_TRY(ensure(m->amp_Jt, (size_t)nh * nb * sizeof(double)));
+      NRE_TRY(amp_jacobian<T>(amp_prior_of(p), m->state.as<double>(), nh, m->amp_eye.as<T>(),
+                              m->amp_Jt.as<double>(), m->amp_G.as<float>(), m->amp_Gt.as<float>(), st));
+      m->amp_lin = true;
+    }
     pro.av = amp_view<T>(p, m->state.as<double>() + as_A(nb), 0);
     NRE_TRY(ensure(m->apix, N * sizeof(T)));
     NRE_TRY(ensure(m->bpix, N * sizeof(int16_t)));
@@ -119,7 +131,10 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   const int nb = p->n_bins;
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
   if (model) {
-    NRE_TRY(amp_jvp<T>(pr, m->state.as<double>(), 0, v + N, S, m->dA.as<double>(), B, st));
+    if (m->amp_lin)
+      NRE_TRY(amp_jvp_lin<T>(m->amp_G.as<float>(), nb, p->n_hyper, v + N, S, m->dA.as<double>(), B, st));
+    else
+      NRE_TRY(amp_jvp<T>(pr, m->state.as<double>(), 0, v + N, S, m->dA.as<double>(), B, st));
     pro.av = metric_view<T>(m);
     pro.dA = m->dA.as<double>();
     pro.nb = nb;
@@ -136,9 +151,14 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   int np = 0;
   NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
                          model ? m->part.as<double>() : nullptr, &np, st));
-  if (model)
-    NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,
-                       B, st, dot));
+  if (model) {
+    if (m->amp_lin)
+      NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->part.as<double>(), np, v + N, S, out + N,
+                             S, B, st, dot));
+    else
+      NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,
+                         B, st, dot));
+  }
   return NRE_OK;
 }
 

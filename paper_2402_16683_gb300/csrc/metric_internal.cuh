@@ -29,6 +29,9 @@ struct nre_metric {
   nre::DevBuf apix;     // [n_data] A_full at xi_p per pixel (power model)
   nre::DevBuf bpix;     // [n_data] int16 log-|k| bin per pixel (power model)
   nre::DevBuf dA;       // [max_batch][n_bins]
+  // FP32 power model: the amplitude Jacobian at xi_p (see amp_jacobian)
+  bool amp_lin = false;
+  nre::DevBuf amp_G, amp_Gt, amp_eye, amp_Jt;
   nre::DevBuf tmp0, tmp1, part;
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;
@@ -44,6 +47,7 @@ struct nre_metric {
   nre::DevBuf pc_tmp, pc_eye, pc_dG;  // preconditioner set-up scratch
   nre::DevBuf pc_invD, pc_e;          // per pixel: 1 / D and A xi_p / D
   nre::DevBuf pc_Gt;                  // float [n_bins][n_hyper]: G transposed
+  nre::DevBuf pc_cdev;                // double: pc_c on the device
 };
 
 namespace nre {

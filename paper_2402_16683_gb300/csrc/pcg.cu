@@ -30,8 +30,13 @@ constexpr int PC_THREADS = 256;
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
        SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
-int pc_blocks(int64_t n) {
-  int64_t nb = (n + PC_THREADS * 8 - 1) / (PC_THREADS * 8);
+// Blocks per system of the vector kernels: about four waves of the 152 SMs
+// over the whole batch (enough loads in flight, few partials to fold), at
+// least 4 vectors per thread and at most 64 blocks.
+int pc_blocks(int64_t n, int B) {
+  int64_t nb = (4 * 152 + B - 1) / B;
+  const int64_t cap = (n + PC_THREADS * 16 - 1) / (PC_THREADS * 16);
+  if (nb > cap) nb = cap;
   if (nb > 64) nb = 64;
   if (nb < 1) nb = 1;
   return (int)nb;
@@ -40,7 +45,9 @@ int pc_blocks(int64_t n) {
 template <typename T>
 struct PCArgs {
   int64_t N;            // field entries (the rest of the latent vector is hyper)
-  double c;             // N * mean(w)
+  double c;             // N * mean(w) (set-up kernels)
+  const double* cdev;   // the same on the device (iteration kernels: read at run time,
+                        // so that captured launches follow a re-linearised metric)
   AmpView<T> av;        // amplitude at the expansion point (set-up only)
   const T* xi_p;        // expansion point (set-up only)
   const T* invD;        // [N] 1 / D_k = 1 / (1 + c A_k^2)
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
 // Hyper block of the preconditioner, one CTA per system:
 // z_h = S^-1 (r_h - c G t), gz = G^T z_h  (G [nh][nb], Gt = G^T [nb][nh]).
 template <typename T>
-__global__ void k_pcg_hyper(const T* r, T* z, int64_t S, int64_t N, int nh, int nb, double c,
+__global__ void k_pcg_hyper(const T* r, T* z, int64_t S, int64_t N, int nh, int nb, const double* cdev,
                             const float* G, const float* Gt, const float* Sinv, const double* bin_part,
                             int nparts, double* gz) {
   extern __shared__ float sh[];
@@ -221,14 +228,11 @@ __global__ void k_pcg_hyper(const T* r, T* z, int64_t S, int64_t N, int nh, int 
   float* u = t + nb;    // [nh]
   float* zh = u + nh;   // [nh]
   const int b = blockIdx.x;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    double s = 0.0;
-    const double* pp = bin_part + (int64_t)b * nparts * nb + i;
-    for (int k = 0; k < nparts; ++k) s += pp[(int64_t)k * nb];
-    t[i] = float(s);
-  }
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    t[i] = float(sum_strided(bin_part + (int64_t)b * nparts * nb + i, nparts, nb));
   __syncthreads();
   const T* rh = r + (int64_t)b * S + N;
+  const double c = *cdev;
   for (int h = threadIdx.x; h < nh; h += blockDim.x) {
     float s0 = 0.f, s1 = 0.f;
     int i = 0;
@@ -274,7 +278,8 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_z(const T* r, T* z, T* p, in
   __shared__ float sgz[1024];
   constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) sgz[i] = float(pc.c * pc.gz[(int64_t)b * pc.nb + i]);
+  const double cc = *pc.cdev;
+  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) sgz[i] = float(cc * pc.gz[(int64_t)b * pc.nb + i]);
   __syncthreads();
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
@@ -450,6 +455,7 @@ PCArgs<T> pc_args(nre_metric* m) {
   PCArgs<T> a{};
   a.N = p->N;
   a.c = m->pc_c;
+  a.cdev = m->pc_cdev.as<double>();
   a.xi_p = m->xi_p.as<T>();
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   a.av = metric_view<T>(m);
@@ -521,6 +527,8 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   NRE_TRY_CUDA(cudaStreamSynchronize(st));
   m->pc_c = wsum;  // N * mean(w) = sum(w)
   m->pc_nh = nh;
+  NRE_TRY(ensure(m->pc_cdev, sizeof(double)));
+  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_cdev.p, &m->pc_c, sizeof(double), cudaMemcpyHostToDevice, st));
   // per-pixel coefficients 1 / D and A xi_p / D
   NRE_TRY(ensure(m->pc_invD, (size_t)N * sizeof(T)));
   if (model) NRE_TRY(ensure(m->pc_e, (size_t)N * sizeof(T)));
@@ -594,7 +602,7 @@ PCGWork<T> pcg_work(nre_metric* m, int B) {
   nre_cf_plan* p = m->cf;
   w.nb = m->pc_nh > 0 ? p->n_bins : 0;
   w.nh = m->pc_nh;
-  w.nblk = pc_blocks(m->latent);
+  w.nblk = pc_blocks(m->latent, B);
   w.r = m->cg_r.as<T>();
   w.p = m->cg_p.as<T>();
   w.q = m->cg_q.as<T>();
@@ -619,7 +627,7 @@ int pcg_precondition(nre_metric* m, const PCGWork<T>& w, int B, int init, cudaSt
   const double vb = (double)B * n * sizeof(T);
   if (w.nb > 0) {
     prof_begin("pcg_hyper", (double)B * w.nh * sizeof(T) * 2, st);
-    k_pcg_hyper<T><<<B, 512, w.hyp_sm, st>>>(w.r, w.z, S, N, w.nh, w.nb, m->pc_c, m->pc_G.as<float>(),
+    k_pcg_hyper<T><<<B, 512, w.hyp_sm, st>>>(w.r, w.z, S, N, w.nh, w.nb, m->pc_cdev.as<double>(), m->pc_G.as<float>(),
                                               m->pc_Gt.as<float>(), m->pc_Sinv.as<float>(), w.pc.bin_part,
                                               w.nblk, m->pc_gz.as<double>());
     prof_end(st);
@@ -641,7 +649,7 @@ int pcg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_
   NRE_TRY(ensure(m->cg_q, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_z, (size_t)B * S * sizeof(T)));
   NRE_TRY(ensure(m->cg_sc, (size_t)B * SC_N * sizeof(double)));
-  const int nblk = pc_blocks(n);
+  const int nblk = pc_blocks(n, B);
   NRE_TRY(ensure(m->cg_part, (size_t)3 * B * nblk * sizeof(double)));
   NRE_TRY(ensure(m->cg_dot, (size_t)B * kDotStride * sizeof(double)));
   if (nb > 0) {

@@ -303,7 +303,8 @@ int col_sweep_reg(ColArgs<T> a, int64_t outer, bool mid, int B, bool bins, int* 
   *handled = false;
   NRE_L_SWITCH(a.log2L, {
     if (ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0) > 200 * 1024) return NRE_OK;
-    a.W = ColShape<L>::W < a.inner ? ColShape<L>::W : (int)a.inner;
+    constexpr int CW = ColShape<L, sizeof(T)>::W;
+    a.W = CW < a.inner ? CW : (int)a.inner;
     a.nblk = a.inner / a.W;
     a.n_units = outer * a.nblk;
     *handled = true;

@@ -32,12 +32,16 @@ int launch_row_pm(const RowArgs<T>& a, int pk, int ek, dim3 grid, size_t smem, c
 template <typename T>
 int pro_kind(const Pro<T>& p) {
   if (p.mode == PRO_BUF) return SK_BUF;
-  return (p.mode == PRO_AMP && p.av.mode == AMPV_PIX && p.av.bpix != nullptr) ? SK_TAB : SK_GEN;
+  // TAB: the metric's prologue (per-pixel bins, the tangent's dA)
+  return (p.mode == PRO_AMP && p.av.mode == AMPV_PIX && p.av.bpix != nullptr && p.dA != nullptr) ? SK_TAB : SK_GEN;
 }
 template <typename T>
 int epi_kind(const Epi<T>& e) {
   if (e.mode == EPI_BUF) return SK_BUF;
-  return (e.mode == EPI_AMP && e.av.mode == AMPV_PIX && e.av.bpix != nullptr) ? SK_TAB : SK_GEN;
+  // TAB: the metric / MGVI epilogue (per-pixel bins, a base, bin sums)
+  return (e.mode == EPI_AMP && e.av.mode == AMPV_PIX && e.av.bpix != nullptr && e.base != nullptr && e.bins)
+             ? SK_TAB
+             : SK_GEN;
 }
 
 template <typename T, int L>
@@ -94,7 +98,7 @@ int row_reg_plan(RowArgs<T>& a, int B, bool bins, dim3* grid, size_t* smem, int*
 
 template <typename T, int L>
 int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_t st, int64_t N) {
-  constexpr int NT = ColShape<L>::NT;
+  constexpr int NT = ColShape<L, sizeof(T)>::NT;
   const int gx = persistent_gx(a.n_units, B);
   *nparts = gx;
   const size_t smem = ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0);

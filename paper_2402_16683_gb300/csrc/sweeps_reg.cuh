@@ -39,10 +39,13 @@ struct RowShape {
   static constexpr int NU = NT / T8;  // units per CTA iteration
 };
 
-template <int L>
+// Column tiles: NL complex lines (2 NL grid columns) per CTA.  FP32 tiles of
+// lines >= 1024 take 512 threads so that a tile row spans 8 columns (32 bytes).
+template <int L, int ES>
 struct ColShape {
   static constexpr int T8 = L / 8;
-  static constexpr int NT = T8 > 256 ? T8 : 256;
+  static constexpr int NTMIN = (ES == 4 && L >= 1024) ? 512 : 256;
+  static constexpr int NT = T8 > NTMIN ? T8 : NTMIN;
   static constexpr int NL = NT / T8;            // complex lines per tile
   static constexpr int W = 2 * NL;              // grid columns per tile
   static constexpr int WP = W + 4;              // padded tile row (16-byte multiple)
@@ -218,26 +221,39 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
           v[q][s] = cmake<C>(sval[2 * q] ? X[(2 * q) * L + x] : T(0), sval[2 * q + 1] ? X[(2 * q + 1) * L + x] : T(0));
         }
     } else {
-      // u = A[bin] v + dA[bin] xi_p (bins per pixel, tables in shared memory)
+      // u = A[bin] v + dA[bin] xi_p (bins per pixel, tables in shared memory;
+      // the metric's prologue always has the tangent's dA).  Rows that are
+      // mirror images in the orbit (flags) share their bin row: only the
+      // canonical slot's bins are loaded.
       const int16_t* bp = pro.av.bpix;
       const T* xp = pro.xi_p + (int64_t)bsample * pro.ps;
       const T a0 = pro.av.a0t;
+      const int fl = valid ? __ldg(&a.gflags[unit]) : 0;
+      const bool f0 = fl & 1, f1 = fl & 2;
 #pragma unroll
-      for (int q = 0; q < LPU; ++q)
+      for (int s = 0; s < 8; ++s) {
+        const int x = t + T8 * s;
+        int bn[LPU][2];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int x = t + T8 * s;
+        for (int q = 0; q < LPU; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (PM == 2 && h == 1 && f0) bn[q][1] = bn[q][0];
+            else bn[q][h] = valid ? (int)__ldg(&bp[row[2 * q + h] * L + x]) : -1;
+          }
+#pragma unroll
+        for (int q = 0; q < LPU; ++q) {
           T e[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int f = row[2 * q + h] * L + x;
-            const int bn = __ldg(&bp[f]);
-            T val = (bn < 0 ? a0 : sA[bn]) * X[(2 * q + h) * L + x];
-            if (stdA != nullptr && bn >= 0) val += sdA[bn] * __ldg(&xp[f]);
+            const int b_ = bn[q][h];
+            T val = (b_ < 0 ? a0 : sA[b_]) * X[(2 * q + h) * L + x];
+            if (b_ >= 0) val += sdA[b_] * __ldg(&xp[row[2 * q + h] * L + x]);
             e[h] = sval[2 * q + h] ? val : T(0);
           }
           v[q][s] = cmake<C>(e[0], e[1]);
         }
+      }
     }
     __syncthreads();  // the stage half becomes the exchange buffer
     C* sm[LPU];
@@ -280,9 +296,11 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
         for (int s = 0; s < CH; ++s)
 #pragma unroll
           for (int sl = 0; sl < SLOTS; ++sl) {
+            // mirror rows of the orbit share the canonical slot's bins
             const int f = row[sl] * L + t + T8 * (c0 + s);
-            bn[s][sl] = valid ? (int)__ldg(&bp[f]) : -1;
-            xv[s][sl] = (valid && bins) ? __ldg(&xp[f]) : T(0);
+            if (PM == 2 && sl == 1 && f0) bn[s][1] = bn[s][0];
+            else bn[s][sl] = valid ? (int)__ldg(&bp[f]) : -1;
+            xv[s][sl] = valid ? __ldg(&xp[f]) : T(0);
           }
 #pragma unroll
         for (int s = 0; s < CH; ++s) {
@@ -312,16 +330,16 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
 #pragma unroll
           for (int sl = 0; sl < SLOTS; ++sl) {
             const int b_ = bn[s][sl];
-            const T bv = sbase ? BV[sl * L + x] : T(0);
+            const T bv = BV[sl * L + x];  // the TAB epilogue always has a base (v or xi')
             const T o = (b_ < 0 ? a0 : sA[b_]) * val[s][sl] + bv;
             if (valid) {
               yo[row[sl] * L + x] = o;
               dsum += bv * o;
             }
             c[sl] = xv[s][sl] * val[s][sl];
-            kb[sl] = (bins && b_ >= 0) ? b_ : -1;
+            kb[sl] = b_;
           }
-          if (bins) add_slots<SLOTS, T>(kb, c, hist);
+          add_slots<SLOTS, T>(kb, c, hist);  // the TAB epilogue always sums the bins
         }
       }
       if (dot) dacc += double(dsum);
@@ -421,26 +439,31 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
 // Shared-memory plan of the column kernel (element counts in T).
 template <typename T, int L>
 struct ColSmem {
-  static constexpr int XS = L * ColShape<L>::WP;                     // one staged tile
-  static constexpr int LNSZ = ColShape<L>::NL * rline(L) * 2;       // exchange lines
+  typedef ColShape<L, sizeof(T)> CS;
+  static constexpr int XS = L * CS::WP;                              // one staged tile
+  static constexpr int LNSZ = CS::NL * rline(L) * 2;                 // exchange lines
+  // the exchange lines live in the current tile once it is in registers when
+  // they fit (short lines carry relatively more padding and get their own)
+  static constexpr bool ALIAS = LNSZ <= XS;
   static size_t bytes(int nb, int nhist_bins) {
-    return (size_t)2 * L * sizeof(T) + (size_t)2 * XS * sizeof(T) + (size_t)LNSZ * sizeof(T) +
+    return (size_t)2 * L * sizeof(T) + (size_t)2 * XS * sizeof(T) + (ALIAS ? 0 : (size_t)LNSZ * sizeof(T)) +
            (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
   }
 };
 
 template <typename T, int L, bool MID, int PK, int EK>
-__global__ void __launch_bounds__(ColShape<L>::NT, (ColShape<L>::NT <= 256 ? 3 : 1)) k_col_reg(ColArgs<T> a) {
+__global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeof(T)>::NT <= 256 ? 3 : (ColShape<L, sizeof(T)>::NT <= 512 ? 2 : 1)))
+    k_col_reg(ColArgs<T> a) {
   typedef typename CplxT<T>::type C;
   typedef ColSmem<T, L> SM;
-  constexpr int T8 = L / 8, NL = ColShape<L>::NL, WP = ColShape<L>::WP;
+  constexpr int T8 = L / 8, NL = ColShape<L, sizeof(T)>::NL, WP = ColShape<L, sizeof(T)>::WP;
   constexpr int LS = rline(L), CH = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   T* xin = reinterpret_cast<T*>(tw + L);      // [2][XS]; the current half is also the output tile
-  C* lines = reinterpret_cast<C*>(xin + 2 * SM::XS);
   const int nbp = (a.nb + 3) / 4 * 4;
-  T* sA = reinterpret_cast<T*>(lines + NL * LS);
+  C* lines_own = reinterpret_cast<C*>(xin + 2 * SM::XS);  // used when !SM::ALIAS
+  T* sA = xin + 2 * SM::XS + (SM::ALIAS ? 0 : SM::LNSZ);
   T* sdA = sA + nbp;
   double* hist = reinterpret_cast<double*>(sdA + nbp);
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
@@ -499,7 +522,8 @@ __global__ void __launch_bounds__(ColShape<L>::NT, (ColShape<L>::NT <= 256 ? 3 :
         v[0][s] = cmake<C>(T(0), T(0));
       }
     }
-    C* sm[1] = {lines + u * LS};
+    if (SM::ALIAS) __syncthreads();  // the whole tile is in registers: its space becomes the exchange lines
+    C* sm[1] = {(SM::ALIAS ? reinterpret_cast<C*>(X) : lines_own) + u * LS};
     C* const* smc = sm;
     reg_fft<C, L, 1>(v, smc, tw, t, sync);
     C zm[1][8];
