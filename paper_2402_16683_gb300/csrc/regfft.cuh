@@ -43,6 +43,24 @@ struct SyncNamed {
   }
 };
 
+// Twiddles in shared memory, one table per pass with twiddles: the pass with
+// stride NS and radix R stores W_{NS R}^{k r} at tw_off(L, NS) + (r - 1) NS + k
+// (k < NS, 1 <= r < R), so a thread reads its R - 1 twiddles at one base
+// address plus compile-time offsets.  The tables total fewer than L entries.
+__host__ __device__ constexpr int pass_radix(int L, int NS) { return L / NS >= 8 ? 8 : L / NS; }
+__host__ __device__ constexpr int tw_off(int L, int NS) {
+  int off = 0;
+  for (int ns = 8; ns < NS; ns *= 8) off += (pass_radix(L, ns) - 1) * ns;
+  return off;
+}
+__host__ __device__ constexpr int tw_total(int L) { return tw_off(L, L); }
+
+// Offset of rpad(base + r * NS) from rpad(base) for a pass's scatter, where
+// base = (j - k) R + k with k = j mod NS (the padding adds one element per 16).
+__host__ __device__ constexpr int scatter_off(int NS, int r) {
+  return NS == 1 ? r : (NS < 16 ? r * NS + ((r * NS) >> 4) : r * NS + r * (NS >> 4));
+}
+
 template <typename C, int L, int NS, int LPT>
 struct RegPass {
   static constexpr int REM = L / NS;
@@ -51,21 +69,27 @@ struct RegPass {
   static constexpr int M = 8 / R;
   static constexpr bool LAST = (NS * R == L);
 
+  // T8 a multiple of 16 (L >= 128): the padded index of every scatter /
+  // gather is one per-thread base plus a compile-time offset.
+  static constexpr bool FAST = (T8 % 16) == 0;
+
   template <class Sync>
   __device__ __forceinline__ static void run(C (&v)[LPT][8], C* const* sm,
                                              const C* __restrict__ tw, int t, Sync sync) {
 #pragma unroll
-    for (int q = 0; q < LPT; ++q) {
+    for (int m = 0; m < M; ++m) {
+      if constexpr (NS > 1) {
+        const int j = t + T8 * m;
+        const C* tk = tw + tw_off(L, NS) + (j & (NS - 1)) - NS;  // entry (r - 1) NS + k at tk + r NS
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        if constexpr (NS > 1) {
-          const int j = t + T8 * m;
-          const int k = j & (NS - 1);
+        for (int r = 1; r < R; ++r) {
+          const C w = tk[r * NS];
 #pragma unroll
-          for (int r = 1; r < R; ++r) v[q][m * R + r] = cmul(v[q][m * R + r], tw[k * r * (L / (NS * R))]);
+          for (int q = 0; q < LPT; ++q) v[q][m * R + r] = cmul(v[q][m * R + r], w);
         }
-        dftR<R>(&v[q][m * R]);
       }
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) dftR<R>(&v[q][m * R]);
     }
     if constexpr (LAST) {
 #pragma unroll
@@ -82,22 +106,41 @@ struct RegPass {
       typedef RegPass<C, L, NS * R, LPT> Next;
       constexpr int R2 = Next::R, M2 = 8 / R2;
 #pragma unroll
-      for (int q = 0; q < LPT; ++q)
+      for (int m = 0; m < M; ++m) {
+        const int j = t + T8 * m;
+        const int k = j & (NS - 1);
+        const int base = (j - k) * R + k;
+        if constexpr (FAST) {
+          const int pb = rpad(base);
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const int j = t + T8 * m;
-          const int k = j & (NS - 1);
-          const int base = (j - k) * R + k;
+          for (int q = 0; q < LPT; ++q)
 #pragma unroll
-          for (int r = 0; r < R; ++r) sm[q][rpad(base + r * NS)] = v[q][m * R + r];
+            for (int r = 0; r < R; ++r) sm[q][pb + scatter_off(NS, r)] = v[q][m * R + r];
+        } else {
+#pragma unroll
+          for (int q = 0; q < LPT; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[q][rpad(base + r * NS)] = v[q][m * R + r];
         }
+      }
       sync();
+      if constexpr (FAST) {
+        // rpad(t + T8 s') = rpad(t) + s' (T8 + T8 / 16)
+        const int pt = rpad(t);
 #pragma unroll
-      for (int q = 0; q < LPT; ++q)
+        for (int q = 0; q < LPT; ++q)
 #pragma unroll
-        for (int m = 0; m < M2; ++m)
+          for (int m = 0; m < M2; ++m)
 #pragma unroll
-          for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][rpad(t + T8 * m + r * (L / R2))];
+            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][pt + (m + r * M2) * (T8 + T8 / 16)];
+      } else {
+#pragma unroll
+        for (int q = 0; q < LPT; ++q)
+#pragma unroll
+          for (int m = 0; m < M2; ++m)
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][rpad(t + T8 * m + r * (L / R2))];
+      }
       sync();
       Next::run(v, sm, tw, t, sync);
     }
@@ -111,20 +154,39 @@ __device__ __forceinline__ void reg_fft(C (&v)[LPT][8], C* const* sm, const C* t
 }
 
 // zm[q][s] = X_q[-(t + s L/8) mod L] through the shared line buffers.
+// For T8 a multiple of 16 the mirror reads rpad(L - t) - s (T8 + T8/16); thread
+// 0's X[0] is also stored at rpad(L) (the line's last slot) for its s = 0 read.
 template <typename C, int L, int LPT, class Sync>
 __device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8], C* const* sm, int t,
                                            Sync sync) {
   constexpr int T8 = L / 8;
+  if constexpr ((T8 % 16) == 0) {
+    constexpr int ST = T8 + T8 / 16;
+    const int pt = rpad(t), pm = rpad(L - t);
 #pragma unroll
-  for (int q = 0; q < LPT; ++q)
+    for (int q = 0; q < LPT; ++q) {
 #pragma unroll
-    for (int s = 0; s < 8; ++s) sm[q][rpad(t + T8 * s)] = v[q][s];
-  sync();
+      for (int s = 0; s < 8; ++s) sm[q][pt + s * ST] = v[q][s];
+      if (t == 0) sm[q][rpad(L)] = v[q][0];
+    }
+    sync();
 #pragma unroll
-  for (int q = 0; q < LPT; ++q)
+    for (int q = 0; q < LPT; ++q)
 #pragma unroll
-    for (int s = 0; s < 8; ++s) zm[q][s] = sm[q][rpad((L - (t + T8 * s)) & (L - 1))];
-  sync();
+      for (int s = 0; s < 8; ++s) zm[q][s] = sm[q][pm - s * ST];
+    sync();
+  } else {
+#pragma unroll
+    for (int q = 0; q < LPT; ++q)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) sm[q][rpad(t + T8 * s)] = v[q][s];
+    sync();
+#pragma unroll
+    for (int q = 0; q < LPT; ++q)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) zm[q][s] = sm[q][rpad((L - (t + T8 * s)) & (L - 1))];
+    sync();
+  }
 }
 
 // Sum `val` over the runs of equal `key` among the lanes of a warp (runs are

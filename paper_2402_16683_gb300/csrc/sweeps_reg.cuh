@@ -61,9 +61,18 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <typename C>
-__device__ __forceinline__ void load_twiddles(C* tw, const C* gtw, int L, int shift) {
-  for (int m = threadIdx.x; m < L; m += blockDim.x) tw[m] = gtw[m << shift];
+// Per-pass twiddle tables (see tw_off) from the plan's table W_{Lmax}^m.
+template <int L, typename C>
+__device__ __forceinline__ void load_twiddles(C* tw, const C* gtw, int shift) {
+  for (int i = threadIdx.x; i < tw_total(L); i += blockDim.x) {
+    int ns = 8, off = 0;
+    while (i >= off + (pass_radix(L, ns) - 1) * ns) {
+      off += (pass_radix(L, ns) - 1) * ns;
+      ns *= 8;
+    }
+    const int R = pass_radix(L, ns), e = i - off, r = e / ns + 1, k = e - (r - 1) * ns;
+    tw[i] = gtw[(k * r * (L / (ns * R))) << shift];
+  }
 }
 
 // Barrier of the T8 threads of line `u` (consecutive threads).
@@ -141,7 +150,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   const int bsample = (PM == 1) ? 0 : blockIdx.y;
   const Pro<T>& pro = a.pro;
   const Epi<T>& epi = a.epi;
-  load_twiddles(tw, a.tw, L, a.log2Lmax - a.log2L);
+  load_twiddles<L>(tw, a.tw, a.log2Lmax - a.log2L);
   bool use_dA = false;
   const bool use_tab = (PM != 1) && load_tables<T>(pro, epi, bsample, sA, sdA, a.nb, &use_dA);
   const T* stab = use_tab ? sA : nullptr;
@@ -470,7 +479,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
   const int b = blockIdx.y;
   const Pro<T>& pro = a.pro;
   const Epi<T>& epi = a.epi;
-  load_twiddles(tw, a.tw, L, a.log2Lmax - a.log2L);
+  load_twiddles<L>(tw, a.tw, a.log2Lmax - a.log2L);
   bool use_dA = false;
   const bool use_tab = load_tables<T>(pro, epi, b, sA, sdA, a.nb, &use_dA);
   const T* stab = use_tab ? sA : nullptr;
