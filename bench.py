@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-metric-grids", action="store_true",
                     help="skip the metric-product roofline leg on 2-D 1024^2 and 3-D 256^3")
     ap.add_argument("--metric-batch", type=int, default=8)
+    ap.add_argument("--cg3d-maxiter", type=int, default=300,
+                    help="iteration cap of the 3-D masked batched CG solve in the metric leg")
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving stream (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -426,6 +428,21 @@ def run_metric_grids(args, lib):
             "kernels": {k: {"us_per_launch": 1e3 * x[1] / x[0], "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None,
                             "frac": (x[2] / (x[1] / 1e3) / 1e9 / peak) if x[1] else None}
                         for k, x in kern.items()}}
+        if len(shape) == 3:
+            # the 3-D masked workload's batched sample solve: plain CG on the
+            # MGVI right-hand sides (the harmonic preconditioner does not model
+            # a 10 % mask), reported as it stands at a bounded iteration count
+            eta = torch.tensor(np.random.default_rng(synth.SEED_RHS).standard_normal((B, plan.n_field)),
+                               dtype=torch.float32, device=dev)
+            M.mgvi_rhs(v, eta, out=o)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, its, rel, st_ = M.cg(o, rtol=1e-5, maxiter=args.cg3d_maxiter)
+            torch.cuda.synchronize()
+            out[f"{len(shape)}d_{name}"]["cg_to_1e-5"] = {
+                "maxiter": args.cg3d_maxiter, "iterations": [int(i) for i in its],
+                "relres": [float(r) for r in rel], "converged": st_ == 0,
+                "seconds": time.perf_counter() - t0, "precond": "none"}
         del M, v, o
         torch.cuda.empty_cache()
     return out
