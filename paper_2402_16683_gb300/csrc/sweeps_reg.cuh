@@ -488,18 +488,21 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
     for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = 0.0;
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
-  const int W = a.W, CPR = W / CH;
+  // W, the chunks per tile row and the tiles per outer index are powers of two:
+  // shifts and masks instead of run-time divisions
+  const int W = a.W, CPR = W / CH, cpr_sh = __ffs(CPR) - 1;
+  const int nblk_sh = __ffsll(a.nblk) - 1;
   const bool lval = 2 * u < W;
 
   auto tile_base = [&](int64_t unit) -> int64_t {
-    const int64_t o = unit / a.nblk;
-    return o * L * a.inner + (unit - o * a.nblk) * W;
+    const int64_t o = unit >> nblk_sh;
+    return o * L * a.inner + (unit & (a.nblk - 1)) * W;
   };
   auto issue = [&](int64_t unit, int buf) {
     const T* src = a.pro.x + b * a.pro.xs + tile_base(unit);
     T* dst = xin + buf * SM::XS;
     for (int c = threadIdx.x; c < L * CPR; c += blockDim.x) {
-      const int l = c / CPR, j = c - l * CPR;
+      const int l = c >> cpr_sh, j = c & (CPR - 1);
       cp_async16(dst + l * WP + j * CH, src + (int64_t)l * a.inner + j * CH);
     }
   };
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
     for (int c0 = 0; c0 < L * CPR; c0 += blockDim.x) {
       const int c = c0 + threadIdx.x;
       const bool act = c < L * CPR;
-      const int l = act ? c / CPR : 0, j = act ? c - l * CPR : 0;
+      const int l = act ? c >> cpr_sh : 0, j = act ? c & (CPR - 1) : 0;
       const int64_t flat = base + (int64_t)l * a.inner + j * CH;
       const T* src = X + l * WP + j * CH;
       if constexpr (EK == SK_BUF) {
