@@ -263,10 +263,11 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // dA[b][i] = sum_h G[i][h] dh[b][h]; one warp per output.
 template <typename T>
 __global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs,
-                                                    double* dA) {
+                                                    double* dA, double* gzero) {
   const int b = blockIdx.y, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= nb) return;
+  if (gzero != nullptr && lane == 0) gzero[(int64_t)b * nb + i] = 0.0;
   const float* g = G + (int64_t)i * nh;
   const T* d = dh + b * dhs;
   // eight independent loads per lane in flight per round
@@ -396,9 +397,10 @@ int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double
 }
 
 template <typename T>
-int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st) {
+int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st,
+                double* gzero) {
   prof_begin("amp_jvp", (double)nb * nh * 4 + (double)B * (nh * sizeof(T) + nb * 8), st);
-  k_amp_jvp_lin<T><<<dim3((nb + 7) / 8, B), 256, 0, st>>>(G, nb, nh, dh, dhs, dA);
+  k_amp_jvp_lin<T><<<dim3((nb + 7) / 8, B), 256, 0, st>>>(G, nb, nh, dh, dhs, dA, gzero);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -424,7 +426,8 @@ int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int npa
                           int64_t, T*, int64_t, int, cudaStream_t, double*);                      \
   template int amp_jacobian<T>(const AmpPrior&, const double*, int, T*, double*, float*, float*,       \
                                cudaStream_t);                                                          \
-  template int amp_jvp_lin<T>(const float*, int, int, const T*, int64_t, double*, int, cudaStream_t);   \
+  template int amp_jvp_lin<T>(const float*, int, int, const T*, int64_t, double*, int, cudaStream_t,    \
+                              double*);                                                               \
   template int amp_vjp_lin<T>(const float*, int, int, const double*, int, const T*, int64_t, T*,        \
                               int64_t, int, cudaStream_t, double*);
 NRE_INST(float)

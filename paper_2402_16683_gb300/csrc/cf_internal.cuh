@@ -141,6 +141,10 @@ struct Epi {
   int64_t ps;
   int bins;           // accumulate the per-bin sums
   AmpView<T> av;
+  // EPI_AMP with bins: when set, the per-bin sums go into gsum[b][nb] in place
+  // (zeroed before the sweep; FP64 atomic adds of the per-CTA sums) instead
+  // of per-CTA partials, so that the reader sums nothing
+  double* gsum;
   // EPI_AMP with base, last sweep of a metric product: per-CTA partials of
   // sum(base * y) at dot[b * kDotStride + cta] (row sweeps of 2-D / 3-D grids;
   // other sweeps leave them to a separate reduction)
@@ -224,6 +228,20 @@ struct Mid {
 };
 
 // Arguments of one row sweep (last axis, length L).
+// A CTA's per-bin sums: into epi.gsum (atomically) or as partial `part` of
+// nparts for sample b.  Called by all threads after the sums are complete.
+template <typename T>
+__device__ __forceinline__ void store_bins(const Epi<T>& e, double* partials, int b, int nparts, int part,
+                                           const double* hist, int nb) {
+  if (e.gsum != nullptr) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      if (hist[i] != 0.0) atomicAdd(&e.gsum[(int64_t)b * nb + i], hist[i]);
+  } else {
+    double* dst = partials + ((int64_t)b * nparts + part) * nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = hist[i];
+  }
+}
+
 template <typename T>
 struct RowArgs {
   int L, log2L, log2Lmax;
@@ -315,7 +333,8 @@ template <typename T>
 int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double* Jt, float* G, float* Gt,
                  cudaStream_t st);
 template <typename T>
-int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st);
+int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st,
+                double* gzero = nullptr);  // gzero: [B][nb] set to 0 (the next sweep's in-place bin sums)
 template <typename T>
 int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int nparts, const T* base_h,
                 int64_t bhs, T* out_h, int64_t ohs, int B, cudaStream_t st, double* dot = nullptr);

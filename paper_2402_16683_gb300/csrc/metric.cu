@@ -92,6 +92,7 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
       NRE_TRY(ensure(m->amp_Gt, (size_t)nb * nh * sizeof(float)));
       NRE_TRY(ensure(m->amp_eye, (size_t)nh * nh * sizeof(T)));
       NRE_TRY(ensure(m->amp_Jt, (size_t)nh * nb * sizeof(double)));
+      NRE_TRY(ensure(m->gsum, (size_t)m->max_batch * nb * sizeof(double)));
       NRE_TRY(amp_jacobian<T>(amp_prior_of(p), m->state.as<double>(), nh, m->amp_eye.as<T>(),
                               m->amp_Jt.as<double>(), m->amp_G.as<float>(), m->amp_Gt.as<float>(), st));
       m->amp_lin = true;
@@ -131,8 +132,9 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   const int nb = p->n_bins;
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
   if (model) {
-    if (m->amp_lin)
-      NRE_TRY(amp_jvp_lin<T>(m->amp_G.as<float>(), nb, p->n_hyper, v + N, S, m->dA.as<double>(), B, st));
+    if (m->amp_lin)  // also zeroes the in-place bin sums of the last sweep
+      NRE_TRY(amp_jvp_lin<T>(m->amp_G.as<float>(), nb, p->n_hyper, v + N, S, m->dA.as<double>(), B, st,
+                             m->gsum.as<double>()));
     else
       NRE_TRY(amp_jvp<T>(pr, m->state.as<double>(), 0, v + N, S, m->dA.as<double>(), B, st));
     pro.av = metric_view<T>(m);
@@ -144,6 +146,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
     epi.bins = 1;
     epi.xi_p = xp;
     epi.ps = 0;
+    if (m->amp_lin) epi.gsum = m->gsum.as<double>();
   } else {
     pro.av = amp_view<T>(p, nullptr, 0);
     epi.av = pro.av;
@@ -152,8 +155,8 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
                          model ? m->part.as<double>() : nullptr, &np, st));
   if (model) {
-    if (m->amp_lin)
-      NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->part.as<double>(), np, v + N, S, out + N,
+    if (m->amp_lin)  // the bin sums are complete in gsum (one "partial")
+      NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->gsum.as<double>(), 1, v + N, S, out + N,
                              S, B, st, dot));
     else
       NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,

@@ -32,6 +32,7 @@ struct nre_metric {
   // FP32 power model: the amplitude Jacobian at xi_p (see amp_jacobian)
   bool amp_lin = false;
   nre::DevBuf amp_G, amp_Gt, amp_eye, amp_Jt;
+  nre::DevBuf gsum;  // [max_batch][n_bins] in-place bin sums of the last sweep
   nre::DevBuf tmp0, tmp1, part;
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;

@@ -202,12 +202,12 @@ __device__ __forceinline__ void warp_run_add(int key, V val, double* hist) {
   const bool head = lane == 0 || prev != key;
   const unsigned heads = __ballot_sync(full, head);
   if (__all_sync(full, key < 0)) return;
-  const int rid = __popc(heads & (0xffffffffu >> (31 - lane)));
+  // first lane of this lane's run (lane 0 always heads a run)
+  const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const V ov = __shfl_up_sync(full, val, o);
-    const int orid = __shfl_up_sync(full, rid, o);
-    if (lane >= o && orid == rid) val += ov;
+    if (lane - o >= seg) val += ov;
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
   if (tail && key >= 0) atomicAdd(&hist[key], double(val));

@@ -104,7 +104,7 @@ uint64_t footprint(const nre_serve_req* r, const Geom& g, int dtype) {
     b += a256((size_t)amp_state_size((int)nb) * 8) + a256(B * nb * 8) + a256(B * 128 * nb * 8) + a256(N * E) +
          a256(N * 2);
   if (nb > 0 && E == 4)  // amplitude Jacobian of the FP32 metric
-    b += 2 * a256(nb * nh * 4) + a256(nh * nh * E) + a256(nh * nb * 8);
+    b += 2 * a256(nb * nh * 4) + a256(nh * nh * E) + a256(nh * nb * 8) + a256(B * nb * 8);
   // CG workspace (r, p, q and z) and scalars
   b += (pc ? 4 : 3) * a256(B * S * E) + a256(B * CG_SC_N * 8) + a256(3 * B * 64 * 8 + B * 4);
   if (pc && nb > 0)

@@ -142,11 +142,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
       for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
         const int hs = i / a.nb, bn = i - hs * a.nb;
         const int sample = 2 * (blockIdx.x * a.nU) + hs;
-        if (sample < a.B) a.partials[(int64_t)sample * a.nb + bn] = hist[i];
+        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = hist[i];
       }
     } else {
-      double* dst = a.partials + ((int64_t)bsample * gridDim.x + blockIdx.x) * a.nb;
-      for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+      store_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, a.nb);
     }
   }
 }
@@ -209,8 +208,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_col_sweep(ColArgs<T> a) {
     __syncthreads();
   }
   if (bins) {
-    double* dst = a.partials + ((int64_t)b * gridDim.x + blockIdx.x) * a.nb;
-    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+    store_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, a.nb);
   }
 }
 

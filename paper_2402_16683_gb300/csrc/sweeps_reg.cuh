@@ -119,7 +119,7 @@ struct RowSmem {
   static constexpr int STG = (XSZ > LNSZ ? XSZ : LNSZ);
   static constexpr int STGA = (STG + 3) / 4 * 4;          // 16-byte multiple
   static size_t bytes(bool base, int nb, int nhist_bins) {
-    return (size_t)2 * L * sizeof(T) + (size_t)2 * STGA * sizeof(T) + (base ? (size_t)2 * XSZ * sizeof(T) : 0) +
+    return (size_t)2 * L * sizeof(T) + (size_t)2 * STGA * sizeof(T) + (base ? (size_t)XSZ * sizeof(T) : 0) +
            (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
   }
 };
@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   C* tw = reinterpret_cast<C*>(smem_raw);
   T* stage = reinterpret_cast<T*>(tw + L);                  // [2][STGA]
   const bool sbase = a.epi.mode == EPI_AMP && a.epi.base != nullptr;
-  T* bstage = stage + 2 * SM::STGA;                          // [2][XSZ] when staged
+  T* bstage = stage + 2 * SM::STGA;                          // [XSZ]: the current units' base rows
   const int nbp = (a.nb + 3) / 4 * 4;
-  T* sA = bstage + (sbase ? 2 * SM::XSZ : 0);
+  T* sA = bstage + (sbase ? SM::XSZ : 0);
   T* sdA = sA + nbp;
   double* hist = reinterpret_cast<double*>(sdA + nbp);
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
@@ -160,20 +160,29 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
 
-  auto issue = [&](int ug, int buf) {
+  // input rows of unit group ug into stage half buf (prefetched one iteration
+  // ahead); with base, the base rows of ug into bstage (issued at the start of
+  // their own iteration: they are read only by the epilogue, so one buffer
+  // suffices and the staging plan stays small)
+  auto issue = [&](int ug, int buf, bool base_only) {
     T* dst = stage + buf * SM::STGA;
-    T* bdst = bstage + buf * SM::XSZ;
-    for (int c = threadIdx.x; c < NU * SLOTS * CPR; c += blockDim.x) {
+    T* bdst = bstage;
+    // a whole number of chunks per thread (the block has RowShape<L>::NT threads)
+    constexpr int NCH = NU * SLOTS * CPR, TRIPS = NCH / RowShape<L>::NT;
+    static_assert(NCH % RowShape<L>::NT == 0, "chunks per thread");
+#pragma unroll
+    for (int k = 0; k < TRIPS; ++k) {
+      const int c = threadIdx.x + k * RowShape<L>::NT;
       const int rr = c / CPR, j = c - rr * CPR;
       const int uu = rr / SLOTS, sl = rr - uu * SLOTS;
       const int un = ug + uu;
-      if (un >= a.n_units) continue;
       const int samp = PM == 1 ? 2 * un + sl : bsample;
-      if (PM == 1 && samp >= a.B) continue;
-      const int row = PM == 1 ? 0 : __ldg(&a.grows[un * SLOTS + sl]);
-      const int64_t g = (int64_t)row * L + j * CH;
-      cp_async16(dst + rr * L + j * CH, a.pro.x + samp * a.pro.xs + g);
-      if (sbase) cp_async16(bdst + rr * L + j * CH, a.epi.base + samp * a.epi.bs + g);
+      if (un < a.n_units && (PM != 1 || samp < a.B)) {
+        const int row = PM == 1 ? 0 : __ldg(&a.grows[un * SLOTS + sl]);
+        const int64_t g = (int64_t)row * L + j * CH;
+        if (base_only) cp_async16(bdst + rr * L + j * CH, a.epi.base + samp * a.epi.bs + g);
+        else cp_async16(dst + rr * L + j * CH, a.pro.x + samp * a.pro.xs + g);
+      }
     }
   };
 
@@ -182,13 +191,15 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   double dacc = 0.0;
   const int ustride = gridDim.x * NU;
   int u0 = blockIdx.x * NU;
-  if (u0 < a.n_units) issue(u0, 0);
+  if (u0 < a.n_units) issue(u0, 0, false);
   cp_commit();
   for (int it = 0; u0 < a.n_units; u0 += ustride, ++it) {
     const int cur = it & 1;
-    if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1);
+    if (sbase) issue(u0, 0, true);  // group B: this iteration's base rows
     cp_commit();
-    cp_wait<1>();
+    if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1, false);  // group A: next input
+    cp_commit();
+    cp_wait<2>();  // everything but B and A: this iteration's input rows
     __syncthreads();
     const int unit = u0 + u;
     const bool valid = unit < a.n_units;
@@ -284,7 +295,11 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
       reg_fft<C, L, LPU>(v, smc, tw, t, sync);
     }
     reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
-    const T* BV = bstage + cur * SM::XSZ + u * SLOTS * L;
+    if (sbase) {
+      cp_wait<1>();  // everything but group A: the base rows
+      __syncthreads();
+    }
+    const T* BV = bstage + u * SLOTS * L;
     if constexpr (EK == SK_TAB && PM >= 2) {
       // The metric's epilogue in two phases so the per-pixel loads (bins,
       // expansion point) are all in flight before they are used:
@@ -436,11 +451,10 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
       for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
         const int hs = i / a.nb, bn = i - hs * a.nb;
         const int sample = 2 * (blockIdx.x * NU) + hs;
-        if (sample < a.B) a.partials[(int64_t)sample * a.nb + bn] = hist[i];
+        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = hist[i];
       }
     } else {
-      double* dst = a.partials + ((int64_t)bsample * gridDim.x + blockIdx.x) * a.nb;
-      for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+      store_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, a.nb);
     }
   }
 }
@@ -586,8 +600,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
   cp_wait<0>();
   if (bins) {
     __syncthreads();
-    double* dst = a.partials + ((int64_t)b * gridDim.x + blockIdx.x) * a.nb;
-    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) dst[i] = hist[i];
+    store_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, a.nb);
   }
 }
 
