@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-metric-grids", action="store_true",
                     help="skip the metric-product roofline leg on 2-D 1024^2 and 3-D 256^3")
     ap.add_argument("--metric-batch", type=int, default=8)
+    ap.add_argument("--icr-batch", type=int, default=32)
     ap.add_argument("--cg3d-maxiter", type=int, default=300,
                     help="iteration cap of the 3-D masked batched CG solve in the metric leg")
     ap.add_argument("--serve-requests", type=int, default=100,
@@ -445,7 +446,63 @@ def run_metric_grids(args, lib):
                 "seconds": time.perf_counter() - t0, "precond": "none"}
         del M, v, o
         torch.cuda.empty_cache()
+    out["icr_8_to_1024"] = run_icr(args, lib, flush, stream, peak)
     return out
+
+
+def run_icr(args, lib, flush, stream, peak):
+    """ICR on the log-radial chart refined 8^2 -> 1024^2 (7 levels), Matern-3/2
+    (length scale 0.1, unit variance), FP32, batch 32: forward (= JVP, the
+    model is linear in xi) and the hand-written VJP; fields/s and the HBM
+    fraction of all refinement kernels together."""
+    import ctypes as C
+
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+    from paper_2402_16683_gb300 import _lib
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = args.icr_batch
+    icr = nre.ICR(n0=8, n_levels=7, rho=0.1, var=1.0, dtype=torch.float32)
+    g = np.random.default_rng(synth.SEED_POS)
+    xi = icr.pad(torch.tensor(g.standard_normal((B, icr.latent_size)), dtype=torch.float32, device=dev))
+    ct = torch.tensor(g.standard_normal((B, icr.n_out)), dtype=torch.float32, device=dev)
+    res = {"batch": B, "levels": 7, "grid": [1024, 1024]}
+    for name, fn in (("forward", lambda: icr.forward(xi)), ("vjp", lambda: icr.vjp(xi, ct))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+
+        def timed(n):
+            ev = []
+            for _ in range(n):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            return sum(a.elapsed_time(b_) for a, b_ in ev) / n
+
+        n = max(5, args.steps)
+        ms = timed(n)
+        lib.nre_prof_enable(1)
+        timed(n)
+        lib.nre_prof_enable(0)
+        buf = C.create_string_buffer(1 << 16)
+        _lib.check(lib.nre_prof_report(buf, len(buf)))
+        kern = json.loads(buf.value.decode())
+        kms = sum(x[1] for x in kern.values())
+        kbytes = sum(x[2] for x in kern.values())
+        res[name] = {"fields_per_s": B / (ms / 1e3), "ms": ms, "bytes": kbytes / n,
+                     "achieved_GBps": kbytes / (kms / 1e3) / 1e9, "frac": kbytes / (kms / 1e3) / 1e9 / peak,
+                     "kernels": {k: {"launches_per_call": x[0] / n, "us_per_call": 1e3 * x[1] / n,
+                                     "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None}
+                                 for k, x in kern.items()}}
+    return res
 
 
 # ----------------------------------------------------------------- serving leg
