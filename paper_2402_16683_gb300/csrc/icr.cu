@@ -11,9 +11,10 @@
 // L_i = chol(K_ff - R_i K_cf).  Rotation invariance makes R, L depend only on
 // (level, radial row); they are assembled in FP64 on the host.
 //
-// Kernels: one thread per coarse pixel.  The forward reads the 9 neighbours
-// (coalesced along the angular axis) and the 2x2 excitations as two 2-vector
-// loads, and writes the children the same way.  The adjoint is a deterministic
+// Kernels: four coarse pixels per thread (one per thread when the level size
+// is not a multiple of 4).  The forward reads the row's matrices once, the
+// 3 x 6 neighbourhood window (coalesced along the angular axis) and the 2 x 8
+// excitations as 16-byte vectors, and writes the children the same way.  The adjoint is a deterministic
 // gather: each coarse pixel collects R^T g from the children of every coarse
 // pixel whose neighbourhood contains it (up to 5 radial rows near the clamped
 // edges), and writes L^T g for its own children.
@@ -151,24 +152,34 @@ bool level_row_matrices(const nre_icr_plan* p, int level, int i, double* out) {
 
 // ---------------------------------------------------------------- kernels
 template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// s_0 = L0 xi_0 per sample: one warp per output row (lanes along the row).
+template <typename T>
 __global__ void k_icr_level0(const T* L0, const T* xi, int64_t xs, T* s0, int64_t ss, int n2) {
-  const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < n2; i += nw) {
     T acc = T(0);
-    for (int j = 0; j <= i; ++j) acc += L0[i * n2 + j] * xi[b * xs + j];
-    s0[b * ss + i] = acc;
+    for (int j = lane; j <= i; j += 32) acc += L0[i * n2 + j] * xi[b * xs + j];
+    acc = warp_sum_t(acc);
+    if (lane == 0) s0[b * ss + i] = acc;
   }
 }
 
+// out = base + L0^T g0 per sample: one warp per output (lanes down the column).
 template <typename T>
 __global__ void k_icr_level0_t(const T* L0, const T* g0, int64_t gs, T* out, int64_t os,
                                const T* base, int64_t bs, int n2) {
-  const int b = blockIdx.y;
-  for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x >> 5; j < n2; j += nw) {
     T acc = T(0);
-    for (int i = j; i < n2; ++i) acc += L0[i * n2 + j] * g0[b * gs + i];
-    if (base) acc += base[b * bs + j];
-    out[b * os + j] = acc;
+    for (int i = j + lane; i < n2; i += 32) acc += L0[i * n2 + j] * g0[b * gs + i];
+    acc = warp_sum_t(acc);
+    if (lane == 0) out[b * os + j] = acc + (base ? base[b * bs + j] : T(0));
   }
 }
 
@@ -295,6 +306,197 @@ __global__ void __launch_bounds__(ICR_THREADS) k_icr_refine_t(int nc, const T* _
   g_c[b * gcs + pix] = acc;
 }
 
+// Four consecutive values at p (16-byte aligned for float, two 16-byte
+// vectors for double).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* o) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), c = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* o) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+  }
+}
+
+// Four coarse pixels per thread (columns j0..j0+3 of radial row i; block
+// (32, 4): 128 columns x 4 rows): the row's matrices, the 3 x 6 neighbourhood
+// window and the 2 x 8 children are read once for the four, with 16-byte
+// loads.  Needs nc % 4 == 0 and 16-byte aligned level offsets (n0 % 4 == 0).
+constexpr int ICR4_X = 32, ICR4_Y = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(ICR4_X * ICR4_Y) k_icr_refine4(int nc, const T* __restrict__ mats,
+                                                                const T* s_c, int64_t scs, const T* xi_f,
+                                                                int64_t xs, T* s_f, int64_t sfs, const T* scale) {
+  const int i = blockIdx.y * ICR4_Y + threadIdx.y, b = blockIdx.z;
+  const int j0 = 4 * (blockIdx.x * ICR4_X + threadIdx.x);
+  if (i >= nc || j0 >= nc) return;
+  const T* M = mats + (int64_t)i * MAT;
+  T m[MAT];
+#pragma unroll
+  for (int k = 0; k < MAT; ++k) m[k] = __ldg(&M[k]);
+  const int w = window(nc, i);
+  const int jm = j0 == 0 ? nc - 1 : j0 - 1, jp = j0 + 4 == nc ? 0 : j0 + 4;
+  const T* sc = s_c + b * scs;
+  T nb[3][6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T* row = sc + (int64_t)(w + a) * nc;
+    nb[a][0] = row[jm];
+    ld4(row + j0, &nb[a][1]);
+    nb[a][5] = row[jp];
+  }
+  const int nf = 2 * nc;
+  const int64_t f0 = (int64_t)(2 * i) * nf + 2 * j0;
+  const T* xf = xi_f + b * xs + f0;
+  T e0[8], e1[8];
+  ld4(xf, e0);
+  ld4(xf + 4, e0 + 4);
+  ld4(xf + nf, e1);
+  ld4(xf + nf + 4, e1 + 4);
+  T o0[8], o1[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T nq[9] = {nb[0][q], nb[0][q + 1], nb[0][q + 2], nb[1][q], nb[1][q + 1],
+                     nb[1][q + 2], nb[2][q], nb[2][q + 1], nb[2][q + 2]};
+    const T e[4] = {e0[2 * q], e0[2 * q + 1], e1[2 * q], e1[2 * q + 1]};
+    T o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int n = 0; n < 9; ++n) acc += m[k * 9 + n] * nq[n];
+#pragma unroll
+      for (int mm = 0; mm <= k; ++mm) acc += m[36 + k * 4 + mm] * e[mm];
+      o[k] = acc;
+    }
+    o0[2 * q] = o[0];
+    o0[2 * q + 1] = o[1];
+    o1[2 * q] = o[2];
+    o1[2 * q + 1] = o[3];
+  }
+  if (scale) {
+    T s0[8], s1[8];
+    ld4(scale + f0, s0);
+    ld4(scale + f0 + 4, s0 + 4);
+    ld4(scale + f0 + nf, s1);
+    ld4(scale + f0 + nf + 4, s1 + 4);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      o0[k] *= s0[k];
+      o1[k] *= s1[k];
+    }
+  }
+  T* sf = s_f + b * sfs + f0;
+  st4(sf, o0);
+  st4(sf + 4, o0 + 4);
+  st4(sf + nf, o1);
+  st4(sf + nf + 4, o1 + 4);
+}
+
+// Adjoint with four coarse pixels per thread (as k_icr_refine_t).
+template <typename T>
+__global__ void __launch_bounds__(ICR4_X * ICR4_Y) k_icr_refine4_t(int nc, const T* __restrict__ mats,
+                                                                  const T* g_f, int64_t gfs, T* g_c, int64_t gcs,
+                                                                  T* g_xi, int64_t gxs, const T* base, int64_t bs) {
+  const int ip = blockIdx.y * ICR4_Y + threadIdx.y, b = blockIdx.z;
+  const int jp0 = 4 * (blockIdx.x * ICR4_X + threadIdx.x);
+  if (ip >= nc || jp0 >= nc) return;
+  const int nf = 2 * nc;
+  const T* gf = g_f + b * gfs;
+  // own children: L^T g (+ base)
+  {
+    const int64_t f0 = (int64_t)(2 * ip) * nf + 2 * jp0;
+    T g0[8], g1[8];
+    ld4(gf + f0, g0);
+    ld4(gf + f0 + 4, g0 + 4);
+    ld4(gf + f0 + nf, g1);
+    ld4(gf + f0 + nf + 4, g1 + 4);
+    const T* ML = mats + (int64_t)ip * MAT + 36;
+    T l[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) l[k] = __ldg(&ML[k]);
+    T o0[8], o1[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T g[4] = {g0[2 * q], g0[2 * q + 1], g1[2 * q], g1[2 * q + 1]};
+      T o[4];
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = mm; k < 4; ++k) acc += l[k * 4 + mm] * g[k];
+        o[mm] = acc;
+      }
+      o0[2 * q] = o[0];
+      o0[2 * q + 1] = o[1];
+      o1[2 * q] = o[2];
+      o1[2 * q + 1] = o[3];
+    }
+    if (base) {
+      const T* bb = base + b * bs + f0;
+      T b0[8], b1[8];
+      ld4(bb, b0);
+      ld4(bb + 4, b0 + 4);
+      ld4(bb + nf, b1);
+      ld4(bb + nf + 4, b1 + 4);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        o0[k] += b0[k];
+        o1[k] += b1[k];
+      }
+    }
+    T* gx = g_xi + b * gxs + f0;
+    st4(gx, o0);
+    st4(gx + 4, o0 + 4);
+    st4(gx + nf, o1);
+    st4(gx + nf + 4, o1 + 4);
+  }
+  // gather R^T g over the coarse pixels whose neighbourhood holds (ip, jp0 + q):
+  // coarse columns jp0 - 1 .. jp0 + 4, i.e. fine columns 2 jp0 - 2 .. 2 jp0 + 9
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  const int jm = jp0 == 0 ? nc - 1 : jp0 - 1, jpp = jp0 + 4 == nc ? 0 : jp0 + 4;
+  const int i_lo = ip - 2 < 0 ? 0 : ip - 2, i_hi = ip + 2 > nc - 1 ? nc - 1 : ip + 2;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const int a = ip - window(nc, i);
+    if (a < 0 || a > 2) continue;
+    const T* MR = mats + (int64_t)i * MAT;
+    T G[2][12];  // fine rows 2i, 2i+1; entry 2 (jj + 1) + c for coarse column jp0 + jj, child column c
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const T* row = gf + (int64_t)(2 * i + r) * nf;
+      G[r][0] = row[2 * jm];
+      G[r][1] = row[2 * jm + 1];
+      ld4(row + 2 * jp0, &G[r][2]);
+      ld4(row + 2 * jp0 + 4, &G[r][6]);
+      G[r][10] = row[2 * jpp];
+      G[r][11] = row[2 * jpp + 1];
+    }
+#pragma unroll
+    for (int bcol = 0; bcol < 3; ++bcol) {
+      const int n = 3 * a + bcol;
+      const T r0 = __ldg(&MR[0 * 9 + n]), r1 = __ldg(&MR[1 * 9 + n]), r2 = __ldg(&MR[2 * 9 + n]),
+              r3 = __ldg(&MR[3 * 9 + n]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t0 = 2 * (q - bcol + 2);  // coarse column jp0 + q - (bcol - 1)
+        acc[q] += r0 * G[0][t0] + r1 * G[0][t0 + 1] + r2 * G[1][t0] + r3 * G[1][t0 + 1];
+      }
+    }
+  }
+  st4(g_c + b * gcs + (int64_t)ip * nc + jp0, acc);
+}
+
 template <typename T>
 __global__ void k_scale_sqrt(const T* w, const T* x, int64_t xs, T* y, int64_t ys, int64_t n) {
   const int b = blockIdx.y;
@@ -328,7 +530,7 @@ int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cud
   const T* L0 = p->L0.as<T>();
   const T* mats = p->mats.as<T>();
   prof_begin("icr_level0", (double)B * 2 * n2 * sizeof(T), st);
-  k_icr_level0<T><<<dim3(1, B), 64, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
+  k_icr_level0<T><<<dim3(1, B), 256, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   for (int l = 0; l < p->n_levels; ++l) {
@@ -337,9 +539,15 @@ int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cud
     T* out = last ? s : bufs[(l + 1) & 1];
     const int64_t os = last ? p->n_out : big;
     prof_begin("icr_refine", (double)nc * nc * sizeof(T) * (9.0 * B + (last && scale ? 4.0 : 0.0)), st);
-    k_icr_refine<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
-        nc, mats + p->mat_off[l], bufs[l & 1], big, xi + p->offsets[l + 1], p->stride, out, os,
-        last ? scale : nullptr);
+    if (nc % 4 == 0 && p->n0 % 4 == 0)
+      k_icr_refine4<T><<<dim3((nc / 4 + ICR4_X - 1) / ICR4_X, (nc + ICR4_Y - 1) / ICR4_Y, B),
+                         dim3(ICR4_X, ICR4_Y), 0, st>>>(nc, mats + p->mat_off[l], bufs[l & 1], big,
+                                                        xi + p->offsets[l + 1], p->stride, out, os,
+                                                        last ? scale : nullptr);
+    else
+      k_icr_refine<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
+          nc, mats + p->mat_off[l], bufs[l & 1], big, xi + p->offsets[l + 1], p->stride, out, os,
+          last ? scale : nullptr);
     prof_end(st);
     NRE_CHECK_LAUNCH();
   }
@@ -360,9 +568,15 @@ int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, in
     const int nc = p->sizes[l];
     T* gc = bufs[which];
     prof_begin("icr_refine_t", (double)nc * nc * sizeof(T) * B * (base ? 13.0 : 9.0), st);
-    k_icr_refine_t<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
-        nc, mats + p->mat_off[l], gin, gis, gc, big, g + p->offsets[l + 1], p->stride,
-        base ? base + p->offsets[l + 1] : nullptr, p->stride);
+    if (nc % 4 == 0 && p->n0 % 4 == 0)
+      k_icr_refine4_t<T><<<dim3((nc / 4 + ICR4_X - 1) / ICR4_X, (nc + ICR4_Y - 1) / ICR4_Y, B),
+                           dim3(ICR4_X, ICR4_Y), 0, st>>>(nc, mats + p->mat_off[l], gin, gis, gc, big,
+                                                          g + p->offsets[l + 1], p->stride,
+                                                          base ? base + p->offsets[l + 1] : nullptr, p->stride);
+    else
+      k_icr_refine_t<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
+          nc, mats + p->mat_off[l], gin, gis, gc, big, g + p->offsets[l + 1], p->stride,
+          base ? base + p->offsets[l + 1] : nullptr, p->stride);
     prof_end(st);
     NRE_CHECK_LAUNCH();
     gin = gc;
@@ -371,7 +585,7 @@ int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, in
   }
   const int n2 = p->n0 * p->n0;
   prof_begin("icr_level0_t", (double)B * (base ? 3 : 2) * n2 * sizeof(T), st);
-  k_icr_level0_t<T><<<dim3(1, B), 64, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
+  k_icr_level0_t<T><<<dim3(1, B), 256, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
