@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--serve-plain-cap-s", type=float, default=90.0,
                     help="stop the sequential FP64 arm after this many seconds")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--icr-only", action="store_true", help="run only the ICR leg")
     return ap.parse_args()
 
 
@@ -202,6 +203,13 @@ def run_ours(args, rank, world):
     if args.serve_only:
         if rank == 0:
             print(json.dumps({"serve": run_serve(args)}), flush=True)
+        return
+    if args.icr_only:
+        lib0 = _lib.load()
+        dev0 = torch.device("cuda", torch.cuda.current_device())
+        fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev0)
+        if rank == 0:
+            print(json.dumps({"icr": run_icr(args, lib0, fl, torch.cuda.current_stream(), peaks()[0])}), flush=True)
         return
     lib = _lib.load()
     lib.nre_launch_count.restype = C.c_ulonglong

@@ -158,11 +158,12 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-// s_0 = L0 xi_0 per sample: one warp per output row (lanes along the row).
+// s_0 = L0 xi_0 per sample: one warp per output row (lanes along the row), all
+// rows in flight at once.
 template <typename T>
 __global__ void k_icr_level0(const T* L0, const T* xi, int64_t xs, T* s0, int64_t ss, int n2) {
-  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x >> 5; i < n2; i += nw) {
+  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.x;
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n2; i += nw) {
     T acc = T(0);
     for (int j = lane; j <= i; j += 32) acc += L0[i * n2 + j] * xi[b * xs + j];
     acc = warp_sum_t(acc);
@@ -174,8 +175,8 @@ __global__ void k_icr_level0(const T* L0, const T* xi, int64_t xs, T* s0, int64_
 template <typename T>
 __global__ void k_icr_level0_t(const T* L0, const T* g0, int64_t gs, T* out, int64_t os,
                                const T* base, int64_t bs, int n2) {
-  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = threadIdx.x >> 5; j < n2; j += nw) {
+  const int b = blockIdx.y, lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.x;
+  for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n2; j += nw) {
     T acc = T(0);
     for (int i = j + lane; i < n2; i += 32) acc += L0[i * n2 + j] * g0[b * gs + i];
     acc = warp_sum_t(acc);
@@ -530,7 +531,7 @@ int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cud
   const T* L0 = p->L0.as<T>();
   const T* mats = p->mats.as<T>();
   prof_begin("icr_level0", (double)B * 2 * n2 * sizeof(T), st);
-  k_icr_level0<T><<<dim3(1, B), 256, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
+  k_icr_level0<T><<<dim3((n2 + 7) / 8, B), 256, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   for (int l = 0; l < p->n_levels; ++l) {
@@ -585,7 +586,7 @@ int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, in
   }
   const int n2 = p->n0 * p->n0;
   prof_begin("icr_level0_t", (double)B * (base ? 3 : 2) * n2 * sizeof(T), st);
-  k_icr_level0_t<T><<<dim3(1, B), 256, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
+  k_icr_level0_t<T><<<dim3((n2 + 7) / 8, B), 256, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
