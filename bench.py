@@ -192,6 +192,23 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------- GPU leg
+def max_over_ranks(t, world, device):
+    """The slowest rank's time (replicas run the same work): all-reduce MAX over
+    the process group when world > 1."""
+    if world <= 1:
+        return t
+    import torch
+    v = torch.tensor([t], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
+    return float(v.item())
+
+
+def replica_throughput(units_per_rank, world, t_max):
+    """Whole-job throughput of `world` replicas: all ranks' units over the
+    slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def run_ours(args, rank, world):
     import ctypes as C
 
@@ -274,15 +291,8 @@ def run_ours(args, rank, world):
     buf = C.create_string_buffer(1 << 16)
     _lib.check(lib.nre_prof_report(buf, len(buf)))
     kern = json.loads(buf.value.decode())
-    t_local = ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    units = world * args.steps * B * CG_ITERS
-    value = units / t_max
+    t_max = max_over_ranks(ms / 1e3, world, dev)
+    value = replica_throughput(args.steps * B * CG_ITERS, world, t_max)
 
     # dominant kernel: largest total device time in the timed region
     name, (cnt, kms, kbytes) = max(kern.items(), key=lambda kv: kv[1][1])
@@ -358,12 +368,8 @@ def run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier):
         ev.append((e0, e1))
     barrier()
     e_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
-    e_t = e_ms / 1e3
-    if world > 1:
-        t = torch.tensor([e_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e_t = float(t.item())
-    return {"value": world * e_steps * B * CG_ITERS / e_t, "unit": UNIT,
+    e_t = max_over_ranks(e_ms / 1e3, world, dev)
+    return {"value": replica_throughput(e_steps * B * CG_ITERS, world, e_t), "unit": UNIT,
             "h2d_bytes_per_step": int(h_xi.numel() * 4 + h_eta.numel() * 4),
             "d2h_bytes_per_step": int(h_x.numel() * 4)}
 
