@@ -84,6 +84,28 @@ __device__ __forceinline__ void for_vec(int64_t n, F f) {
   for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) f(i, 1);
 }
 
+// As for_vec, U vectors per thread and step: fv(idx, ok) gets the element
+// indices of U vectors (ok: in range) so that it can issue all their loads
+// before using any; fs(i) handles one tail entry.  The vectors a thread visits
+// come in the same order as in for_vec.
+template <typename T, int U, class FV, class FS>
+__device__ __forceinline__ void for_vec_u(int64_t n, FV fv, FS fs) {
+  constexpr int W = V16<T>::W;
+  const int64_t nv = n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += U * stride) {
+    int64_t idx[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      idx[u] = (v + u * stride) * W;
+      ok[u] = v + u * stride < nv;
+    }
+    fv(idx, ok);
+  }
+  for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) fs(i);
+}
+
 template <typename T>
 __device__ __forceinline__ V16<T> ldv(const T* p) { return *reinterpret_cast<const V16<T>*>(p); }
 template <typename T>
@@ -163,7 +185,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, i
 // system) every block forms alpha = r.r / p.q itself; the last block of the
 // system, which alone rewrites r.r, starts only after every block has read it.
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS) k_cg_update(T* x, T* r, const T* p, const T* q, int64_t n,
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T* p, const T* q, int64_t n,
                                                          int64_t S, double* sc, double* rr_part,
                                                          unsigned* counter, double rtol, const double* pq) {
   const int b = blockIdx.y;
@@ -178,34 +200,48 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(T* x, T* r, const T* p
   }
   const int64_t off = (int64_t)b * S;
   double acc = 0.0;
-  for_vec<T>(n, [&](int64_t i, int w) {
-    T run = T(0);
-    if (w > 1) {
-      V16<T> ri = ldv(r + off + i);
-      if (active) {
-        V16<T> xi = ldv(x + off + i);
-        const V16<T> pi = ldv(p + off + i), qi = ldv(q + off + i);
+  constexpr int U = 2;
+  for_vec_u<T, U>(
+      n,
+      [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
+        V16<T> ri[U], xi[U], pi[U], qi[U];
 #pragma unroll
-        for (int k = 0; k < V16<T>::W; ++k) {
-          xi.e[k] += alpha * pi.e[k];
-          ri.e[k] -= alpha * qi.e[k];
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+            ri[u] = ldv(r + off + idx[u]);
+            if (active) {
+              xi[u] = ldv(x + off + idx[u]);
+              pi[u] = ldv(p + off + idx[u]);
+              qi[u] = ldv(q + off + idx[u]);
+            }
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+            if (active) {
+#pragma unroll
+              for (int k = 0; k < V16<T>::W; ++k) {
+                xi[u].e[k] += alpha * pi[u].e[k];
+                ri[u].e[k] -= alpha * qi[u].e[k];
+              }
+              stv(x + off + idx[u], xi[u]);
+              stv(r + off + idx[u], ri[u]);
+            }
+            T run = T(0);  // one vector
+#pragma unroll
+            for (int k = 0; k < V16<T>::W; ++k) run += ri[u].e[k] * ri[u].e[k];
+            acc += double(run);
+          }
+      },
+      [&](int64_t i) {
+        T ri = r[off + i];
+        if (active) {
+          x[off + i] += alpha * p[off + i];
+          ri -= alpha * q[off + i];
+          r[off + i] = ri;
         }
-        stv(x + off + i, xi);
-        stv(r + off + i, ri);
-      }
-#pragma unroll
-      for (int k = 0; k < V16<T>::W; ++k) run += ri.e[k] * ri.e[k];
-    } else {
-      T ri = r[off + i];
-      if (active) {
-        x[off + i] += alpha * p[off + i];
-        ri -= alpha * q[off + i];
-        r[off + i] = ri;
-      }
-      run = ri * ri;
-    }
-    acc += double(run);
-  });
+        acc += double(ri * ri);
+      });
   finish_partial(acc, rr_part, counter, [&](double rr_new) {
     if (c[SC_ACTIVE] == 0.0) {
       c[SC_BETA] = 0.0;
@@ -223,27 +259,35 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(T* x, T* r, const T* p
 
 // p = r + beta p with beta from the update kernel (0 for a frozen system).
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS) k_cg_pupdate(T* p, const T* r, int64_t n, int64_t S,
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* p, const T* r, int64_t n, int64_t S,
                                                           const double* sc) {
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
   if (c[SC_ACTIVE] == 0.0) return;
   const T beta = T(c[SC_BETA]);
   const int64_t off = (int64_t)b * S;
-  for_vec<T>(n, [&](int64_t i, int w) {
-    if (w > 1) {
-      const V16<T> ri = ldv(r + off + i);
-      V16<T> pi = ldv(p + off + i);
+  constexpr int U = 4;
+  for_vec_u<T, U>(
+      n,
+      [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
+        V16<T> ri[U], pi[U];
 #pragma unroll
-      for (int k = 0; k < V16<T>::W; ++k) pi.e[k] = ri.e[k] + beta * pi.e[k];
-      stv(p + off + i, pi);
-    } else {
-      p[off + i] = r[off + i] + beta * p[off + i];
-    }
-  });
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+            ri[u] = ldv(r + off + idx[u]);
+            pi[u] = ldv(p + off + idx[u]);
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+#pragma unroll
+            for (int k = 0; k < V16<T>::W; ++k) pi[u].e[k] = ri[u].e[k] + beta * pi[u].e[k];
+            stv(p + off + idx[u], pi[u]);
+          }
+      },
+      [&](int64_t i) { p[off + i] = r[off + i] + beta * p[off + i]; });
 }
 
-// Device pointers of the CG workspace of a batch of B systems.
 template <typename T>
 struct CGWork {
   T *r, *p, *q;
