@@ -244,13 +244,19 @@ __global__ void k_eye(T* e, int n) {
     e[k] = (k / n == k % n) ? T(1) : T(0);
 }
 
+// Jacobian copies in FP32 with rows padded to a multiple of four floats
+// (zeros), so that the products below read them as 16-byte vectors:
+// G [nb][nhp] and Gt [nh][nbp], nhp / nbp = nh / nb rounded up to 4.
 __global__ void k_jac_store(const double* Jt, int nh, int nb, float* G, float* Gt) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nh * nb;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int h = (int)(k / nb), i = (int)(k % nb);
-    const float v = float(Jt[k]);
-    Gt[k] = v;                     // [nh][nb]
-    G[(int64_t)i * nh + h] = v;    // [nb][nh]
+  const int nhp = (nh + 3) & ~3, nbp = (nb + 3) & ~3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nb * nhp; k += stride) {
+    const int i = (int)(k / nhp), h = (int)(k % nhp);
+    G[k] = h < nh ? float(Jt[(int64_t)h * nb + i]) : 0.f;
+  }
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nh * nbp; k += stride) {
+    const int h = (int)(k / nbp), i = (int)(k % nbp);
+    Gt[k] = i < nb ? float(Jt[(int64_t)h * nb + i]) : 0.f;
   }
 }
 
@@ -260,7 +266,13 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// dA[b][i] = sum_h G[i][h] dh[b][h]; one warp per output.
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+
+// dA[b][i] = sum_h G[i][h] dh[b][h] (G rows padded to nhp floats); one warp
+// per output, each lane with eight loads of G and eight of dh in flight per
+// round, FP32 arithmetic (the FP64 units of this part are a small fraction of
+// its FP32 rate).  Staging dh in shared memory measured slower: the barrier
+// puts a second round trip on the path of this latency-bound kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs,
                                                     double* dA, double* gzero) {
@@ -268,9 +280,8 @@ __global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= nb) return;
   if (gzero != nullptr && lane == 0) gzero[(int64_t)b * nb + i] = 0.0;
-  const float* g = G + (int64_t)i * nh;
+  const float* g = G + (int64_t)i * ((nh + 3) & ~3);
   const T* d = dh + b * dhs;
-  // eight independent loads per lane in flight per round
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int h0 = 0; h0 < nh; h0 += 256) {
 #pragma unroll
@@ -283,49 +294,74 @@ __global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int
   if (lane == 0) dA[(int64_t)b * nb + i] = double(t);
 }
 
-// out_h[b] = base_h[b] + G^T gA[b], gA[b] = sum_c partials[b][c][:]; CTAs of
-// 32 outputs (8 warps, 4 outputs each: 32 loads per lane in flight); with
-// `dot`, also the CTA's share of sum(base_h * out_h) at dot[b][kDotHyper + cta].
+// out_h[b] = base_h[b] + G^T g[b] with the per-bin sums g[b] complete in
+// gsum[b][nb] (nb <= 1024); CTAs of 32 outputs, 8 warps of 4 rows of Gt,
+// g[b] staged in shared memory as FP32.  With `dot`, also the CTA's share of
+// sum(base_h * out_h) at dot[b][kDotHyper + cta].  FP32 arithmetic; FP64 only
+// for the one conversion of each staged sum and of the CTA's share.
 template <typename T>
-__global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials,
-                                                    int nparts, const T* base, int64_t bhs, T* out, int64_t ohs,
+__global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum,
+                                                    const T* base, int64_t bhs, T* out, int64_t ohs,
                                                     double* dot) {
-  __shared__ float gA[1024];
-  __shared__ double red[8];
+  __shared__ float4 sg[256];
+  __shared__ float red[8];
   const int b = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x)
-    gA[i] = float(sum_strided(partials + (int64_t)b * nparts * nb + i, nparts, nb));
-  __syncthreads();
-  const T* bb = base ? base + b * bhs : nullptr;
-  T* o = out + b * ohs;
-  double dsum = 0.0;
+  const int nb4 = (nb + 3) >> 2;
   const int h0 = blockIdx.x * 32 + w * 4;
+  const int hq = h0 + (lane & 3);  // lanes 0-3: the warp's four outputs
+  const T* bb = base ? base + b * bhs : nullptr;
+  float bval = 0.f;
+  if (bb != nullptr && lane < 4 && hq < nh) bval = float(bb[hq]);
+  // first 64 vectors of the warp's rows, in flight across the staging barrier
+  float4 gv[4][2];
+  const float4* g4 = reinterpret_cast<const float4*>(Gt);
+  auto load = [&](int j0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int j = j0 + lane + 32 * k;
+        gv[q][k] = (h0 + q < nh && j < nb4) ? __ldg(g4 + (int64_t)(h0 + q) * nb4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+  };
+  load(0);
+  float* sgf = reinterpret_cast<float*>(sg);
+  const double* gs = gsum + (int64_t)b * nb;
+  for (int i = threadIdx.x; i < 4 * nb4; i += blockDim.x) sgf[i] = i < nb ? float(gs[i]) : 0.f;
+  __syncthreads();
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int i0 = 0; i0 < nb; i0 += 256) {
+  for (int j0 = 0; j0 < nb4; j0 += 64) {
+    if (j0 > 0) load(j0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = i0 + lane + 32 * k;
-      if (i < nb) {
-        const float a = gA[i];
+    for (int k = 0; k < 2; ++k) {
+      const int j = j0 + lane + 32 * k;
+      if (j < nb4) {
+        const float4 a = sg[j];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (h0 + q < nh) acc[q] += __ldg(&Gt[(int64_t)(h0 + q) * nb + i]) * a;
+        for (int q = 0; q < 4; ++q) acc[q] += dot4(gv[q][k], a);
       }
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float t = warp_sum_f(acc[q]);
-    const int h = h0 + q;
-    if (lane == 0 && h < nh) {
-      const T v = T((bb ? float(bb[h]) : 0.f) + t);
-      o[h] = v;
-      if (bb) dsum += double(bb[h] * v);
-    }
+  for (int q = 0; q < 4; ++q) acc[q] = warp_sum_f(acc[q]);
+  const int ql = lane & 3;
+  const float t = ql == 0 ? acc[0] : ql == 1 ? acc[1] : ql == 2 ? acc[2] : acc[3];
+  float dsum = 0.f;
+  if (lane < 4 && hq < nh) {
+    const T v = T(bval + t);
+    out[b * ohs + hq] = v;
+    dsum = bval * float(v);
   }
   if (dot != nullptr) {
-    const double tot = block_sum(dsum, red);
-    if (threadIdx.x == 0) dot[(int64_t)b * kDotStride + kDotHyper + blockIdx.x] = tot;
+    dsum = warp_sum_f(dsum);
+    if (lane == 0) red[w] = dsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tot = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tot += red[k];
+      dot[(int64_t)b * kDotStride + kDotHyper + blockIdx.x] = double(tot);
+    }
   }
 }
 
@@ -407,12 +443,10 @@ int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double
 }
 
 template <typename T>
-int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int nparts, const T* base_h,
-                int64_t bhs, T* out_h, int64_t ohs, int B, cudaStream_t st, double* dot) {
-  prof_begin("amp_vjp", (double)nb * nh * 4 + (double)B * (8.0 * nparts * nb + (base_h ? 2 : 1) * nh * sizeof(T)),
-             st);
-  k_amp_vjp_lin<T><<<dim3((nh + 31) / 32, B), 256, 0, st>>>(Gt, nb, nh, partials, nparts, base_h, bhs, out_h,
-                                                             ohs, dot);
+int amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum, const T* base_h, int64_t bhs, T* out_h,
+                int64_t ohs, int B, cudaStream_t st, double* dot) {
+  prof_begin("amp_vjp", (double)nb * nh * 4 + (double)B * (8.0 * nb + (base_h ? 2 : 1) * nh * sizeof(T)), st);
+  k_amp_vjp_lin<T><<<dim3((nh + 31) / 32, B), 256, 0, st>>>(Gt, nb, nh, gsum, base_h, bhs, out_h, ohs, dot);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -428,8 +462,8 @@ int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int npa
                                cudaStream_t);                                                          \
   template int amp_jvp_lin<T>(const float*, int, int, const T*, int64_t, double*, int, cudaStream_t,    \
                               double*);                                                               \
-  template int amp_vjp_lin<T>(const float*, int, int, const double*, int, const T*, int64_t, T*,        \
-                              int64_t, int, cudaStream_t, double*);
+  template int amp_vjp_lin<T>(const float*, int, int, const double*, const T*, int64_t, T*, int64_t, int, \
+                              cudaStream_t, double*);
 NRE_INST(float)
 NRE_INST(double)
 #undef NRE_INST

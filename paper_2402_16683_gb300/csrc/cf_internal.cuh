@@ -327,8 +327,9 @@ int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* p
 
 // Linearised amplitude model at an expansion point (FP32 path): the Jacobian
 // from nh JVPs along the unit vectors (eye: [nh][nh] scratch, Jt: [nh][nb] FP64
-// scratch), stored as G [nb][nh] and Gt [nh][nb] floats; then dA = G dh and
-// out_h = base_h + Gt^T-contractions of the per-bin sums (as amp_jvp / amp_vjp).
+// scratch), stored as G [nb][nhp] and Gt [nh][nbp] floats (rows zero-padded to
+// multiples of 4); then dA = G dh and out_h = base_h + Gt-contractions of the
+// complete per-bin sums gsum [B][nb] (as amp_jvp / amp_vjp; nb, nh <= 1024).
 template <typename T>
 int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double* Jt, float* G, float* Gt,
                  cudaStream_t st);
@@ -336,8 +337,8 @@ template <typename T>
 int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st,
                 double* gzero = nullptr);  // gzero: [B][nb] set to 0 (the next sweep's in-place bin sums)
 template <typename T>
-int amp_vjp_lin(const float* Gt, int nb, int nh, const double* partials, int nparts, const T* base_h,
-                int64_t bhs, T* out_h, int64_t ohs, int B, cudaStream_t st, double* dot = nullptr);
+int amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum, const T* base_h, int64_t bhs, T* out_h,
+                int64_t ohs, int B, cudaStream_t st, double* dot = nullptr);
 
 // Sweep chains (sweeps.cu).  Runs one Hartley transform (mid == nullptr) or the
 // metric's transform pair with t = w * y between them (mid != nullptr) over a

@@ -5,9 +5,9 @@
 // per system b: x_0 = 0, r_0 = b, p_0 = r_0; alpha = r.r / p.Mp;
 // x += alpha p; r -= alpha Mp; beta = r'.r' / r.r; p = r' + beta p.  A system
 // stops (x frozen) once ||r|| <= rtol ||b|| on the recursive residual; rtol = 0
-// runs exactly maxiter iterations.  Inner products and alpha / beta are FP64;
-// each thread folds short runs of products in the vector dtype into an FP64
-// accumulator.
+// runs exactly maxiter iterations.  Inner products and alpha / beta are FP64
+// across threads and blocks; within a thread, FP32 products are summed in
+// compensated FP32 (RunSum), FP64 products in FP64.
 #include <cmath>
 
 #include "metric_internal.cuh"
@@ -33,20 +33,19 @@ int cg_blocks(int64_t n, int B) {
 }
 
 // Sum over the block, then one partial per (system, block).
-__device__ void write_partial(double acc, double* part) {
-  __shared__ double red[CG_THREADS / 32];
-  const double t = block_sum(acc, red);
+template <typename T>
+__device__ void write_partial(const RunSum<T>& acc, double* part) {
+  const double t = acc.block_sum();
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // As write_partial; the last block of system blockIdx.y to finish then sums
 // the partials in block order (deterministic) and calls fin(total) from
 // thread 0.  counter[system] must be 0 on entry and is reset.
-template <class F>
-__device__ void finish_partial(double acc, double* part, unsigned* counter, F fin) {
-  __shared__ double red[CG_THREADS / 32];
+template <typename T, class F>
+__device__ void finish_partial(const RunSum<T>& acc, double* part, unsigned* counter, F fin) {
   __shared__ bool last;
-  const double t = block_sum(acc, red);
+  const double t = acc.block_sum();
   const int b = blockIdx.y, nblk = gridDim.x;
   if (threadIdx.x == 0) {
     part[b * nblk + blockIdx.x] = t;
@@ -115,7 +114,7 @@ template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_init(const T* b, T* x, T* r, T* p, int64_t n,
                                                        int64_t S, double* part) {
   const int64_t off = (int64_t)blockIdx.y * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_vec<T>(n, [&](int64_t i, int w) {
     if (w > 1) {
       const V16<T> v = ldv(b + off + i);
@@ -129,13 +128,13 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(const T* b, T* x, T* r, 
       stv(x + off + i, z);
       stv(r + off + i, v);
       stv(p + off + i, v);
-      acc += double(run);
+      acc.add(run);
     } else {
       const T v = b[off + i];
       x[off + i] = T(0);
       r[off + i] = v;
       p[off + i] = v;
-      acc += double(v * v);
+      acc.add(v * v);
     }
   });
   write_partial(acc, part);
@@ -160,7 +159,7 @@ template <typename T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, int64_t n, int64_t S,
                                                       double* part, unsigned* counter, double* sc) {
   const int64_t off = (int64_t)blockIdx.y * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_vec<T>(n, [&](int64_t i, int w) {
     T run = T(0);  // one vector's products in T, folded into FP64
     if (w > 1) {
@@ -170,7 +169,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, i
     } else {
       run = a[off + i] * q[off + i];
     }
-    acc += double(run);
+    acc.add(run);
   });
   double* c = sc + blockIdx.y * SC_N;
   finish_partial(acc, part, counter, [&](double pq) {
@@ -193,13 +192,17 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T
   const bool active = c[SC_ACTIVE] != 0.0;
   T alpha;
   if (pq != nullptr) {
+    // one FP64 division per block, not per thread
+    __shared__ T s_alpha;
     const double s = block_sum_array(pq + (int64_t)b * kDotStride, kDotStride);
-    alpha = T(active && s != 0.0 ? c[SC_RR] / s : 0.0);
+    if (threadIdx.x == 0) s_alpha = T(active && s != 0.0 ? c[SC_RR] / s : 0.0);
+    __syncthreads();
+    alpha = s_alpha;
   } else {
     alpha = T(c[SC_ALPHA]);
   }
   const int64_t off = (int64_t)b * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   constexpr int U = 2;
   for_vec_u<T, U>(
       n,
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T
             T run = T(0);  // one vector
 #pragma unroll
             for (int k = 0; k < V16<T>::W; ++k) run += ri[u].e[k] * ri[u].e[k];
-            acc += double(run);
+            acc.add(run);
           }
       },
       [&](int64_t i) {
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T
           ri -= alpha * q[off + i];
           r[off + i] = ri;
         }
-        acc += double(ri * ri);
+        acc.add(ri * ri);
       });
   finish_partial(acc, rr_part, counter, [&](double rr_new) {
     if (c[SC_ACTIVE] == 0.0) {

@@ -108,6 +108,59 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
 
 // ---------------------------------------------------------------- reductions
+// Sum of two unevaluated pairs hi + lo of floats (double-float numbers,
+// about 48 significant bits) in FP32 arithmetic: Knuth's two-sum of the high
+// parts, the low parts added to its error term, renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bv = s - a.x;
+  const float e = ((a.x - (s - bv)) + (b.x - bv)) + (a.y + b.y);
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+// A thread's running sum of many terms: compensated (Kahan) FP32 for FP32
+// terms, plain FP64 for FP64 terms.  The FP64 units of this part run at a
+// small fraction of the FP32 rate, so per-element FP64 adds and conversions
+// in FP32 loops cost more than the loads they follow; the compensation keeps
+// the FP32 sum's error at a few units in the last place whatever the number
+// of terms.  block_sum() totals the block's sums (all threads must call it;
+// the result is valid in thread 0): in FP64 for FP64, in double-float FP32
+// arithmetic for FP32, converted to a double once.
+template <typename T>
+struct RunSum {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T x) { s += double(x); }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ double block_sum() const;
+};
+template <>
+struct RunSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return double(s) - double(c); }
+  __device__ double block_sum() const {
+    __shared__ float2 red[32];
+    float2 v = make_float2(s, -c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      v = df_add(v, make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o)));
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x != 0) return 0.0;
+    v = red[0];
+    for (int i = 1; i < nw; ++i) v = df_add(v, red[i]);
+    return double(v.x) + double(v.y);
+  }
+};
+
 // Sum over the block of one double per thread; deterministic order.  `red`
 // must hold blockDim.x/32 doubles.  The result is returned to every thread.
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -121,6 +174,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int i = 0; i < nw; ++i) t += red[i];
   __syncthreads();
   return t;
+}
+
+template <typename T>
+__device__ double RunSum<T>::block_sum() const {
+  __shared__ double red[32];
+  return ::nre::block_sum(s, red);
 }
 
 // sum_{c < n} p[c * stride] by one thread, fixed order, eight loads in flight

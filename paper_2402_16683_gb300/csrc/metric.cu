@@ -88,8 +88,9 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
       // FP32 products: the amplitude JVP / VJP become products with the
       // Jacobian at xi_p, formed once here from FP64 JVPs
       const int nh = p->n_hyper;
-      NRE_TRY(ensure(m->amp_G, (size_t)nb * nh * sizeof(float)));
-      NRE_TRY(ensure(m->amp_Gt, (size_t)nb * nh * sizeof(float)));
+      // rows padded to multiples of four floats
+      NRE_TRY(ensure(m->amp_G, (size_t)nb * ((nh + 3) & ~3) * sizeof(float)));
+      NRE_TRY(ensure(m->amp_Gt, (size_t)nh * ((nb + 3) & ~3) * sizeof(float)));
       NRE_TRY(ensure(m->amp_eye, (size_t)nh * nh * sizeof(T)));
       NRE_TRY(ensure(m->amp_Jt, (size_t)nh * nb * sizeof(double)));
       NRE_TRY(ensure(m->gsum, (size_t)m->max_batch * nb * sizeof(double)));
@@ -156,7 +157,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
                          model ? m->part.as<double>() : nullptr, &np, st));
   if (model) {
     if (m->amp_lin)  // the bin sums are complete in gsum (one "partial")
-      NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->gsum.as<double>(), 1, v + N, S, out + N,
+      NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->gsum.as<double>(), v + N, S, out + N,
                              S, B, st, dot));
     else
       NRE_TRY(amp_vjp<T>(pr, m->state.as<double>(), 0, m->part.as<double>(), np, v + N, S, out + N, S,

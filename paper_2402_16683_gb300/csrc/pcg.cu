@@ -58,9 +58,9 @@ struct PCArgs {
   const double* gz;     // [B][nb]
 };
 
-__device__ void partial_out(double acc, double* part) {
-  __shared__ double red[PC_THREADS / 32];
-  const double t = block_sum(acc, red);
+template <typename T>
+__device__ void partial_out(const RunSum<T>& acc, double* part) {
+  const double t = acc.block_sum();
   if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T*
   for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
   const int64_t off = (int64_t)b * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_pv<T>(n, [&](int64_t i, bool full) {
     T v[W];
     T run = T(0);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T*
         }
       }
     }
-    acc += double(run);
+    acc.add(run);
     if (pc.nb > 0) bins_add(pc, i, v, hist);
   });
   partial_out(acc, rr_part);
@@ -169,10 +169,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
   __syncthreads();
   const double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
+  __shared__ T s_alpha;  // one FP64 division per block, not per thread
   const double pq = block_sum_array(pq_part + (int64_t)b * npq, npq);
-  const T alpha = T(active && pq != 0.0 ? c[SC_RZ] / pq : 0.0);
+  if (threadIdx.x == 0) s_alpha = T(active && pq != 0.0 ? c[SC_RZ] / pq : 0.0);
+  __syncthreads();
+  const T alpha = s_alpha;
   const int64_t off = (int64_t)b * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_pv<T>(n, [&](int64_t i, bool full) {
     T v[W];
     T run = T(0);
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
         }
       }
     }
-    acc += double(run);
+    acc.add(run);
     if (pc.nb > 0) bins_add(pc, i, v, hist);
   });
   partial_out(acc, rr_part);
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_z(const T* r, T* z, T* p, in
   for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) sgz[i] = float(cc * pc.gz[(int64_t)b * pc.nb + i]);
   __syncthreads();
   const int64_t off = (int64_t)b * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_pv<T>(n, [&](int64_t i, bool full) {
     T run = T(0);
     if (full && i + W <= pc.N) {
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_z(const T* r, T* z, T* p, in
         run += ri * zi;
       }
     }
-    acc += double(run);
+    acc.add(run);
   });
   partial_out(acc, rz_part);
 }
@@ -355,8 +358,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_pupdate(T* p, const T* z, in
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
   if (c[SC_ACTIVE] == 0.0) return;
+  __shared__ T s_beta;  // one FP64 division per block, not per thread
   const double rz = block_sum_array(rz_part + (int64_t)b * nblk, nblk);
-  const T beta = T(rz / c[SC_RZ]);
+  if (threadIdx.x == 0) s_beta = T(rz / c[SC_RZ]);
+  __syncthreads();
+  const T beta = s_beta;
   const int64_t off = (int64_t)b * S;
   for_pv<T>(n, [&](int64_t i, bool full) {
     if (full) {
@@ -394,7 +400,7 @@ template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) k_dot_p(const T* a, const T* q, int64_t n, int64_t S, double* part) {
   constexpr int W = PV<T>::W;
   const int64_t off = (int64_t)blockIdx.y * S;
-  double acc = 0.0;
+  RunSum<T> acc;
   for_pv<T>(n, [&](int64_t i, bool full) {
     T run = T(0);
     if (full) {
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_dot_p(const T* a, const T* q, in
       for (int k = 0; k < W; ++k)
         if (i + k < n) run += a[off + i + k] * q[off + i + k];
     }
-    acc += double(run);
+    acc.add(run);
   });
   partial_out(acc, part);
 }

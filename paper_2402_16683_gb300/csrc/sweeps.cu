@@ -317,11 +317,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_dot_fallback(const T* base, int64_t bs, const T* y, int64_t ys,
                                                      int64_t N, double* dot) {
   const int b = blockIdx.y;
-  double acc = 0.0;
+  RunSum<T> acc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    acc += double(base[b * bs + i] * y[b * ys + i]);
-  __shared__ double red[8];
-  const double t = block_sum(acc, red);
+    acc.add(base[b * bs + i] * y[b * ys + i]);
+  const double t = acc.block_sum();
   double* dp = dot + (int64_t)b * kDotStride;
   if (threadIdx.x == 0) dp[blockIdx.x] = t;
   if (blockIdx.x == 0)

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
 
   // fused inner product sum(base * y) of a metric product (see Epi::dot)
   const bool dot = PM >= 2 && epi.dot != nullptr;
-  double dacc = 0.0;
+  RunSum<T> dacc;
   const int ustride = gridDim.x * NU;
   int u0 = blockIdx.x * NU;
   if (u0 < a.n_units) issue(u0, 0, false);
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
           add_slots<SLOTS, T>(kb, c, hist);  // the TAB epilogue always sums the bins
         }
       }
-      if (dot) dacc += double(dsum);
+      if (dot) dacc.add(dsum);
     } else {
     T dsum = T(0);
     // output of slot value `val` at row `rw`, column x of sample `sp`
@@ -432,14 +432,13 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
         if (bins) add_slots<4, T>(bn, c, hist);
       }
     }
-    if (dot) dacc += double(dsum);
+    if (dot) dacc.add(dsum);
     }  // generic epilogue
     __syncthreads();  // this half is refilled two iterations later
   }
   cp_wait<0>();
   if (dot) {
-    __shared__ double dred[32];
-    const double tot = block_sum(dacc, dred);
+    const double tot = dacc.block_sum();
     double* dp = epi.dot + (int64_t)blockIdx.y * kDotStride;
     if (threadIdx.x == 0) dp[blockIdx.x] = tot;
     if (blockIdx.x == 0)
