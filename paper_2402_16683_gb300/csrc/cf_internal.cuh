@@ -230,12 +230,12 @@ struct Mid {
 // Arguments of one row sweep (last axis, length L).
 // A CTA's per-bin sums: into epi.gsum (atomically) or as partial `part` of
 // nparts for sample b.  Called by all threads after the sums are complete.
-template <typename T>
+template <typename T, typename H>
 __device__ __forceinline__ void store_bins(const Epi<T>& e, double* partials, int b, int nparts, int part,
-                                           const double* hist, int nb) {
+                                           const H* hist, int nb) {
   if (e.gsum != nullptr) {
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
-      if (hist[i] != 0.0) atomicAdd(&e.gsum[(int64_t)b * nb + i], hist[i]);
+      if (hist[i] != H(0)) atomicAdd(&e.gsum[(int64_t)b * nb + i], double(hist[i]));
   } else {
     double* dst = partials + ((int64_t)b * nparts + part) * nb;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = hist[i];

@@ -193,9 +193,13 @@ __device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8]
 // maximal ranges of consecutive lanes with the same key) and add each run's
 // total to hist[key] from its last lane.  key < 0: no contribution.
 // The run sums are formed in V (the plan's value type: FP32 products of FP32
-// data are summed over at most 32 lanes) and accumulated in FP64.
-template <typename V>
-__device__ __forceinline__ void warp_run_add(int key, V val, double* hist) {
+// data are summed over at most 32 lanes) and added to hist in H: the register
+// sweeps keep a CTA's sums in V (shared-memory FP32 atomics for FP32 plans:
+// FP64 adds and conversions per run cost more than the rest of the epilogue
+// on this part, whose FP64 rate is a small fraction of its FP32 rate) and
+// fold them into FP64 once per CTA; the other callers pass FP64 sums.
+template <typename V, typename H>
+__device__ __forceinline__ void warp_run_add(int key, V val, H* hist) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int prev = __shfl_up_sync(full, key, 1);
@@ -210,14 +214,14 @@ __device__ __forceinline__ void warp_run_add(int key, V val, double* hist) {
     if (lane - o >= seg) val += ov;
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (tail && key >= 0) atomicAdd(&hist[key], double(val));
+  if (tail && key >= 0) atomicAdd(&hist[key], H(val));
 }
 
 // Adds the contributions c[s] of slots with bins bn[s] (all into the same
 // histogram): slots sharing a bin are summed first, then each distinct bin is
 // reduced over the warp.  Must be called by all lanes of the warp.
-template <int S, typename V>
-__device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], double* hist) {
+template <int S, typename V, typename H>
+__device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], H* hist) {
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     int key = bn[s];

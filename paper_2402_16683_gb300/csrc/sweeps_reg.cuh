@@ -120,7 +120,7 @@ struct RowSmem {
   static constexpr int STGA = (STG + 3) / 4 * 4;          // 16-byte multiple
   static size_t bytes(bool base, int nb, int nhist_bins) {
     return (size_t)2 * L * sizeof(T) + (size_t)2 * STGA * sizeof(T) + (base ? (size_t)XSZ * sizeof(T) : 0) +
-           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
+           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(T);
   }
 };
 
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   const int nbp = (a.nb + 3) / 4 * 4;
   T* sA = bstage + (sbase ? SM::XSZ : 0);
   T* sdA = sA + nbp;
-  double* hist = reinterpret_cast<double*>(sdA + nbp);
+  T* hist = sdA + nbp;  // per-bin sums of the CTA in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
   const int nhist = (PM == 1) ? 2 * NU : 1;
   const int bsample = (PM == 1) ? 0 : blockIdx.y;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   const T* stab = use_tab ? sA : nullptr;
   const T* stdA = use_dA ? sdA : nullptr;
   if (bins)
-    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = 0.0;
+    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = T(0);
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
 
@@ -469,7 +469,7 @@ struct ColSmem {
   static constexpr bool ALIAS = LNSZ <= XS;
   static size_t bytes(int nb, int nhist_bins) {
     return (size_t)2 * L * sizeof(T) + (size_t)2 * XS * sizeof(T) + (ALIAS ? 0 : (size_t)LNSZ * sizeof(T)) +
-           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(double);
+           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(T);
   }
 };
 
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
   C* lines_own = reinterpret_cast<C*>(xin + 2 * SM::XS);  // used when !SM::ALIAS
   T* sA = xin + 2 * SM::XS + (SM::ALIAS ? 0 : SM::LNSZ);
   T* sdA = sA + nbp;
-  double* hist = reinterpret_cast<double*>(sdA + nbp);
+  T* hist = sdA + nbp;  // per-bin sums of the CTA in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
   const int b = blockIdx.y;
   const Pro<T>& pro = a.pro;
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeo
   const T* stab = use_tab ? sA : nullptr;
   const T* stdA = use_dA ? sdA : nullptr;
   if (bins)
-    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = 0.0;
+    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = T(0);
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
   // W, the chunks per tile row and the tiles per outer index are powers of two:

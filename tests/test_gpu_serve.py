@@ -3,13 +3,18 @@ direct Metric.cg path, admission respects the HBM budget, and the footprint
 charged is an upper bound of what a request actually allocates.
 
 FP32 tolerances: the server and Metric.cg run the same kernels on the same
-inputs, so they agree to the FP32 metric-product tolerance (1e-5 relative);
-the only run-to-run difference is the order of FP64 atomic bin sums.
+inputs; the run-to-run difference is the order in which the register sweeps'
+FP32 shared-memory atomics add a CTA's log-|k| bin contributions (about 1e-7
+of a bin sum), which the FP32 solves amplify by the metric's conditioning
+(up to ~1e-5 measured after hundreds of iterations).  Two FP32 solves are
+compared at SOLVE_TOL, a tenfold margin on that.
 """
 import numpy as np
 import pytest
 
 import synth
+
+SOLVE_TOL = 1e-4
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,10 +85,10 @@ def _requests(n_samples=4, mgvi=False):
 def test_serve_matches_direct_path_and_alone_vs_mix(response):
     """Gaussian requests with the identity response (the serving stream's) and
     with the exponential one (a harder metric: hundreds of FP32 iterations,
-    where the run-dependent order of the FP64 atomic bin sums shows as
-    ~1e-5 differences)."""
+    where the run-dependent order of the bin sums shows as ~1e-5
+    differences)."""
     nre = _nre()
-    tol = 1e-5 if response == "identity" else 3e-5
+    tol = SOLVE_TOL
     reqs_alone = _requests()
     reqs_mix = [(s, l, xp, b, e, np.zeros_like(x)) for (s, l, xp, b, e, x) in reqs_alone]
     alone = nre.Server(max_slots=1, use_graphs=True)
@@ -108,7 +113,7 @@ def test_serve_matches_direct_path_and_alone_vs_mix(response):
         xd, its, rel, *_ = _direct(shape, lik, xi_p, b, response=response if lik == "gauss" else "exp")
         assert _rel(xa, xd) <= tol, (shape, lik, _rel(xa, xd))
         # iteration counts agree up to the rounding chaos of long FP32 CG runs
-        # (FP64 atomic bin sums are summed in a run-dependent order)
+        # (the bin sums are added in a run-dependent order)
         print(shape, lik, "iterations", ra["iters"][:n], list(its))
         assert all(abs(a - c) <= max(3, 0.1 * c) for a, c in zip(ra["iters"][:n], its))
 
@@ -132,7 +137,7 @@ def test_serve_reused_slot_follows_new_expansion_point():
     for (shape, lik, xi_p, b, _, x), r in zip(reqs, res):
         assert r["status"] == 0, r["error"]
         xd, *_ = _direct(shape, lik, xi_p, b)
-        assert _rel(x, xd) <= 1e-5, _rel(x, xd)
+        assert _rel(x, xd) <= SOLVE_TOL, _rel(x, xd)
 
 
 def test_serve_true_residual_fp64_metric():
@@ -177,7 +182,7 @@ def test_serve_mgvi_rhs_on_device():
     srv.close()
     assert r["status"] == 0
     xd, *_ = _direct(shape, lik, xi_p, b, eta=eta)
-    assert _rel(x, xd) <= 1e-5
+    assert _rel(x, xd) <= SOLVE_TOL
 
 
 def test_serve_fp64_matches_cg_solve():
