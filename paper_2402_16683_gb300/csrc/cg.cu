@@ -87,12 +87,13 @@ __device__ __forceinline__ void for_vec(int64_t n, F f) {
 // indices of U vectors (ok: in range) so that it can issue all their loads
 // before using any; fs(i) handles one tail entry.  The vectors a thread visits
 // come in the same order as in for_vec.
+// The loop runs over the CTAs cta = 0 .. ncta-1 of the system.
 template <typename T, int U, class FV, class FS>
-__device__ __forceinline__ void for_vec_u(int64_t n, FV fv, FS fs) {
+__device__ __forceinline__ void for_vec_u(int64_t n, int cta, int ncta, FV fv, FS fs) {
   constexpr int W = V16<T>::W;
   const int64_t nv = n / W;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += U * stride) {
+  const int64_t stride = (int64_t)ncta * blockDim.x;
+  for (int64_t v = cta * (int64_t)blockDim.x + threadIdx.x; v < nv; v += U * stride) {
     int64_t idx[U];
     bool ok[U];
 #pragma unroll
@@ -102,8 +103,35 @@ __device__ __forceinline__ void for_vec_u(int64_t n, FV fv, FS fs) {
     }
     fv(idx, ok);
   }
-  for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) fs(i);
+  for (int64_t i = nv * W + cta * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) fs(i);
 }
+
+// The FP32 power-spectrum model's hyper-parameter block, handled inside the
+// CG vector kernels (G == nullptr: not fused; the metric product then forms
+// dA and the hyper part of q itself).  Latent layout: field entries [0, N),
+// hyper-parameters [N, N + nh).  With the Jacobian G of the amplitude model
+// at the expansion point (G [nb][nhp], Gt [nh][nbp], rows zero-padded to
+// multiples of 4 floats), the metric product's hyper part is
+// q_h = p_h + G^T g with g = gsum, the log-|k| bin sums of its last sweep,
+// and the product's tangent amplitude is dA = G p_h; so
+// p_h . q_h = p_h . p_h + dA . g needs no G^T product.  The update kernel
+// forms q_h row by row (each block a share of the rows), the p-update kernel's
+// last block forms the next p_h, its dA and zeroes gsum for the next product.
+struct CGHyper {
+  const float* G;
+  const float* Gt;
+  double* dA;    // [B][nb]: G p_h of the current p
+  double* gsum;  // [B][nb]
+  int nb, nh;
+  int64_t N;
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
 
 template <typename T>
 __device__ __forceinline__ V16<T> ldv(const T* p) { return *reinterpret_cast<const V16<T>*>(p); }
@@ -183,29 +211,53 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, i
 // With pq (the fused p.q partials of the metric product, kDotStride per
 // system) every block forms alpha = r.r / p.q itself; the last block of the
 // system, which alone rewrites r.r, starts only after every block has read it.
+// With hy.G (CGHyper): the vector loop covers the field entries; p.q gains the
+// hyper part p_h . p_h + dA . g (one warp per block, read from pn = the
+// current p_h), and each block takes a share of the hyper rows: q_h = p_h +
+// Gt[h] . g, x_h += alpha p_h, r_h -= alpha q_h, p_h copied from pn into p.
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T* p, const T* q, int64_t n,
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, const T* q, int64_t n,
                                                          int64_t S, double* sc, double* rr_part,
-                                                         unsigned* counter, double rtol, const double* pq) {
+                                                         unsigned* counter, double rtol, const double* pq,
+                                                         CGHyper hy, const T* pn) {
   const int b = blockIdx.y;
   double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
+  const bool fused = hy.G != nullptr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t off = (int64_t)b * S;
   T alpha;
   if (pq != nullptr) {
     // one FP64 division per block, not per thread
     __shared__ T s_alpha;
-    const double s = block_sum_array(pq + (int64_t)b * kDotStride, kDotStride);
-    if (threadIdx.x == 0) s_alpha = T(active && s != 0.0 ? c[SC_RR] / s : 0.0);
+    __shared__ double s_hd;
+    if (fused && wid == 1) {
+      float pp = 0.f;
+      for (int h = lane; h < hy.nh; h += 32) {
+        const float v = float(pn[(int64_t)b * hy.nh + h]);
+        pp += v * v;
+      }
+      double dg = 0.0;
+      for (int i = lane; i < hy.nb; i += 32) dg += hy.dA[(int64_t)b * hy.nb + i] * hy.gsum[(int64_t)b * hy.nb + i];
+      pp = warp_sum_f(pp);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, o);
+      if (lane == 0) s_hd = dg + double(pp);
+    }
+    const double s0 = block_sum_array(pq + (int64_t)b * kDotStride, kDotStride);
+    if (threadIdx.x == 0) {
+      const double s = s0 + (fused ? s_hd : 0.0);
+      s_alpha = T(active && s != 0.0 ? c[SC_RR] / s : 0.0);
+    }
     __syncthreads();
     alpha = s_alpha;
   } else {
     alpha = T(c[SC_ALPHA]);
   }
-  const int64_t off = (int64_t)b * S;
   RunSum<T> acc;
   constexpr int U = 2;
   for_vec_u<T, U>(
-      n,
+      fused ? hy.N : n, blockIdx.x, gridDim.x,
       [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
         V16<T> ri[U], xi[U], pi[U], qi[U];
 #pragma unroll
@@ -245,6 +297,58 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T
         }
         acc.add(ri * ri);
       });
+  if (fused) {
+    // g = gsum[b] in FP32 (zero-padded), then four rows of Gt per warp and
+    // round, all their 16-byte loads in flight
+    __shared__ float4 sg4[256];
+    float* sg = reinterpret_cast<float*>(sg4);
+    const int nb4 = (hy.nb + 3) >> 2;
+    for (int i = threadIdx.x; i < 4 * nb4; i += blockDim.x)
+      sg[i] = i < hy.nb ? float(hy.gsum[(int64_t)b * hy.nb + i]) : 0.f;
+    __syncthreads();
+    const int rows = (hy.nh + gridDim.x - 1) / gridDim.x;
+    const int h0 = blockIdx.x * rows, h1 = min(hy.nh, h0 + rows);
+    const float4* G4 = reinterpret_cast<const float4*>(hy.Gt);
+    for (int hb = h0 + 4 * wid; hb < h1; hb += 32) {
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j0 = 0; j0 < nb4; j0 += 64) {
+        float4 gv[4][2];
+#pragma unroll
+        for (int qr = 0; qr < 4; ++qr)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int j = j0 + lane + 32 * k;
+            gv[qr][k] = (hb + qr < h1 && j < nb4) ? __ldg(G4 + (int64_t)(hb + qr) * nb4 + j)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int j = j0 + lane + 32 * k;
+          if (j < nb4) {
+            const float4 a4 = sg4[j];
+#pragma unroll
+            for (int qr = 0; qr < 4; ++qr) t[qr] += dot4(gv[qr][k], a4);
+          }
+        }
+      }
+#pragma unroll
+      for (int qr = 0; qr < 4; ++qr) t[qr] = warp_sum_f(t[qr]);
+      const int ql = lane & 3, h = hb + ql;
+      if (lane < 4 && h < h1) {
+        const int64_t e = off + hy.N + h;
+        const T ph = pn[(int64_t)b * hy.nh + h];
+        const T tq = T(ql == 0 ? t[0] : ql == 1 ? t[1] : ql == 2 ? t[2] : t[3]);
+        T rh = r[e];
+        p[e] = ph;
+        if (active) {
+          x[e] += alpha * ph;
+          rh -= alpha * (ph + tq);
+          r[e] = rh;
+        }
+        acc.add(rh * rh);
+      }
+    }
+  }
   finish_partial(acc, rr_part, counter, [&](double rr_new) {
     if (c[SC_ACTIVE] == 0.0) {
       c[SC_BETA] = 0.0;
@@ -261,17 +365,25 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, const T
 }
 
 // p = r + beta p with beta from the update kernel (0 for a frozen system).
+// With hy.G: the vector loop covers the field entries; every block forms the
+// next p_h = r_h + beta p_h in shared memory (p_h itself is not written here:
+// every block reads it), block 0 stores it to pn, and each block takes a
+// share of the bins: dA = G p_h, gsum = 0 (the next product's bin sums).
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* p, const T* r, int64_t n, int64_t S,
-                                                          const double* sc) {
+                                                          const double* sc, CGHyper hy, T* pn) {
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
+  const bool fused = hy.G != nullptr;
+  const int rows = fused ? (hy.nb + gridDim.x - 1) / gridDim.x : 0;
+  const int i0 = blockIdx.x * rows, i1 = fused ? min(hy.nb, i0 + rows) : 0;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) hy.gsum[(int64_t)b * hy.nb + i] = 0.0;
   if (c[SC_ACTIVE] == 0.0) return;
   const T beta = T(c[SC_BETA]);
   const int64_t off = (int64_t)b * S;
   constexpr int U = 4;
   for_vec_u<T, U>(
-      n,
+      fused ? hy.N : n, blockIdx.x, gridDim.x,
       [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
         V16<T> ri[U], pi[U];
 #pragma unroll
@@ -289,6 +401,51 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* p, const T* r, 
           }
       },
       [&](int64_t i) { p[off + i] = r[off + i] + beta * p[off + i]; });
+  if (!fused || i0 >= i1) return;
+  __shared__ float4 sp4[256];
+  float* sp = reinterpret_cast<float*>(sp4);
+  const int nh4 = (hy.nh + 3) >> 2;
+  for (int h = threadIdx.x; h < 4 * nh4; h += blockDim.x) {
+    float v = 0.f;
+    if (h < hy.nh) {
+      const int64_t e = off + hy.N + h;
+      const T ph = r[e] + beta * p[e];
+      if (blockIdx.x == 0) pn[(int64_t)b * hy.nh + h] = ph;
+      v = float(ph);
+    }
+    sp[h] = v;
+  }
+  __syncthreads();
+  // two rows of G per warp and round (a row: nh4 16-byte vectors)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float4* G4 = reinterpret_cast<const float4*>(hy.G);
+  for (int ib = i0 + 2 * wid; ib < i1; ib += 16) {
+    float t[2] = {0.f, 0.f};
+    for (int j0 = 0; j0 < nh4; j0 += 160) {
+      float4 gv[2][5];
+#pragma unroll
+      for (int qr = 0; qr < 2; ++qr)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const int j = j0 + lane + 32 * k;
+          gv[qr][k] = (ib + qr < i1 && j < nh4) ? __ldg(G4 + (int64_t)(ib + qr) * nh4 + j)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const int j = j0 + lane + 32 * k;
+        if (j < nh4) {
+          const float4 a4 = sp4[j];
+#pragma unroll
+          for (int qr = 0; qr < 2; ++qr) t[qr] += dot4(gv[qr][k], a4);
+        }
+      }
+    }
+    t[0] = warp_sum_f(t[0]);
+    t[1] = warp_sum_f(t[1]);
+    const int i = ib + (lane & 1);
+    if (lane < 2 && i < i1) hy.dA[(int64_t)b * hy.nb + i] = double(lane == 0 ? t[0] : t[1]);
+  }
 }
 
 template <typename T>
@@ -297,7 +454,29 @@ struct CGWork {
   double *sc, *part_a, *part_b;
   unsigned* counter;
   int nblk;
+  CGHyper hy;  // hy.G == nullptr: the metric product handles the hyper block
+  T* pn;
 };
+
+// The CG kernels take over the hyper block of FP32 power-model products
+// (CGHyper) when the metric has the linearised amplitude model and the latent
+// vector is exactly [field, hyper-parameters].
+template <typename T>
+CGHyper cg_hyper(nre_metric* m) {
+  CGHyper h{};
+  const nre_cf_plan* p = m->cf;
+  if (sizeof(T) != 4 || m->model_kind != NRE_MODEL_CF || !m->amp_lin || m->precond != NRE_PRECOND_NONE ||
+      p == nullptr || p->n_hyper <= 0 || m->latent != p->N + p->n_hyper)
+    return h;
+  h.G = m->amp_G.as<float>();
+  h.Gt = m->amp_Gt.as<float>();
+  h.dA = m->dA.as<double>();
+  h.gsum = m->gsum.as<double>();
+  h.nb = p->n_bins;
+  h.nh = p->n_hyper;
+  h.N = p->N;
+  return h;
+}
 
 template <typename T>
 CGWork<T> cg_work(nre_metric* m, int B) {
@@ -310,6 +489,8 @@ CGWork<T> cg_work(nre_metric* m, int B) {
   w.part_a = m->cg_part.as<double>();
   w.part_b = w.part_a + (size_t)B * w.nblk;
   w.counter = reinterpret_cast<unsigned*>(w.part_b + (size_t)B * w.nblk);
+  w.hy = cg_hyper<T>(m);
+  w.pn = m->cg_pn.as<T>();
   return w;
 }
 
@@ -324,6 +505,7 @@ int cg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_t
   const int nblk = cg_blocks(n, B);
   NRE_TRY(ensure(m->cg_part, (size_t)2 * B * nblk * sizeof(double) + (size_t)B * sizeof(unsigned)));
   if (m->model_kind == NRE_MODEL_CF) NRE_TRY(ensure(m->cg_dot, (size_t)B * kDotStride * sizeof(double)));
+  if (cg_hyper<T>(m).G != nullptr) NRE_TRY(ensure(m->cg_pn, (size_t)B * m->cf->n_hyper * sizeof(T)));
   const CGWork<T> w = cg_work<T>(m, B);
   NRE_TRY_CUDA(cudaMemsetAsync(w.counter, 0, (size_t)B * sizeof(unsigned), st));
   const dim3 grid(nblk, B);
@@ -335,6 +517,13 @@ int cg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_t
   k_cg_start<<<B, 32, 0, st>>>(w.sc, w.part_a, nblk, rtol);
   prof_end(st);
   NRE_CHECK_LAUNCH();
+  if (w.hy.G != nullptr) {
+    // p_0 = b: its hyper block into pn, its dA, zero bin sums
+    const int64_t N = w.hy.N;
+    NRE_TRY_CUDA(cudaMemcpy2DAsync(w.pn, (size_t)w.hy.nh * sizeof(T), w.p + N, (size_t)S * sizeof(T),
+                                   (size_t)w.hy.nh * sizeof(T), B, cudaMemcpyDeviceToDevice, st));
+    NRE_TRY(amp_jvp_lin<T>(w.hy.G, w.hy.nb, w.hy.nh, w.p + N, S, w.hy.dA, B, st, w.hy.gsum));
+  }
   return NRE_OK;
 }
 
@@ -348,17 +537,18 @@ int cg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t s
   // correlated field: p.q comes fused with the metric product
   double* pq = m->model_kind == NRE_MODEL_CF ? m->cg_dot.as<double>() : nullptr;
   for (int it = 0; it < iters; ++it) {
-    NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, pq));
+    NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, pq, w.hy.G != nullptr && pq != nullptr));
     if (!pq) {
       prof_begin("cg_dot", 2 * vb, st);
       k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.q, n, S, w.part_a, w.counter, w.sc);
       prof_end(st);
     }
     prof_begin("cg_update", 6 * vb, st);
-    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, w.r, w.p, w.q, n, S, w.sc, w.part_b, w.counter, rtol, pq);
+    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, w.r, w.p, w.q, n, S, w.sc, w.part_b, w.counter, rtol, pq,
+                                                 pq ? w.hy : CGHyper{}, w.pn);
     prof_end(st);
     prof_begin("cg_pupdate", 3 * vb, st);
-    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.r, n, S, w.sc);
+    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.r, n, S, w.sc, pq ? w.hy : CGHyper{}, w.pn);
     prof_end(st);
     NRE_CHECK_LAUNCH();
   }

@@ -113,7 +113,8 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
 }
 
 template <typename T>
-int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, double* dot) {
+int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, double* dot,
+                    bool hyper_in_cg) {
   nre_cf_plan* p = m->cf;
   const int64_t N = p->N, S = p->stride;
   const T* xp = m->xi_p.as<T>();
@@ -132,8 +133,11 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
   const int nb = p->n_bins;
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
+  hyper_in_cg = hyper_in_cg && model && m->amp_lin;
   if (model) {
-    if (m->amp_lin)  // also zeroes the in-place bin sums of the last sweep
+    if (hyper_in_cg)
+      ;  // dA of v formed and gsum zeroed by the CG kernels
+    else if (m->amp_lin)  // also zeroes the in-place bin sums of the last sweep
       NRE_TRY(amp_jvp_lin<T>(m->amp_G.as<float>(), nb, p->n_hyper, v + N, S, m->dA.as<double>(), B, st,
                              m->gsum.as<double>()));
     else
@@ -155,7 +159,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   int np = 0;
   NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
                          model ? m->part.as<double>() : nullptr, &np, st));
-  if (model) {
+  if (model && !hyper_in_cg) {
     if (m->amp_lin)  // the bin sums are complete in gsum (one "partial")
       NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->gsum.as<double>(), v + N, S, out + N,
                              S, B, st, dot));
@@ -209,10 +213,12 @@ int metric_relinearize(nre_metric* m, const void* xi_p, cudaStream_t st) {
   return m->dtype == NRE_F64 ? cf_metric_setup<double>(m, xi_p, st) : cf_metric_setup<float>(m, xi_p, st);
 }
 
-int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st, double* dot) {
+int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st, double* dot,
+                      bool hyper_in_cg) {
   if (m->model_kind == NRE_MODEL_ICR) return icr_metric_apply(m, v, out, batch, st);
-  if (m->dtype == NRE_F64) return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st, dot);
-  return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st, dot);
+  if (m->dtype == NRE_F64)
+    return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st, dot, hyper_in_cg);
+  return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st, dot, hyper_in_cg);
 }
 }  // namespace nre
 

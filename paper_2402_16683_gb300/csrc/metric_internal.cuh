@@ -37,6 +37,7 @@ struct nre_metric {
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;
   nre::DevBuf cg_dot;  // [max batch][kDotStride] fused p.q partials
+  nre::DevBuf cg_pn;   // [batch][n_hyper] the current p_h when CG handles the hyper block (cg.cu)
   std::vector<double> cg_host;
   // preconditioner (metric_set_precond)
   int precond = 0;
@@ -59,8 +60,12 @@ AmpView<T> metric_view(const nre_metric* m);
 // out = v + J^T (w * J v) for a batch (dtype-dispatched inside).  With `dot`
 // (correlated field only) also the inner products v . out as partials
 // dot[b * kDotStride + i], whose sum over i is the product of system b.
+// hyper_in_cg (FP32 power model with the linearised amplitude, CG only): the
+// caller has formed dA for v and zeroed gsum, and forms the hyper part of out
+// and of the inner product itself from gsum (see CGHyper in cg.cu); the
+// product then covers the field part only.
 int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st,
-                      double* dot = nullptr);
+                      double* dot = nullptr, bool hyper_in_cg = false);
 // ICR model hooks (icr.cu).
 int icr_metric_setup(nre_metric* m, cudaStream_t st);
 int icr_metric_apply(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st);

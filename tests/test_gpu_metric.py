@@ -226,6 +226,41 @@ def test_pcg_fp64_matches_plain_solution(shape, kind, lik):
         assert rel_l2(xs[i], xr) <= 1e-8
 
 
+def test_cg_fp32_power_model_iterates():
+    """FP32 plain CG on the 2-D power-model Poisson metric, where the CG
+    kernels take over the metric product's hyper-parameter block (q_h from the
+    bin sums, p.q's hyper part as p_h.p_h + dA.g, the next dA in the p-update):
+    the iterates match the oracle's FP64 CG iterates, field and hyper blocks
+    separately.  This metric is so ill-conditioned (relres 30-60 after one
+    iteration) that CG amplifies rounding fast: iterates 1 and 2 must match to
+    the FP32 product tolerance 1e-5 (measured <= 5e-7); iterate 4 must lie
+    within ten times the spread of oracle runs whose products carry a seeded
+    relative error of 1e-6 (the FP32 product's size), as CG's chaos allows no
+    fixed bound (measured: GPU 2e-6 / 8e-5, spread 1e-4 / 2e-4)."""
+    plan, om, M, xi_p, w = _setup((64, 64), "power", "f32", "poisson", max_batch=2)
+    b = rounded(np.random.default_rng(14).standard_normal((2, om.latent_size)), "f32")
+    mv = lambda p: ometric(om, xi_p, w, p)
+    for k in (1, 2, 4):
+        x, its, rel, st = M.cg(to_dev(plan, b), rtol=0.0, maxiter=k)
+        assert its == [k, k] and st == 0
+        xs = host(x, om.latent_size)
+        for i in range(2):
+            xr, _, rr = ocg(mv, b[i], rtol=0.0, maxiter=k)
+            e = blocks_rel(xs[i], xr, om.n_field)
+            if k <= 2:
+                assert e <= 1e-5, (k, i, e)
+                assert abs(rel[i] - rr) <= 1e-5 * rr, (k, i, rel[i], rr)
+                continue
+            g = np.random.default_rng(100 + i)
+
+            def noisy(p):
+                y = mv(p)
+                return y + 1e-6 * np.linalg.norm(y) / np.sqrt(y.size) * g.standard_normal(y.shape)
+
+            spread = max(blocks_rel(ocg(noisy, b[i], rtol=0.0, maxiter=k)[0], xr, om.n_field) for _ in range(3))
+            assert e <= 10 * spread, (k, i, e, spread)
+
+
 def test_cg_fixed_iterations_and_notconv():
     plan, om, M, xi_p, w = _setup((64, 64), "power", "f32", "poisson", max_batch=2)
     b = rounded(np.random.default_rng(11).standard_normal((2, om.latent_size)), "f32")
