@@ -66,6 +66,15 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
+# one capture, caches flushed before each launch) of the kernels that can be
+# the dominant one, keyed by (kernel tag, batch), averaged over the launch
+# variants the tag covers; None where no capture of the current kernels exists.
+DRAM_TRAFFIC = {
+    ("row_sweep_f32_2d", 32): (52.58e6, "profiles/traffic_f32_2d_512x512_b32.md"),
+}
+
+
 def config(batch):
     return {"workload": WORKLOAD, "grid": list(GRID), "batch": batch, "cg_iters": CG_ITERS,
             "amplitude": "power-spectrum model, 256 log-|k| bins", "likelihood": "poisson, rate 10 exp(cf)",
@@ -298,8 +307,11 @@ def run_ours(args, rank, world):
     name, (cnt, kms, kbytes) = max(kern.items(), key=lambda kv: kv[1][1])
     peak, peak_kind = peaks()
     achieved = kbytes / (kms / 1e3) / 1e9
+    traffic = DRAM_TRAFFIC.get((name, B))
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic[0] if traffic else None,
+                "traffic_source": traffic[1] if traffic else None,
                 "launches": int(cnt), "avg_launch_us": 1e3 * kms / cnt,
                 "algorithmic_bytes_per_launch": kbytes / cnt}
     kernels = {k: {"launches": int(v[0]), "ms": v[1], "share": v[1] / sum(u[1] for u in kern.values()),
