@@ -63,10 +63,10 @@ int row_reg_L(RowArgs<T> a, bool mid, dim3 grid, size_t smem, cudaStream_t st, i
   return NRE_OK;
 }
 
-// CTAs per sample of a persistent sweep: about kResidentCTAs in total, at least
+// CTAs per sample of a persistent sweep: about `resident` in total, at least
 // one, at most one per unit group and at most kMaxGridX.
-inline int persistent_gx(int64_t groups, int B) {
-  int64_t gx = (kResidentCTAs + B - 1) / B;
+inline int persistent_gx(int64_t groups, int B, int resident) {
+  int64_t gx = (resident + B - 1) / B;
   if (gx > groups) gx = groups;
   if (gx > kMaxGridX) gx = kMaxGridX;
   return gx < 1 ? 1 : (int)gx;
@@ -83,25 +83,30 @@ int row_reg_plan(RowArgs<T>& a, int B, bool bins, dim3* grid, size_t* smem, int*
     nhist = 2 * NU;
     *nparts = 1;
   } else {
-    const int gx = persistent_gx((a.n_units + NU - 1) / NU, B);
-    *grid = dim3(gx, B);
     nhist = 1;
-    *nparts = gx;
   }
   a.nU = NU;
   const int pm = a.pm;
-  *smem = pm == 1   ? RowSmem<T, L, 1>::bytes(sbase, a.nb, bins ? nhist * a.nb : 0)
-          : pm == 2 ? RowSmem<T, L, 2>::bytes(sbase, a.nb, bins ? a.nb : 0)
-                    : RowSmem<T, L, 3>::bytes(sbase, a.nb, bins ? a.nb : 0);
+  const int ek = pm == 1 ? SK_GEN : epi_kind(a.epi);
+  const bool bstaged = sbase && !row_direct_base(RowShape<L>::NT, pm, ek, sizeof(T), L);
+  *smem = pm == 1   ? RowSmem<T, L, 1>::bytes(bstaged, a.nb, bins ? nhist * a.nb : 0)
+          : pm == 2 ? RowSmem<T, L, 2>::bytes(bstaged, a.nb, bins ? a.nb : 0)
+                    : RowSmem<T, L, 3>::bytes(bstaged, a.nb, bins ? a.nb : 0);
+  if (pm != 1) {
+    const int gx = persistent_gx((a.n_units + NU - 1) / NU, B,
+                                 resident_ctas(row_min_ctas(RowShape<L>::NT, pm, ek, sizeof(T), L), *smem));
+    *grid = dim3(gx, B);
+    *nparts = gx;
+  }
   return *smem <= 200 * 1024 ? NRE_OK : NRE_EINVAL;
 }
 
 template <typename T, int L>
 int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_t st, int64_t N) {
   constexpr int NT = ColShape<L, sizeof(T)>::NT;
-  const int gx = persistent_gx(a.n_units, B);
-  *nparts = gx;
   const size_t smem = ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0);
+  const int gx = persistent_gx(a.n_units, B, resident_ctas(col_min_ctas(NT, sizeof(T)), smem));
+  *nparts = gx;
   if (smem > 200 * 1024) return set_error(NRE_EINVAL, "column sweep of length %d needs %zu bytes of shared memory", L, smem);
   const dim3 grid((unsigned)gx, B);
   const char* name = sizeof(T) == 8 ? (mid ? "col_sweep_f64_metric" : "col_sweep_f64")

@@ -9,7 +9,23 @@
 namespace nre {
 
 constexpr int kMaxGridX = 128;      // CTAs per sample of a sweep (bounds the partials buffer)
-constexpr int kResidentCTAs = 456;  // target CTAs of a persistent sweep (3 per SM)
+
+// CTAs of a persistent register sweep resident at once: per SM the fewer of
+// the kernel's compiled minimum (row_min_ctas / col_min_ctas) and what its
+// shared memory admits (1 KB reserved per CTA), times the SMs of the device.
+inline int resident_ctas(int min_ctas, size_t smem) {
+  static const int2 dev = [] {
+    int d = 0, nsm = 152, sm = 228 * 1024;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+    return make_int2(nsm, sm);
+  }();
+  int per = (int)((size_t)dev.y / (smem + 1024));
+  if (per > min_ctas) per = min_ctas;
+  if (per < 1) per = 1;
+  return per * dev.x;
+}
 
 // Algorithmic bytes of a sweep: per-sample arrays count B times, arrays shared
 // by the batch (expansion point, weights, fixed spectrum) once.

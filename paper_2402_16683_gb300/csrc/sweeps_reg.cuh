@@ -129,8 +129,26 @@ struct RowSmem {
 // per-pixel int16 bins and per-bin tables in shared memory.
 enum { SK_GEN = 0, SK_BUF = 1, SK_TAB = 2 };
 
+// CTAs per SM the sweeps are compiled for (the minimum of their
+// __launch_bounds__; the host sizes persistent grids with it): four 256-thread
+// CTAs for FP32 lines (at most 64 registers, measured without spills), three
+// for FP64 lines and for the row sweep with the metric's epilogue at
+// L >= 1024 (four would spill there), two for 3-D orbits (two lines per
+// thread), one for wider CTAs.
+__host__ __device__ constexpr int row_min_ctas(int nt, int pm, int ek, int es, int l) {
+  return nt <= 256 ? (pm == 3 ? 2 : (((ek == SK_TAB && l >= 1024) || es == 8) ? 3 : 4)) : 1;
+}
+// The row sweep with the metric's epilogue loads its base values straight from
+// global memory (with its other per-pixel loads) where that lets four CTAs
+// share an SM; elsewhere the base rows are staged with cp.async, which hides
+// their latency better at the lower occupancy.
+__host__ __device__ constexpr bool row_direct_base(int nt, int pm, int ek, int es, int l) {
+  return ek == SK_TAB && row_min_ctas(nt, pm, ek, es, l) >= 4;
+}
+__host__ __device__ constexpr int col_min_ctas(int nt, int es) { return nt <= 256 ? (es == 8 ? 3 : 4) : (nt <= 512 ? 2 : 1); }
+
 template <typename T, int L, int PM, bool MID, int PK, int EK>
-__global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM == 3 ? 2 : 3) : 1))
+__global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT, PM, EK, sizeof(T), L))
     k_row_reg(RowArgs<T> a) {
   typedef typename CplxT<T>::type C;
   typedef RowSmem<T, L, PM> SM;
@@ -140,9 +158,11 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   C* tw = reinterpret_cast<C*>(smem_raw);
   T* stage = reinterpret_cast<T*>(tw + L);                  // [2][STGA]
   const bool sbase = a.epi.mode == EPI_AMP && a.epi.base != nullptr;
+  constexpr bool DIRECT_BASE = row_direct_base(RowShape<L>::NT, PM, EK, sizeof(T), L);
+  const bool bstaged = sbase && !DIRECT_BASE;
   T* bstage = stage + 2 * SM::STGA;                          // [XSZ]: the current units' base rows
   const int nbp = (a.nb + 3) / 4 * 4;
-  T* sA = bstage + (sbase ? SM::XSZ : 0);
+  T* sA = bstage + (bstaged ? SM::XSZ : 0);
   T* sdA = sA + nbp;
   T* hist = sdA + nbp;  // per-bin sums of the CTA in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
@@ -195,7 +215,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
   cp_commit();
   for (int it = 0; u0 < a.n_units; u0 += ustride, ++it) {
     const int cur = it & 1;
-    if (sbase) issue(u0, 0, true);  // group B: this iteration's base rows
+    if (bstaged) issue(u0, 0, true);  // group B: this iteration's base rows
     cp_commit();
     if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1, false);  // group A: next input
     cp_commit();
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
       reg_fft<C, L, LPU>(v, smc, tw, t, sync);
     }
     reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
-    if (sbase) {
+    if (bstaged) {
       cp_wait<1>();  // everything but group A: the base rows
       __syncthreads();
     }
@@ -306,6 +326,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
       // A) loads and the P combination, B) stores and bin reductions.
       const int16_t* bp = epi.av.bpix;
       const T* xp = epi.xi_p + (int64_t)bsample * epi.ps;
+      const T* bsrc = epi.base + (int64_t)bsample * epi.bs;  // the TAB epilogue always has a base
       T* yo = epi.y + (int64_t)bsample * epi.ys;
       const int fl = valid ? __ldg(&a.gflags[unit]) : 0;
       const bool f0 = fl & 1, f1 = fl & 2;
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
 #pragma unroll
       for (int c0 = 0; c0 < 8; c0 += CH) {
         int bn[CH][SLOTS];
-        T xv[CH][SLOTS], val[CH][SLOTS];
+        T xv[CH][SLOTS], val[CH][SLOTS], bvv[CH][SLOTS];
 #pragma unroll
         for (int s = 0; s < CH; ++s)
 #pragma unroll
@@ -325,6 +346,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
             if (PM == 2 && sl == 1 && f0) bn[s][1] = bn[s][0];
             else bn[s][sl] = valid ? (int)__ldg(&bp[f]) : -1;
             xv[s][sl] = valid ? __ldg(&xp[f]) : T(0);
+            if constexpr (DIRECT_BASE) bvv[s][sl] = valid ? bsrc[f] : T(0);
           }
 #pragma unroll
         for (int s = 0; s < CH; ++s) {
@@ -354,7 +376,9 @@ __global__ void __launch_bounds__(RowShape<L>::NT, (RowShape<L>::NT <= 256 ? (PM
 #pragma unroll
           for (int sl = 0; sl < SLOTS; ++sl) {
             const int b_ = bn[s][sl];
-            const T bv = BV[sl * L + x];  // the TAB epilogue always has a base (v or xi')
+            T bv;
+            if constexpr (DIRECT_BASE) bv = bvv[s][sl];
+            else bv = BV[sl * L + x];
             const T o = (b_ < 0 ? a0 : sA[b_]) * val[s][sl] + bv;
             if (valid) {
               yo[row[sl] * L + x] = o;
@@ -474,7 +498,7 @@ struct ColSmem {
 };
 
 template <typename T, int L, bool MID, int PK, int EK>
-__global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, (ColShape<L, sizeof(T)>::NT <= 256 ? 3 : (ColShape<L, sizeof(T)>::NT <= 512 ? 2 : 1)))
+__global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColShape<L, sizeof(T)>::NT, sizeof(T)))
     k_col_reg(ColArgs<T> a) {
   typedef typename CplxT<T>::type C;
   typedef ColSmem<T, L> SM;
