@@ -20,6 +20,9 @@ void clear_error();
 
 // Launch tracing (prof.cu): bracket every kernel launch; `bytes` is the
 // launch's algorithmic traffic (unique bytes of its global inputs + outputs).
+// Whether per-launch tracing is on (callers that would run launches
+// concurrently on several streams serialise them while it is).
+bool prof_tracing();
 void prof_begin(const char* name, double bytes, cudaStream_t st);
 void prof_end(cudaStream_t st);
 

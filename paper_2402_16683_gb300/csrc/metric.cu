@@ -53,6 +53,12 @@ template <typename T>
 int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   nre_cf_plan* p = m->cf;
   const int64_t N = p->N;
+  if (!m->side && p->ndim >= 2 && m->max_batch >= 2) {
+    // the second stream of split products (created here, outside any capture)
+    NRE_TRY_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    NRE_TRY_CUDA(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    NRE_TRY_CUDA(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+  }
   NRE_TRY(ensure(m->xi_p, p->stride * sizeof(T)));
   NRE_TRY_CUDA(cudaMemcpyAsync(m->xi_p.p, xi_p_in, p->latent * sizeof(T), cudaMemcpyDeviceToDevice, st));
   NRE_TRY(ensure(m->w, N * sizeof(T)));
@@ -157,8 +163,37 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
     epi.av = pro.av;
   }
   int np = 0;
-  NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
-                         model ? m->part.as<double>() : nullptr, &np, st));
+  // Two half batches on two streams: the persistent sweeps of one half fill
+  // the SMs that the other half's last rounds leave idle (a sweep's units
+  // rarely divide evenly over its resident CTAs).  Grids and fused partials
+  // are per sample, so each half is the same computation on its own samples.
+  // Needs per-sample bin sums (gsum) or none; not while launches are traced.
+  const bool split = m->side && B >= 2 && p->ndim >= 2 && (!model || m->amp_lin) && !prof_tracing();
+  if (!split) {
+    NRE_TRY(run_hartley<T>(p, B, pro, epi, &mid, m->tmp0.as<T>(), m->tmp1.as<T>(),
+                           model ? m->part.as<double>() : nullptr, &np, st));
+  } else {
+    NRE_TRY_CUDA(cudaEventRecord(m->ev_fork, st));
+    NRE_TRY_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+    const int B0 = (B + 1) / 2;
+    for (int h = 0; h < 2; ++h) {
+      const int b0 = h ? B0 : 0, Bh = h ? B - B0 : B0;
+      Pro<T> ph = pro;
+      Epi<T> eh = epi;
+      ph.x += (int64_t)b0 * pro.xs;
+      if (ph.dA) ph.dA += (int64_t)b0 * nb;
+      if (ph.ps) ph.xi_p += (int64_t)b0 * ph.ps;
+      eh.y += (int64_t)b0 * epi.ys;
+      if (eh.base) eh.base += (int64_t)b0 * epi.bs;
+      if (eh.ps) eh.xi_p += (int64_t)b0 * eh.ps;
+      if (eh.gsum) eh.gsum += (int64_t)b0 * nb;
+      if (eh.dot) eh.dot += (int64_t)b0 * kDotStride;
+      NRE_TRY(run_hartley<T>(p, Bh, ph, eh, &mid, m->tmp0.as<T>() + (int64_t)b0 * N,
+                             m->tmp1.as<T>() + (int64_t)b0 * N, nullptr, &np, h ? m->side : st));
+    }
+    NRE_TRY_CUDA(cudaEventRecord(m->ev_join, m->side));
+    NRE_TRY_CUDA(cudaStreamWaitEvent(st, m->ev_join, 0));
+  }
   if (model && !hyper_in_cg) {
     if (m->amp_lin)  // the bin sums are complete in gsum (one "partial")
       NRE_TRY(amp_vjp_lin<T>(m->amp_Gt.as<float>(), nb, p->n_hyper, m->gsum.as<double>(), v + N, S, out + N,

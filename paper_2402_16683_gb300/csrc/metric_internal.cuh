@@ -50,6 +50,17 @@ struct nre_metric {
   nre::DevBuf pc_invD, pc_e;          // per pixel: 1 / D and A xi_p / D
   nre::DevBuf pc_Gt;                  // float [n_bins][n_hyper]: G transposed
   nre::DevBuf pc_cdev;                // double: pc_c on the device
+  // second stream of a metric product split into two half batches (metric.cu)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  nre_metric() = default;
+  nre_metric(const nre_metric&) = delete;
+  nre_metric& operator=(const nre_metric&) = delete;
+  ~nre_metric() {
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
 };
 
 namespace nre {

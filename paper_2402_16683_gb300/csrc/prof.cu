@@ -47,6 +47,8 @@ std::atomic<long long>& dev_bytes() {
 
 void prof_add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+bool prof_tracing() { return g_on.load(std::memory_order_relaxed) != 0; }
+
 void prof_begin(const char* name, double bytes, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
