@@ -485,7 +485,8 @@ def run_icr(args, lib, flush, stream, peak):
     """ICR on the log-radial chart refined 8^2 -> 1024^2 (7 levels), Matern-3/2
     (length scale 0.1, unit variance), FP32, batch 32: forward (= JVP, the
     model is linear in xi) and the hand-written VJP; fields/s and the HBM
-    fraction of all refinement kernels together."""
+    fraction of a whole call (its kernels' algorithmic bytes over its untraced
+    time) and of its kernels traced one by one."""
     import ctypes as C
 
     import torch
@@ -529,7 +530,10 @@ def run_icr(args, lib, flush, stream, peak):
         kms = sum(x[1] for x in kern.values())
         kbytes = sum(x[2] for x in kern.values())
         res[name] = {"fields_per_s": B / (ms / 1e3), "ms": ms, "bytes": kbytes / n,
-                     "achieved_GBps": kbytes / (kms / 1e3) / 1e9, "frac": kbytes / (kms / 1e3) / 1e9 / peak,
+                     # all bytes of a call over its untraced time; and over the summed
+                     # device times of its kernels traced one by one
+                     "achieved_GBps": kbytes / n / (ms / 1e3) / 1e9, "frac": kbytes / n / (ms / 1e3) / 1e9 / peak,
+                     "frac_traced_kernels": kbytes / (kms / 1e3) / 1e9 / peak,
                      "kernels": {k: {"launches_per_call": x[0] / n, "us_per_call": 1e3 * x[1] / n,
                                      "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None}
                                  for k, x in kern.items()}}

@@ -34,6 +34,17 @@ struct nre_icr_plan {
   nre::DevBuf mats;              // per level: [n_l][52]: R (4x9 row-major), L (4x4 row-major)
   std::vector<int64_t> mat_off;  // element offset of level l in mats
   nre::DevBuf ws_a, ws_b, ws_c;  // per-batch level buffers
+  // second stream of a batch split into two halves (see icr_forward_t)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  nre_icr_plan() = default;
+  nre_icr_plan(const nre_icr_plan&) = delete;
+  nre_icr_plan& operator=(const nre_icr_plan&) = delete;
+  ~nre_icr_plan() {
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
 };
 
 namespace {
@@ -521,12 +532,40 @@ int ensure_ws(nre_icr_plan* p, int B) {
   return NRE_OK;
 }
 
-// s = ICR(xi) (optionally times `scale`), batch B.
+// Runs f(b0, Bh, stream) over the batch: as two halves on two streams when
+// B >= 2 and the plan has its second stream (the small levels of one half
+// are latency-bound chains of short launches; the other half's launches fill
+// the SMs meanwhile), else once.  Launch tracing serialises (one call).
+template <class F>
+int icr_split(nre_icr_plan* p, int B, cudaStream_t st, F f) {
+  if (B < 2 || nre::prof_tracing()) return f(0, B, st);
+  if (!p->side) {
+    // created on first use outside a stream capture (never inside one)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NRE_TRY_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return f(0, B, st);
+    NRE_TRY_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    NRE_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    NRE_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  }
+  NRE_TRY_CUDA(cudaEventRecord(p->ev_fork, st));
+  NRE_TRY_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  const int B0 = (B + 1) / 2;
+  NRE_TRY(f(0, B0, st));
+  NRE_TRY(f(B0, B - B0, p->side));
+  NRE_TRY_CUDA(cudaEventRecord(p->ev_join, p->side));
+  NRE_TRY_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
+  return NRE_OK;
+}
+
+// s = ICR(xi) (optionally times `scale`) for samples b0 .. b0 + B - 1 of the
+// batch (level buffers at their own samples' offsets).
 template <typename T>
-int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cudaStream_t st) {
-  NRE_TRY(ensure_ws<T>(p, B));
+int icr_forward_range(nre_icr_plan* p, const T* xi, T* s, int b0, int B, const T* scale, cudaStream_t st) {
   const int64_t big = (int64_t)p->sizes[p->n_levels - 1] * p->sizes[p->n_levels - 1];
-  T* bufs[2] = {p->ws_a.as<T>(), p->ws_b.as<T>()};
+  T* bufs[2] = {p->ws_a.as<T>() + b0 * big, p->ws_b.as<T>() + b0 * big};
+  xi += b0 * p->stride;
+  s += b0 * p->n_out;
   const int n0 = p->n0, n2 = n0 * n0;
   const T* L0 = p->L0.as<T>();
   const T* mats = p->mats.as<T>();
@@ -555,12 +594,24 @@ int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cud
   return NRE_OK;
 }
 
-// g = base + ICR^T ct, batch B (ct: [B][n_out]).
+// s = ICR(xi) (optionally times `scale`), batch B.
 template <typename T>
-int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, int B, cudaStream_t st) {
+int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cudaStream_t st) {
   NRE_TRY(ensure_ws<T>(p, B));
+  return icr_split(p, B, st, [&](int b0, int Bh, cudaStream_t sh) {
+    return icr_forward_range<T>(p, xi, s, b0, Bh, scale, sh);
+  });
+}
+
+// g = base + ICR^T ct for samples b0 .. b0 + B - 1 (ct: [batch][cts]).
+template <typename T>
+int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, int b0, int B,
+                  cudaStream_t st) {
   const int64_t big = (int64_t)p->sizes[p->n_levels - 1] * p->sizes[p->n_levels - 1];
-  T* bufs[2] = {p->ws_a.as<T>(), p->ws_b.as<T>()};
+  T* bufs[2] = {p->ws_a.as<T>() + b0 * big, p->ws_b.as<T>() + b0 * big};
+  ct += b0 * cts;
+  g += b0 * p->stride;
+  if (base) base += b0 * p->stride;
   const T* mats = p->mats.as<T>();
   const T* gin = ct;
   int64_t gis = cts;
@@ -590,6 +641,15 @@ int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, in
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
+}
+
+// g = base + ICR^T ct, batch B (ct: [B][cts]).
+template <typename T>
+int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, int B, cudaStream_t st) {
+  NRE_TRY(ensure_ws<T>(p, B));
+  return icr_split(p, B, st, [&](int b0, int Bh, cudaStream_t sh) {
+    return icr_vjp_range<T>(p, ct, cts, g, base, b0, Bh, sh);
+  });
 }
 
 template <typename T>
