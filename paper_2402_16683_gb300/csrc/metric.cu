@@ -222,7 +222,6 @@ int cf_mgvi_rhs(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cud
   epi.base = xi_prime;
   epi.bs = S;
   const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
-  const int nb = p->n_bins;
   if (model) {
     epi.av = metric_view<T>(m);
     epi.bins = 1;

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       const T* xp = pro.xi_p + (int64_t)bsample * pro.ps;
       const T a0 = pro.av.a0t;
       const int fl = valid ? __ldg(&a.gflags[unit]) : 0;
-      const bool f0 = fl & 1, f1 = fl & 2;
+      const bool f0 = fl & 1;  // mirror rows of a 2-D orbit share the canonical slot's bins
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const int x = t + T8 * s;
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
     k_col_reg(ColArgs<T> a) {
   typedef typename CplxT<T>::type C;
   typedef ColSmem<T, L> SM;
-  constexpr int T8 = L / 8, NL = ColShape<L, sizeof(T)>::NL, WP = ColShape<L, sizeof(T)>::WP;
+  constexpr int T8 = L / 8, WP = ColShape<L, sizeof(T)>::WP;
   constexpr int LS = rline(L), CH = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
