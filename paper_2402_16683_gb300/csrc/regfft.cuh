@@ -22,9 +22,24 @@
 namespace nre {
 
 __host__ __device__ constexpr int rpad(int e) { return e + (e >> 4); }
-// Line stride: padded length plus one, so that lines sit on different banks
-// (the stride is an odd number of complex elements).
-__host__ __device__ constexpr int rline(int L) { return L + L / 16 + 1; }
+// Exchange layouts: element e of a line at e + Q (e div 16), Q pad elements per
+// 16.  Which Q keeps a half-warp's 8-byte accesses on distinct banks depends
+// on the exchange (a model of the access patterns, checked for every line of
+// 256..4096 points): after the first radix-8 pass Q = 1, after the second
+// Q = 2 (with Q = 1 its scatter puts two lanes of each half-warp on one bank),
+// the mirror exchange Q = 0 (its reversed reads collide at every other Q).
+// Lines of up to 128 points (several lines per warp) and 16-byte elements
+// keep Q = 1 throughout.
+template <int Q>
+__host__ __device__ constexpr int qpad(int e) { return e + Q * (e >> 4); }
+template <typename C, int L, int NS>
+__host__ __device__ constexpr int exch_q() { return (sizeof(C) == 8 && L / 8 >= 32 && NS == 8) ? 2 : 1; }
+template <typename C, int L>
+__host__ __device__ constexpr int mirror_q() { return (sizeof(C) == 8 && L / 8 >= 32) ? 0 : 1; }
+// Line stride: room for the widest layout (Q = 2 from 256 points on) plus one;
+// up to 128 points an odd number of complex elements, so that the lines that
+// share a warp sit on different banks.
+__host__ __device__ constexpr int rline(int L) { return L >= 256 ? L + L / 8 + 1 : L + L / 16 + 1; }
 // Line stride when NL lines are interleaved across the lanes of a warp: the
 // lines start 16/NL complex elements apart modulo 16.
 __host__ __device__ constexpr int rline_il(int L, int NL) { return L + L / 16 + (NL < 16 ? 16 / NL : 1); }
@@ -55,10 +70,11 @@ __host__ __device__ constexpr int tw_off(int L, int NS) {
 }
 __host__ __device__ constexpr int tw_total(int L) { return tw_off(L, L); }
 
-// Offset of rpad(base + r * NS) from rpad(base) for a pass's scatter, where
-// base = (j - k) R + k with k = j mod NS (the padding adds one element per 16).
-__host__ __device__ constexpr int scatter_off(int NS, int r) {
-  return NS == 1 ? r : (NS < 16 ? r * NS + ((r * NS) >> 4) : r * NS + r * (NS >> 4));
+// Offset of qpad<Q>(base + r * NS) from qpad<Q>(base) for a pass's scatter,
+// where base = (j - k) R + k with k = j mod NS (base mod 16 + r NS never
+// crosses a 16-block other than through r NS itself).
+__host__ __device__ constexpr int scatter_off(int NS, int r, int Q) {
+  return NS == 1 ? r : (NS < 16 ? r * NS + Q * ((r * NS) >> 4) : r * NS + Q * r * (NS >> 4));
 }
 
 template <typename C, int L, int NS, int LPT>
@@ -105,41 +121,42 @@ struct RegPass {
     } else {
       typedef RegPass<C, L, NS * R, LPT> Next;
       constexpr int R2 = Next::R, M2 = 8 / R2;
+      constexpr int Q = exch_q<C, L, NS>();
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const int j = t + T8 * m;
         const int k = j & (NS - 1);
         const int base = (j - k) * R + k;
         if constexpr (FAST) {
-          const int pb = rpad(base);
+          const int pb = qpad<Q>(base);
 #pragma unroll
           for (int q = 0; q < LPT; ++q)
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[q][pb + scatter_off(NS, r)] = v[q][m * R + r];
+            for (int r = 0; r < R; ++r) sm[q][pb + scatter_off(NS, r, Q)] = v[q][m * R + r];
         } else {
 #pragma unroll
           for (int q = 0; q < LPT; ++q)
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[q][rpad(base + r * NS)] = v[q][m * R + r];
+            for (int r = 0; r < R; ++r) sm[q][qpad<Q>(base + r * NS)] = v[q][m * R + r];
         }
       }
       sync();
       if constexpr (FAST) {
-        // rpad(t + T8 s') = rpad(t) + s' (T8 + T8 / 16)
-        const int pt = rpad(t);
+        // qpad(t + T8 s') = qpad(t) + s' (T8 + Q T8 / 16)
+        const int pt = qpad<Q>(t);
 #pragma unroll
         for (int q = 0; q < LPT; ++q)
 #pragma unroll
           for (int m = 0; m < M2; ++m)
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][pt + (m + r * M2) * (T8 + T8 / 16)];
+            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][pt + (m + r * M2) * (T8 + Q * (T8 / 16))];
       } else {
 #pragma unroll
         for (int q = 0; q < LPT; ++q)
 #pragma unroll
           for (int m = 0; m < M2; ++m)
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][rpad(t + T8 * m + r * (L / R2))];
+            for (int r = 0; r < R2; ++r) v[q][m * R2 + r] = sm[q][qpad<Q>(t + T8 * m + r * (L / R2))];
       }
       sync();
       Next::run(v, sm, tw, t, sync);
@@ -154,20 +171,22 @@ __device__ __forceinline__ void reg_fft(C (&v)[LPT][8], C* const* sm, const C* t
 }
 
 // zm[q][s] = X_q[-(t + s L/8) mod L] through the shared line buffers.
-// For T8 a multiple of 16 the mirror reads rpad(L - t) - s (T8 + T8/16); thread
-// 0's X[0] is also stored at rpad(L) (the line's last slot) for its s = 0 read.
+// For T8 a multiple of 16 the mirror reads qpad(L - t) - s (T8 + Q T8/16);
+// thread 0's X[0] is also stored at qpad(L) (past the line's last element)
+// for its s = 0 read.
 template <typename C, int L, int LPT, class Sync>
 __device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8], C* const* sm, int t,
                                            Sync sync) {
   constexpr int T8 = L / 8;
   if constexpr ((T8 % 16) == 0) {
-    constexpr int ST = T8 + T8 / 16;
-    const int pt = rpad(t), pm = rpad(L - t);
+    constexpr int Q = mirror_q<C, L>();
+    constexpr int ST = T8 + Q * (T8 / 16);
+    const int pt = qpad<Q>(t), pm = qpad<Q>(L - t);
 #pragma unroll
     for (int q = 0; q < LPT; ++q) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) sm[q][pt + s * ST] = v[q][s];
-      if (t == 0) sm[q][rpad(L)] = v[q][0];
+      if (t == 0) sm[q][qpad<Q>(L)] = v[q][0];
     }
     sync();
 #pragma unroll
