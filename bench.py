@@ -71,7 +71,7 @@ def parse():
 # the dominant one, keyed by (kernel tag, batch), averaged over the launch
 # variants the tag covers; None where no capture of the current kernels exists.
 DRAM_TRAFFIC = {
-    ("row_sweep_f32_2d", 32): (52.36e6, "profiles/traffic_f32_2d_512x512_b32.md"),
+    ("row_sweep_f32_2d", 32): (53.12e6, "profiles/traffic_f32_2d_512x512_b32.md"),
 }
 
 
