@@ -30,6 +30,13 @@ CASES = [
     ((64, 64), "power", "f32", 256),
     ((32, 16, 64), "power", "f32", 256),
     ((4096, 8), "matern", "f32", 256),
+    # lines of 512 / 1024 / 2048 points along either axis (each FFT exchange
+    # has its own shared-memory layout from 256 points on)
+    ((2048,), "power", "f32", 256),
+    ((16, 2048), "power", "f32", 256),
+    ((2048, 16), "power", "f32", 256),
+    ((8, 1024), "matern", "f32", 256),
+    ((512, 8), "power", "f32", 256),
 ]
 
 

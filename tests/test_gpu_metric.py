@@ -75,6 +75,8 @@ def lanczos_kappa(om, xi_p, w, b, iters):
     ((64, 64, 64), "power", "f32", "gauss"),
     ((4096,), "power", "f32", "gauss"),
     ((1024, 1024), "power", "f32", "gauss"),
+    ((2048, 16), "power", "f32", "poisson"),
+    ((16, 2048), "power", "f32", "poisson"),
 ])
 def test_metric_apply(shape, kind, dtype, lik):
     plan, om, M, xi_p, w = _setup(shape, kind, dtype, lik)
