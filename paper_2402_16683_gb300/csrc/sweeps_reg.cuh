@@ -274,12 +274,16 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       for (int s = 0; s < 8; ++s) {
         const int x = t + T8 * s;
         int bn[LPU][2];
+        T xv[LPU][2];
 #pragma unroll
         for (int q = 0; q < LPU; ++q)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             if (PM == 2 && h == 1 && f0) bn[q][1] = bn[q][0];
             else bn[q][h] = valid ? (int)__ldg(&bp[row[2 * q + h] * L + x]) : -1;
+            // the expansion point does not depend on the bin: its load goes
+            // out with the bin's instead of after it
+            xv[q][h] = __ldg(&xp[row[2 * q + h] * L + x]);
           }
 #pragma unroll
         for (int q = 0; q < LPU; ++q) {
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
           for (int h = 0; h < 2; ++h) {
             const int b_ = bn[q][h];
             T val = (b_ < 0 ? a0 : sA[b_]) * X[(2 * q + h) * L + x];
-            if (b_ >= 0) val += sdA[b_] * __ldg(&xp[row[2 * q + h] * L + x]);
+            if (b_ >= 0) val += sdA[b_] * xv[q][h];
             e[h] = sval[2 * q + h] ? val : T(0);
           }
           v[q][s] = cmake<C>(e[0], e[1]);
