@@ -103,8 +103,9 @@ struct Pro {
     if (mode == PRO_BUF) return v;
     if (mode == PRO_SQRTW) return sqrt(__ldg(&w[flat])) * v;
     const int bn = av.binned() ? av.bin(flat) : -1;
+    const T xv = dA != nullptr ? xi_p[b * ps + flat] : T(0);  // loaded alongside the bin, not after it
     T u = av.amp_t(b, flat, bn, stab) * v;
-    if (dA != nullptr && bn >= 0) u += (stdA ? stdA[bn] : T(__ldg(&dA[b * nb + bn]))) * xi_p[b * ps + flat];
+    if (dA != nullptr && bn >= 0) u += (stdA ? stdA[bn] : T(__ldg(&dA[b * nb + bn]))) * xv;
     return u;
   }
   // Values at flat and flat + 1 (flat even) as one complex pair.
@@ -187,11 +188,12 @@ struct Epi {
       return w;
     } else {
       const int bn = av.binned() ? av.bin(flat) : -1;
+      const T xv = bins ? xi_p[b * ps + flat] : T(0);  // loaded alongside the bin, not after it
       const T o = av.amp_t(b, flat, bn, stab) * val + bval;
       y[b * ys + flat] = o;
       if (bins && bn >= 0) {
         bn_out = bn;
-        contrib = xi_p[b * ps + flat] * val;
+        contrib = xv * val;
       }
       return o;
     }
