@@ -509,6 +509,192 @@ __global__ void __launch_bounds__(ICR4_X * ICR4_Y) k_icr_refine4_t(int nc, const
   st4(g_c + b * gcs + (int64_t)ip * nc + jp0, acc);
 }
 
+// The coarse end of a chart, level 0 and the refinements whose coarse side is
+// at most kSmallN, in one CTA per sample with the levels in shared memory:
+// as separate launches they were a chain of short latency-bound kernels.
+constexpr int kSmallN = 32;
+constexpr int SMALL_THREADS = 1024;
+struct IcrSmall {
+  int n0, nlev;            // fused refinements: levels 0 .. nlev - 1
+  int nc[10];              // coarse side of level l
+  int64_t mat_off[10];     // its matrices in mats
+  int64_t xi_off[10];      // its fine excitations in the latent vector
+};
+
+// Shared memory of the fused forward (two level buffers, one level's fine
+// excitations and one level's matrices) and adjoint (the finest fused fine
+// level, one coarse level and one level's matrices), in elements.
+inline int64_t small_smem(const IcrSmall& sp, bool adjoint) {
+  const int64_t n = sp.nc[sp.nlev - 1];
+  return (adjoint ? 5 : 6) * n * n + n * MAT;
+}
+
+// Forward: s_0 = L_K0 xi_0, then s_f = R s_nbhd + L xi_f level by level; the
+// last fused level goes to out (times `scale` when given).
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS) k_icr_small(IcrSmall sp, const T* __restrict__ L0,
+                                                            const T* __restrict__ mats, const T* xi, int64_t xs,
+                                                            T* out, int64_t os, const T* scale) {
+  extern __shared__ __align__(16) unsigned char small_raw[];
+  const int ncl = sp.nc[sp.nlev - 1];
+  T* cur = reinterpret_cast<T*>(small_raw);
+  T* nxt = cur + ncl * ncl;
+  T* sxi = nxt + ncl * ncl;      // [4 ncl^2]: this level's fine excitations
+  T* smat = sxi + 4 * ncl * ncl;
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  const T* x = xi + b * xs;
+  const int n2 = sp.n0 * sp.n0;
+  for (int i = tid >> 5; i < n2; i += SMALL_THREADS / 32) {
+    T acc = T(0);
+    for (int j = lane; j <= i; j += 32) acc += L0[i * n2 + j] * x[j];
+    acc = warp_sum_t(acc);
+    if (lane == 0) cur[i] = acc;
+  }
+  for (int l = 0; l < sp.nlev; ++l) {
+    const int nc = sp.nc[l], nf = 2 * nc;
+    for (int k = tid; k < nc * MAT; k += SMALL_THREADS) smat[k] = mats[sp.mat_off[l] + k];
+    for (int k = tid; k < nf * nf; k += SMALL_THREADS) sxi[k] = x[sp.xi_off[l] + k];
+    __syncthreads();  // this level's input, excitations and matrices are in place
+    const bool last = l == sp.nlev - 1;
+    T* dst = last ? out + b * os : nxt;
+    const T* xf = sxi;
+    for (int pix = tid; pix < nc * nc; pix += SMALL_THREADS) {
+      const int i = pix / nc, j = pix - i * nc;
+      const T* m = smat + i * MAT;
+      const int w = window(nc, i);
+      const int jm = j == 0 ? nc - 1 : j - 1, jp = j == nc - 1 ? 0 : j + 1;
+      T nq[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* row = cur + (w + a) * nc;
+        nq[3 * a] = row[jm];
+        nq[3 * a + 1] = row[j];
+        nq[3 * a + 2] = row[jp];
+      }
+      const int64_t f0 = (int64_t)(2 * i) * nf + 2 * j, f1 = f0 + nf;
+      const T e[4] = {xf[f0], xf[f0 + 1], xf[f1], xf[f1 + 1]};
+      T o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) acc += m[k * 9 + n] * nq[n];
+#pragma unroll
+        for (int mm = 0; mm <= k; ++mm) acc += m[36 + k * 4 + mm] * e[mm];
+        o[k] = acc;
+      }
+      if (last && scale) {
+        o[0] *= scale[f0];
+        o[1] *= scale[f0 + 1];
+        o[2] *= scale[f1];
+        o[3] *= scale[f1 + 1];
+      }
+      dst[f0] = o[0];
+      dst[f0 + 1] = o[1];
+      dst[f1] = o[2];
+      dst[f1 + 1] = o[3];
+    }
+    __syncthreads();  // the next level reads nxt; cur and the matrices are rewritten
+    T* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
+// Adjoint of the fused levels: from g at the finest fused level (gin), per
+// level g_xi_f = base + L^T g_children and the gather g_c = sum R^T g_children,
+// then level 0: g_0 = base + L_K0^T g.
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS) k_icr_small_t(IcrSmall sp, const T* __restrict__ L0,
+                                                              const T* __restrict__ mats, const T* gin,
+                                                              int64_t gis, T* g, int64_t gs, const T* base,
+                                                              int64_t bs) {
+  extern __shared__ __align__(16) unsigned char small_raw[];
+  const int ncl = sp.nc[sp.nlev - 1], nfl = 2 * ncl;
+  T* fine = reinterpret_cast<T*>(small_raw);  // [nfl^2], later a coarse level
+  T* coarse = fine + nfl * nfl;                 // [ncl^2], later a fine level
+  T* smat = coarse + ncl * ncl;
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < nfl * nfl; k += SMALL_THREADS) fine[k] = gin[b * gis + k];
+  for (int l = sp.nlev - 1; l >= 0; --l) {
+    const int nc = sp.nc[l], nf = 2 * nc;
+    for (int k = tid; k < nc * MAT; k += SMALL_THREADS) smat[k] = mats[sp.mat_off[l] + k];
+    __syncthreads();  // this level's g and matrices are in place
+    T* gx = g + b * gs + sp.xi_off[l];
+    const T* bb = base ? base + b * bs + sp.xi_off[l] : nullptr;
+    for (int pix = tid; pix < nc * nc; pix += SMALL_THREADS) {
+      const int ip = pix / nc, jp = pix - ip * nc;
+      {
+        const int64_t f0 = (int64_t)(2 * ip) * nf + 2 * jp, f1 = f0 + nf;
+        const T gc[4] = {fine[f0], fine[f0 + 1], fine[f1], fine[f1 + 1]};
+        const T* M = smat + ip * MAT + 36;
+        T o[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          T acc = T(0);
+#pragma unroll
+          for (int k = m; k < 4; ++k) acc += M[k * 4 + m] * gc[k];
+          o[m] = acc;
+        }
+        if (bb) {
+          o[0] += bb[f0];
+          o[1] += bb[f0 + 1];
+          o[2] += bb[f1];
+          o[3] += bb[f1 + 1];
+        }
+        gx[f0] = o[0];
+        gx[f0 + 1] = o[1];
+        gx[f1] = o[2];
+        gx[f1 + 1] = o[3];
+      }
+      T acc = T(0);
+      const int i_lo = ip - 2 < 0 ? 0 : ip - 2, i_hi = ip + 2 > nc - 1 ? nc - 1 : ip + 2;
+      for (int i = i_lo; i <= i_hi; ++i) {
+        const int a = ip - window(nc, i);
+        if (a < 0 || a > 2) continue;
+        const T* M = smat + i * MAT;
+#pragma unroll
+        for (int bcol = 0; bcol < 3; ++bcol) {
+          int j = jp - (bcol - 1);
+          j = j < 0 ? j + nc : (j >= nc ? j - nc : j);
+          const int f0 = 2 * i * nf + 2 * j;
+          const int n = 3 * a + bcol;
+          acc += M[0 * 9 + n] * fine[f0] + M[1 * 9 + n] * fine[f0 + 1] + M[2 * 9 + n] * fine[f0 + nf] +
+                 M[3 * 9 + n] * fine[f0 + nf + 1];
+        }
+      }
+      coarse[pix] = acc;
+    }
+    __syncthreads();  // the next level reads coarse as its fine level
+    T* t = fine;
+    fine = coarse;
+    coarse = t;
+  }
+  const int n2 = sp.n0 * sp.n0;
+  for (int j = tid >> 5; j < n2; j += SMALL_THREADS / 32) {
+    T acc = T(0);
+    for (int i = j + lane; i < n2; i += 32) acc += L0[i * n2 + j] * fine[i];
+    acc = warp_sum_t(acc);
+    if (lane == 0) g[b * gs + j] = acc + (base ? base[b * bs + j] : T(0));
+  }
+}
+
+// The fused coarse levels of the plan: refinements 0 .. K - 1 with coarse side
+// at most kSmallN (K = 0: none).
+IcrSmall small_plan(const nre_icr_plan* p) {
+  IcrSmall sp{};
+  sp.n0 = p->n0;
+  int K = 0;
+  while (K < p->n_levels && p->sizes[K] <= kSmallN) {
+    sp.nc[K] = p->sizes[K];
+    sp.mat_off[K] = p->mat_off[K];
+    sp.xi_off[K] = p->offsets[K + 1];
+    ++K;
+  }
+  sp.nlev = K;
+  return sp;
+}
+
 template <typename T>
 __global__ void k_scale_sqrt(const T* w, const T* x, int64_t xs, T* y, int64_t ys, int64_t n) {
   const int b = blockIdx.y;
@@ -569,11 +755,28 @@ int icr_forward_range(nre_icr_plan* p, const T* xi, T* s, int b0, int B, const T
   const int n0 = p->n0, n2 = n0 * n0;
   const T* L0 = p->L0.as<T>();
   const T* mats = p->mats.as<T>();
-  prof_begin("icr_level0", (double)B * 2 * n2 * sizeof(T), st);
-  k_icr_level0<T><<<dim3((n2 + 7) / 8, B), 256, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
-  prof_end(st);
-  NRE_CHECK_LAUNCH();
-  for (int l = 0; l < p->n_levels; ++l) {
+  const IcrSmall sp = small_plan(p);
+  if (sp.nlev > 0) {
+    // level 0 and the coarse refinements in one CTA per sample
+    const bool all = sp.nlev == p->n_levels;
+    const int ncl = sp.nc[sp.nlev - 1];
+    const size_t smem = (size_t)small_smem(sp, false) * sizeof(T);
+    if (smem > 48 * 1024)
+      NRE_TRY_CUDA(cudaFuncSetAttribute(k_icr_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double xib = 0.0;
+    for (int l = 0; l < sp.nlev; ++l) xib += 4.0 * sp.nc[l] * sp.nc[l];
+    prof_begin("icr_small", (double)B * sizeof(T) * (n2 + xib + 4.0 * ncl * ncl * (all && scale ? 2 : 1)), st);
+    k_icr_small<T><<<B, SMALL_THREADS, smem, st>>>(sp, L0, mats, xi, p->stride, all ? s : bufs[sp.nlev & 1],
+                                                   all ? p->n_out : big, all ? scale : nullptr);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+  } else {
+    prof_begin("icr_level0", (double)B * 2 * n2 * sizeof(T), st);
+    k_icr_level0<T><<<dim3((n2 + 7) / 8, B), 256, 0, st>>>(L0, xi, p->stride, bufs[0], big, n2);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+  }
+  for (int l = sp.nlev; l < p->n_levels; ++l) {
     const int nc = p->sizes[l];
     const bool last = l == p->n_levels - 1;
     T* out = last ? s : bufs[(l + 1) & 1];
@@ -616,7 +819,8 @@ int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base
   const T* gin = ct;
   int64_t gis = cts;
   int which = 0;
-  for (int l = p->n_levels - 1; l >= 0; --l) {
+  const IcrSmall sp = small_plan(p);
+  for (int l = p->n_levels - 1; l >= sp.nlev; --l) {
     const int nc = p->sizes[l];
     T* gc = bufs[which];
     prof_begin("icr_refine_t", (double)nc * nc * sizeof(T) * B * (base ? 13.0 : 9.0), st);
@@ -636,6 +840,21 @@ int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base
     which ^= 1;
   }
   const int n2 = p->n0 * p->n0;
+  if (sp.nlev > 0) {
+    // the coarse refinements and level 0 in one CTA per sample
+    const int ncl = sp.nc[sp.nlev - 1];
+    const size_t smem = (size_t)small_smem(sp, true) * sizeof(T);
+    if (smem > 48 * 1024)
+      NRE_TRY_CUDA(cudaFuncSetAttribute(k_icr_small_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double xib = 0.0;
+    for (int l = 0; l < sp.nlev; ++l) xib += 4.0 * sp.nc[l] * sp.nc[l];
+    prof_begin("icr_small_t", (double)B * sizeof(T) * (4.0 * ncl * ncl + (xib + n2) * (base ? 2 : 1)), st);
+    k_icr_small_t<T><<<B, SMALL_THREADS, smem, st>>>(sp, p->L0.as<T>(), mats, gin, gis, g, p->stride, base,
+                                                     p->stride);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+    return NRE_OK;
+  }
   prof_begin("icr_level0_t", (double)B * (base ? 3 : 2) * n2 * sizeof(T), st);
   k_icr_level0_t<T><<<dim3((n2 + 7) / 8, B), 256, 0, st>>>(p->L0.as<T>(), gin, gis, g, p->stride, base, p->stride, n2);
   prof_end(st);
