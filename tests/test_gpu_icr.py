@@ -93,9 +93,12 @@ def test_cf_autograd_fd_and_oracle_gradient():
     assert rel_max(host(fd)[0], jv) <= 1e-3
 
 
-def test_icr_metric_and_cg():
+@pytest.mark.parametrize("n0,levels", [(8, 4), (4, 3)])
+def test_icr_metric_and_cg(n0, levels):
+    """(8, 4): coarse levels fused, the finest refinement (with the weights)
+    separate; (4, 3): every level in the fused kernel, weights included."""
     import paper_2402_16683_gb300 as nre
-    plan, oc = _pair(8, 4, "f64")
+    plan, oc = _pair(n0, levels, "f64")
     lik = nre.Likelihood("gauss", sigma=0.1, response="identity", n_data=plan.n_out)
     xi_p = synth.normal(synth.SEED_POS, oc.latent_size)
     M = nre.Metric(plan, lik, _dev(plan, xi_p)[0], max_batch=2)
