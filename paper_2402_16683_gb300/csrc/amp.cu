@@ -260,14 +260,6 @@ __global__ void k_jac_store(const double* Jt, int nh, int nb, float* G, float* G
   }
 }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
-
 // dA[b][i] = sum_h G[i][h] dh[b][h] (G rows padded to nhp floats); one warp
 // per output, each lane with eight loads of G and eight of dh in flight per
 // round, FP32 arithmetic (the FP64 units of this part are a small fraction of

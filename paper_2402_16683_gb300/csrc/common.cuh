@@ -111,6 +111,15 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
 
 // ---------------------------------------------------------------- reductions
+// Sum of a float over the 32 lanes of a warp (every lane gets it).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// Dot product of two 16-byte float vectors.
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+
 // Sum of two unevaluated pairs hi + lo of floats (double-float numbers,
 // about 48 significant bits) in FP32 arithmetic: Knuth's two-sum of the high
 // parts, the low parts added to its error term, renormalised.
