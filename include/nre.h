@@ -166,7 +166,10 @@ int icr_create(nre_icr_plan **plan, const icr_chart_params *chart,
 int icr_destroy(nre_icr_plan *plan);
 int icr_latent_layout(const nre_icr_plan *plan, int64_t *n_out,
                       int64_t *latent_size, int64_t *stride);
-/* s[b] = ICR(xi[b]); xi: [batch][stride], s: [batch][n_L * n_L]. */
+/* s[b] = ICR(xi[b]); xi: [batch][stride], s: [batch][n_L * n_L].  Calls of two
+ * or more samples run as two half batches on `stream` and on a second stream
+ * the plan creates on first use (never during a stream capture), forked and
+ * joined by events: the work stays ordered on `stream`. */
 int icr_forward(nre_icr_plan *plan, const void *xi, void *s, int batch,
                 nre_stream_t stream);
 /* The ICR map is linear: jv = ICR(v) (xi_p is accepted for symmetry, unused). */
@@ -210,7 +213,10 @@ int metric_create(nre_metric **m, int model_kind, void *model_plan,
                   nre_stream_t stream);
 int metric_destroy(nre_metric *m);
 /* out[b] = v[b] + J^T (w * J v[b]), v and out [batch][stride], batch <= max_batch.
- * out may not alias v. */
+ * out may not alias v.  A product of two or more samples on a 2-D / 3-D grid
+ * runs its two half batches on `stream` and on a second stream the metric
+ * owns, forked from and joined back into `stream` by events: the call's work
+ * stays ordered on `stream` (and is captured whole into a CUDA graph). */
 int metric_apply(nre_metric *m, const void *v, void *out, int batch,
                  nre_stream_t stream);
 
