@@ -133,9 +133,12 @@ int cf_vjp(nre_cf_plan *plan, const void *xi_p, const void *ct, void *g,
  * work is enqueued, if `batch` needs more than 16 MiB of intermediates (about
  * batch * N * sizeof(dtype) per intermediate: one for 2-D grids, two for 3-D).
  * The first call on a device looks up the array's device address (with that
- * device current), so make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU (other streams, or
- * unordered host threads) race on it. */
+ * device current), so make that first call before any stream capture.  The
+ * address is kept per device ordinal for the life of the process: call from
+ * the device's primary context (the runtime API's default), and not after a
+ * cudaDeviceReset, which would leave the kept address stale.  All calls share
+ * the array: calls that overlap on the GPU (other streams, or unordered host
+ * threads) race on it. */
 int cf_forward_noalloc(nre_cf_plan *plan, const void *xi, void *s, int batch,
                        nre_stream_t stream);
 
@@ -231,7 +234,8 @@ int mgvi_rhs(nre_metric *m, const void *xi_prime, const void *eta, void *b,
  * M_p x[b] = b[b] for every b < batch by conjugate gradients, x_0 = 0, with
  * FP64 inner products and alpha/beta.  A system stops (its x frozen) once
  * ||r|| <= rtol ||b|| (recursive residual) or after maxiter iterations; rtol = 0
- * runs exactly maxiter iterations.  iters_out[batch], relres_out[batch] are
+ * runs exactly maxiter iterations unless a residual becomes exactly zero (the
+ * system is then solved and stops, as the rtol test would at any rtol).  iters_out[batch], relres_out[batch] are
  * HOST arrays (may be NULL), written after a synchronisation of `stream`.
  * Returns NRE_ENOTCONV if rtol > 0 and some system missed it. */
 int cg_solve(nre_metric *m, const void *b, void *x, int batch, double rtol,

@@ -20,11 +20,11 @@ constexpr int CG_THREADS = 256;
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
        SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
-// Blocks per system of the vector kernels: about four waves of the 152 SMs
+// Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
 // least 4 vectors per thread and at most 64 blocks.
 int cg_blocks(int64_t n, int B) {
-  int64_t nb = (4 * 152 + B - 1) / B;
+  int64_t nb = (4 * (int64_t)sm_count() + B - 1) / B;
   const int64_t cap = (n + CG_THREADS * 16 - 1) / (CG_THREADS * 16);
   if (nb > cap) nb = cap;
   if (nb > 64) nb = 64;
@@ -347,10 +347,11 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, c
       c[SC_BETA] = 0.0;
       return;
     }
-    c[SC_BETA] = rr_new / c[SC_RR];
+    c[SC_BETA] = c[SC_RR] != 0.0 ? rr_new / c[SC_RR] : 0.0;
     c[SC_RR] = rr_new;
     c[SC_ITERS] += 1.0;
-    if (rtol > 0.0 && sqrt(rr_new) <= rtol * sqrt(c[SC_BB])) {
+    // an exact zero residual ends the system at any rtol (beta would be 0/0 next)
+    if (rr_new == 0.0 || (rtol > 0.0 && sqrt(rr_new) <= rtol * sqrt(c[SC_BB]))) {
       c[SC_ACTIVE] = 0.0;
       c[SC_BETA] = 0.0;
     }

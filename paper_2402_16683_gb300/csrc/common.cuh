@@ -53,6 +53,23 @@ std::atomic<long long>& dev_bytes();
 // Kernels launched outside prof_begin (graph replays): adds to the launch count.
 void prof_add_launches(unsigned long long n);
 
+// Streaming multiprocessors of the current device (queried once per device).
+inline int sm_count() {
+  static int cache[64] = {0};
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d < 0 || d >= 64) d = 0;
+  if (cache[d] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cache[d] = n;
+  }
+  return cache[d];
+}
+
 // Owning device allocation (freed in the destructor).
 struct DevBuf {
   void* p = nullptr;

@@ -12,7 +12,8 @@
 //
 // The device address of the array is looked up with cudaGetSymbolAddress the
 // first time the entry point runs on a device (with that device current) and
-// cached per device.  Every call shares the array and leaves its last contents
+// cached per device ordinal: the cache assumes the device's primary context
+// (the runtime API's default) and is not refreshed after cudaDeviceReset.  Every call shares the array and leaves its last contents
 // in it; each call rewrites everything it reads, so nothing has to start at
 // zero.  Calls whose work overlaps on the GPU (different streams, or different
 // host threads without ordering) race on the array.

@@ -30,11 +30,11 @@ constexpr int PC_THREADS = 256;
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
        SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
 
-// Blocks per system of the vector kernels: about four waves of the 152 SMs
+// Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
 // least 4 vectors per thread and at most 64 blocks.
 int pc_blocks(int64_t n, int B) {
-  int64_t nb = (4 * 152 + B - 1) / B;
+  int64_t nb = (4 * (int64_t)sm_count() + B - 1) / B;
   const int64_t cap = (n + PC_THREADS * 16 - 1) / (PC_THREADS * 16);
   if (nb > cap) nb = cap;
   if (nb > 64) nb = 64;
@@ -388,11 +388,15 @@ __global__ void k_pcg_finish(double* sc, const double* rr_part, const double* rz
     rr += rr_part[b * nblk + i];
     rz += rz_part[b * nblk + i];
   }
-  c[SC_BETA] = rz / c[SC_RZ];
+  c[SC_BETA] = c[SC_RZ] != 0.0 ? rz / c[SC_RZ] : 0.0;
   c[SC_RR] = rr;
   c[SC_RZ] = rz;
   c[SC_ITERS] += 1.0;
-  if (rtol > 0.0 && sqrt(rr) <= rtol * sqrt(c[SC_BB])) c[SC_ACTIVE] = 0.0;
+  // an exact zero residual ends the system at any rtol (beta would be 0/0 next)
+  if (rr == 0.0 || rz == 0.0 || (rtol > 0.0 && sqrt(rr) <= rtol * sqrt(c[SC_BB]))) {
+    c[SC_ACTIVE] = 0.0;
+    c[SC_BETA] = 0.0;
+  }
 }
 
 // Partials of p.q.
@@ -524,7 +528,7 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   PCArgs<T> a = pc_args<T>(m);
   a.c = 0.0;
   prof_begin("pc_setup", (double)N * sizeof(T), st);
-  k_pc_setup<T><<<152, PC_THREADS, (size_t)(nb > 0 ? nb : 1) * sizeof(double), st>>>(
+  k_pc_setup<T><<<sm_count(), PC_THREADS, (size_t)(nb > 0 ? nb : 1) * sizeof(double), st>>>(
       m->w.as<T>(), N, a, dbuf.as<double>() + 1, dbuf.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();
@@ -548,7 +552,7 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   NRE_TRY_CUDA(cudaMemsetAsync(dbuf.p, 0, (size_t)(1 + nb) * sizeof(double), st));
   a.c = m->pc_c;
   prof_begin("pc_setup", (double)N * 2 * sizeof(T), st);
-  k_pc_setup<T><<<152, PC_THREADS, (size_t)nb * sizeof(double), st>>>(m->w.as<T>(), N, a,
+  k_pc_setup<T><<<sm_count(), PC_THREADS, (size_t)nb * sizeof(double), st>>>(m->w.as<T>(), N, a,
                                                                      dbuf.as<double>() + 1, dbuf.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();

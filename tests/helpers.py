@@ -70,3 +70,26 @@ def blocks_rel(got, ref, n_field):
     if ref.shape[0] > n_field:
         e.append(rel_max(got[n_field:], ref[n_field:]))
     return max(e)
+
+
+def icr_fp64_tol(n0, n_levels, rho=0.1):
+    """FP64 parity tolerance of ICR outputs (rel_max), derived from conditioning.
+
+    Both sides assemble R = K_fc K_cc^-1 and L_D = chol(K_ff - R K_cf) in FP64
+    from chart positions and kernel values that may differ in the last bit.  A
+    relative perturbation eps64 of the 9x9 neighbourhood matrix moves the solve
+    by up to n eps64 kappa(K_cc) (n = 9, a backward-stable solver), and each
+    refinement adds its level's error to the output.  Hence
+        tol = max(1e-12, 9 eps64 sum_l max_i kappa(K_cc[l, i])).
+    Returns (tol, [max kappa per level])."""
+    from oracle.icr import ICRChart
+    c = ICRChart(n0=n0, n_levels=n_levels, rho=rho)
+    kap = []
+    for lev in range(n_levels):
+        k = 0.0
+        for i in range(c.sizes[lev]):
+            pc, _ = c.coarse_fine_points(lev, i)
+            k = max(k, float(np.linalg.cond(c.kmat(pc, pc))))
+        kap.append(k)
+    tol = max(1e-12, 9 * np.finfo(np.float64).eps * sum(kap))
+    return tol, kap

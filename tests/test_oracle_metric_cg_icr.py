@@ -229,3 +229,187 @@ def test_icr_metric_spd():
     Mu, Mv = c.metric_apply(u), c.metric_apply(v)
     assert abs(np.dot(Mu, v) - np.dot(u, Mv)) <= 1e-11 * np.linalg.norm(Mu) * np.linalg.norm(v)
     assert np.dot(v, Mv) >= np.dot(v, v)
+
+
+# ---------------------------------------------------------------- ICR gather pins
+#
+# With level 0 drawn exactly (Cov s_0 = K0), one refinement
+#     s_f = R s_nbhd + L_D xi_f,   R = K_fc K_cc^-1,  L_D L_D^T = K_ff - R K_cf
+# reproduces the kernel exactly on every child block and its neighbourhood:
+#     Cov(s_f, s_nbhd) = R K_cc = K_fc,   Cov(s_f, s_f) = R K_cc R^T + D = K_ff.
+# Both sides are computed below from the oracle's dense linear map, the right-hand
+# sides from positions and a Matern-3/2 kernel written out here, and the
+# neighbourhood (clamped radial window, periodic angle) and the child order from
+# their definitions.  A swapped neighbour order, a different clamp or wrap, or a
+# permuted child block breaks an equality by O(1).
+
+
+def _chart_pos(n0, level, i, j):
+    n = n0 * 2 ** level
+    u, v = (i + 0.5) / n, (j + 0.5) / n
+    r = 0.1 * 10.0 ** u            # r_min (r_max / r_min)^u with r_min = 0.1, r_max = 1
+    return np.array([r * np.cos(2 * np.pi * v), r * np.sin(2 * np.pi * v)])
+
+
+def _matern32(pa, pb, rho):
+    d = np.linalg.norm(pa - pb)
+    return (1.0 + np.sqrt(3.0) * d / rho) * np.exp(-np.sqrt(3.0) * d / rho)
+
+
+def _dense_levels(c):
+    """Rows of s_0 and s_1 as linear maps of the latent vector (columns = unit xi)."""
+    n = c.latent_size
+    cols = [c.forward(np.eye(n)[j], return_levels=True) for j in range(n)]
+    L0 = np.stack([col[0].ravel() for col in cols], axis=1)
+    L1 = np.stack([col[1].ravel() for col in cols], axis=1)
+    return L0, L1
+
+
+@pytest.mark.parametrize("n0,rho", [(4, 0.4), (5, 0.25), (6, 0.15), (6, 0.6)])
+def test_icr_one_refinement_reproduces_kernel(n0, rho):
+    c = ICRChart(n0=n0, n_levels=1, rho=rho)
+    L0, L1 = _dense_levels(c)
+    C10 = L1 @ L0.T          # Cov(s_1, s_0)
+    C11 = L1 @ L1.T          # Cov(s_1, s_1)
+    n1 = 2 * n0
+    worst = 0.0
+    for i in range(n0):
+        w = min(max(i - 1, 0), n0 - 3)          # clamped radial window
+        nb = [(w + a, (j_off) % n0) for a in range(3) for j_off in (-1, 0, 1)]
+        for j in range(n0):
+            nbh = [(r, (j + dj) % n0) for (r, dj) in [(w + a, d) for a in range(3) for d in (-1, 0, 1)]]
+            kids = [(2 * i + a, 2 * j + b) for a in range(2) for b in range(2)]
+            for (fi, fj) in kids:
+                pf = _chart_pos(n0, 1, fi, fj)
+                for (ci, cj) in nbh:
+                    got = C10[fi * n1 + fj, ci * n0 + cj]
+                    exp = _matern32(pf, _chart_pos(n0, 0, ci, cj), rho)
+                    worst = max(worst, abs(got - exp))
+                for (gi, gj) in kids:
+                    got = C11[fi * n1 + fj, gi * n1 + gj]
+                    exp = _matern32(pf, _chart_pos(n0, 1, gi, gj), rho)
+                    worst = max(worst, abs(got - exp))
+        del nb
+    assert worst <= 1e-11, worst
+
+
+def test_icr_one_refinement_detects_outside_neighbours():
+    """The identity holds for the 3x3 neighbourhood only: against a coarse pixel
+    two radial rows away from an interior child block the covariance is not the
+    kernel (so the pin above would see a neighbourhood that is too small or
+    shifted)."""
+    n0, rho = 6, 0.4
+    c = ICRChart(n0=n0, n_levels=1, rho=rho)
+    L0, L1 = _dense_levels(c)
+    C10 = L1 @ L0.T
+    i, j = 2, 3                                  # interior: window rows 1..3
+    fi, fj = 2 * i, 2 * j
+    ci, cj = 5, j                                # outside the window
+    got = C10[fi * 2 * n0 + fj, ci * n0 + cj]
+    exp = _matern32(_chart_pos(n0, 1, fi, fj), _chart_pos(n0, 0, ci, cj), rho)
+    assert abs(got - exp) > 1e-6
+
+
+def test_icr_deeper_refinement_conditional_identities():
+    """At level 1 -> 2 (level 1 no longer exactly the kernel) the refinement is
+    still the conditional step: with C = Cov(s_1) and the neighbourhood /
+    children written out here,
+        Cov(s_f, s_nbhd) = R C_nn   and   Cov(s_f) - R C_nn R^T = L_D L_D^T."""
+    c = ICRChart(n0=4, n_levels=2, rho=0.3)
+    n = c.latent_size
+    cols = [c.forward(np.eye(n)[k], return_levels=True) for k in range(n)]
+    L1 = np.stack([col[1].ravel() for col in cols], axis=1)
+    L2 = np.stack([col[2].ravel() for col in cols], axis=1)
+    C11, C21, C22 = L1 @ L1.T, L2 @ L1.T, L2 @ L2.T
+    R, LD = c.matrices(1)
+    nc = 8
+    for i in range(nc):
+        w = min(max(i - 1, 0), nc - 3)
+        for j in (0, 3, nc - 1):
+            nb = [(w + a) * nc + (j + d) % nc for a in range(3) for d in (-1, 0, 1)]
+            kids = [(2 * i + a) * 2 * nc + 2 * j + b for a in range(2) for b in range(2)]
+            Cnn = C11[np.ix_(nb, nb)]
+            np.testing.assert_allclose(C21[np.ix_(kids, nb)], R[i] @ Cnn, atol=1e-12)
+            resid = C22[np.ix_(kids, kids)] - R[i] @ Cnn @ R[i].T
+            np.testing.assert_allclose(resid, LD[i] @ LD[i].T, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Fisher weight pins
+#
+# The Fisher metric of a likelihood p(d | cf) in the coordinate cf is
+#     w(cf) = E_d[ (d/dcf log p(d | cf))^2 ]  =  E_d[ -d^2/dcf^2 log p(d | cf) ].
+# Below both expectations are taken from the densities themselves: the Poisson
+# one by summing over its probability mass function, the Gaussian one by
+# Gauss-Hermite quadrature of a central-difference second derivative of the
+# log-density.
+
+
+def _poisson_logpmf(d, lam):
+    from scipy.special import gammaln
+    return d * np.log(lam) - lam - gammaln(d + 1.0)
+
+
+@pytest.mark.parametrize("cf", [-2.0, -0.3, 0.0, 0.7, 1.5])
+def test_poisson_weight_is_fisher_information(cf):
+    scale = 10.0
+    lam = scale * np.exp(cf)
+    d = np.arange(0, int(lam + 40 * np.sqrt(lam) + 60), dtype=np.float64)
+    p = np.exp(_poisson_logpmf(d, lam))
+    assert abs(p.sum() - 1.0) < 1e-13
+    h = 1e-4
+    score = (_poisson_logpmf(d, scale * np.exp(cf + h)) - _poisson_logpmf(d, scale * np.exp(cf - h))) / (2 * h)
+    fisher = float(np.sum(p * score * score))
+    w = poisson_weight(np.array([cf]), scale)[0]
+    assert abs(w - fisher) <= 1e-7 * fisher
+    assert abs(w - 1.0 / lam) > 0.5 * fisher or lam < 1.5    # not the inverse rate
+
+
+@pytest.mark.parametrize("response", ["exp", "identity"])
+@pytest.mark.parametrize("cf", [-1.0, 0.2, 1.3])
+def test_gaussian_weight_is_fisher_information(response, cf):
+    sigma = 0.37
+    resp = np.exp if response == "exp" else (lambda z: z)
+
+    def logp(d, c):
+        return -0.5 * (d - resp(c)) ** 2 / sigma ** 2 - np.log(sigma * np.sqrt(2 * np.pi))
+
+    z, wq = np.polynomial.hermite_e.hermegauss(40)          # nodes for N(0, 1)
+    wq = wq / wq.sum()
+    d = resp(cf) + sigma * z
+    h = 1e-3
+    hess = (logp(d, cf + h) - 2 * logp(d, cf) + logp(d, cf - h)) / (h * h)
+    fisher = -float(np.sum(wq * hess))
+    w = gaussian_weight(np.array([cf]), sigma, response=response)[0]
+    assert abs(w - fisher) <= 1e-5 * fisher
+    # mask: an unobserved pixel carries no information
+    assert gaussian_weight(np.array([cf]), sigma, mask=np.array([0.0]), response=response)[0] == 0.0
+
+
+@pytest.mark.parametrize("n0,levels", [(8, 3), (4, 4)])
+def test_icr_fp64_tolerance_covers_last_bit_inputs(n0, levels):
+    """The FP64 ICR parity tolerance (helpers.icr_fp64_tol, from kappa(K_cc))
+    bounds how far the oracle itself moves when every chart coordinate changes
+    in its last bit, as it may between two independent FP64 assemblies."""
+    from helpers import icr_fp64_tol
+    tol, _ = icr_fp64_tol(n0, levels)
+    eps = np.finfo(np.float64).eps
+
+    class Perturbed(ICRChart):
+        def __init__(self, seed, **kw):
+            super().__init__(**kw)
+            self._g = np.random.default_rng(seed)
+
+        def position(self, level, i, j):
+            p = super().position(level, i, j)
+            return p * (1 + eps * self._g.choice([-1.0, 0.0, 1.0], size=p.shape))
+
+    base = ICRChart(n0=n0, n_levels=levels)
+    g = np.random.default_rng(21)
+    xi = g.standard_normal(base.latent_size)
+    s0 = base.forward(xi).ravel()
+    ct = g.standard_normal(s0.shape)
+    v0 = base.vjp(ct)
+    for seed in range(3):
+        pc = Perturbed(seed, n0=n0, n_levels=levels)
+        assert np.abs(pc.forward(xi).ravel() - s0).max() <= tol * np.abs(s0).max()
+        assert np.abs(pc.vjp(ct) - v0).max() <= tol * np.abs(v0).max()

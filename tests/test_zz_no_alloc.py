@@ -4,7 +4,9 @@ synchronise the device or because their runtime owns the memory budget).
 
 It must give the same result as cf_forward (the FP32 / FP64 tolerances of the
 other GPU tests) on two calls in a row, since every call reuses the same fixed
-scratch array, and reject a batch that needs more than that array holds.
+scratch array, leave the library's and torch's device-memory counts unchanged
+on a plan whose workspaces were never grown, and reject a batch that needs
+more than that array holds.
 This file is collected last, so a run that stops at the first failure has run
 every other test before it."""
 import ctypes as C
@@ -23,6 +25,12 @@ def _lib():
     return L, L.load()
 
 
+def _device_bytes(lib):
+    v = C.c_int64(-1)
+    assert lib.nre_device_bytes(C.byref(v)) == 0
+    return v.value
+
+
 @pytest.mark.parametrize("shape,dtype,tol", [((64, 128), torch.float32, 1e-5),
                                              ((16, 32, 64), torch.float32, 1e-5),
                                              ((256,), torch.float64, 1e-12)])
@@ -34,12 +42,20 @@ def test_noalloc_matches_cf_forward(shape, dtype, tol):
     B = 3
     xi = plan.pad(torch.randn(B, plan.latent_size, dtype=dtype, device="cuda:0", generator=g))
     ref = plan.forward(xi)
+    # a second plan that has never run cf_forward: its workspaces are empty, so
+    # any allocation inside the call would show in the library's device bytes
+    fresh = nre.CorrelatedField(shape, amplitude="power", prior=dict(n_bins=64), dtype=dtype)
     st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):
-        out = torch.full_like(ref, float("nan"))
-        rc = lib.cf_forward_noalloc(plan.handle, C.c_void_p(xi.data_ptr()), C.c_void_p(out.data_ptr()), B, st)
+    outs = [torch.full_like(ref, float("nan")) for _ in range(2)]
+    torch.cuda.synchronize()
+    for out in outs:
+        lib_before = _device_bytes(lib)
+        torch_before = torch.cuda.memory_allocated()
+        rc = lib.cf_forward_noalloc(fresh.handle, C.c_void_p(xi.data_ptr()), C.c_void_p(out.data_ptr()), B, st)
         assert rc == L.NRE_OK, lib.nre_last_error()
         torch.cuda.synchronize()
+        assert _device_bytes(lib) == lib_before, "cf_forward_noalloc allocated device memory"
+        assert torch.cuda.memory_allocated() == torch_before
         err = (out - ref).abs().max().item() / ref.abs().max().item()
         assert err <= tol, err
 
