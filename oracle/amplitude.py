@@ -26,6 +26,21 @@ reading used throughout this project, written step by step in float64:
 
 Hyper-latent layout h = [xi_fluct, xi_slope, xi_flex, xi_asp,
 xi1_1..xi1_{B-1}, xi2_1..xi2_{B-1}], of size 4 + 2 (B - 1).
+
+The parametric alternative, the Matern amplitude of the same section (the
+paper names it beside the non-parametric kernel and defers its form to its
+citations), is read here as a Matern-type power spectrum on the same log-|k|
+bins, evaluated at the bin-centre wavenumbers k_b = exp(l_b):
+
+1. theta_scale and theta_cutoff log-normal, theta_slope normal, from
+   standard-normal excitations as in step 1 above;
+2. a_b = (1 + (k_b / theta_cutoff)^2)^(theta_slope / 4), so that the power
+   a_b^2 falls off with log-log slope theta_slope far above the cutoff and is
+   flat below it;
+3. A_b = theta_scale a_b / sqrt(sum_b n_b a_b^2) (pointwise field variance
+   without the zero mode theta_scale^2).
+
+Hyper-latent layout h = [xi_scale, xi_cutoff, xi_slope].
 """
 import numpy as np
 
@@ -46,6 +61,24 @@ class AmpPrior:
     @property
     def n_hyper(self):
         return 4 + 2 * (self.n_bins - 1)
+
+
+class MaternPrior:
+    """Prior (mean, std) pairs of the parametric Matern amplitude and of the
+    offset: scale and cutoff log-normal, loglogslope normal."""
+
+    def __init__(self, scale=(1.0, 0.5), cutoff=(8.0, 2.0), loglogslope=(-4.0, 0.5),
+                 offset_mean=0.0, offset_std=1.0, n_bins=256):
+        self.scale = tuple(map(float, scale))
+        self.cutoff = tuple(map(float, cutoff))
+        self.loglogslope = tuple(map(float, loglogslope))
+        self.offset_mean = float(offset_mean)
+        self.offset_std = float(offset_std)
+        self.n_bins = int(n_bins)
+
+    @property
+    def n_hyper(self):
+        return 3
 
 
 def lognormal_params(mean, std):
@@ -76,6 +109,8 @@ def _thetas(h, prior):
 
 def forward(h, prior, bins):
     """Amplitude per bin A_b (float64, length n_bins) and the intermediates."""
+    if isinstance(prior, MaternPrior):
+        return matern_forward(h, prior, bins)
     nb = prior.n_bins
     (th_fl, th_sl, th_fx, th_as), _, xi1, xi2 = _thetas(h, prior)
     l = bins.centres
@@ -101,6 +136,8 @@ def amplitude(h, prior, bins):
 
 def jvp(h, dh, prior, bins):
     """Forward-mode derivative dA_b of the amplitude in direction ``dh``."""
+    if isinstance(prior, MaternPrior):
+        return matern_jvp(h, dh, prior, bins)
     nb = prior.n_bins
     (th_fl, th_sl, th_fx, th_as), (s_fl, s_sl, s_fx, s_as), xi1, xi2 = _thetas(h, prior)
     d_fl, d_sl, d_fx, d_as, dxi1, dxi2 = _split(dh, nb)
@@ -128,6 +165,8 @@ def jvp(h, dh, prior, bins):
 
 def vjp(h, gA, prior, bins):
     """Reverse-mode derivative: the hyper-latent cotangent for cotangent ``gA``."""
+    if isinstance(prior, MaternPrior):
+        return matern_vjp(h, gA, prior, bins)
     nb = prior.n_bins
     (th_fl, th_sl, th_fx, th_as), (s_fl, s_sl, s_fx, s_as), xi1, xi2 = _thetas(h, prior)
     gA = np.asarray(gA, dtype=np.float64)
@@ -177,3 +216,61 @@ def vjp(h, gA, prior, bins):
     out[4:4 + nb - 1] = g_xi1
     out[4 + nb - 1:] = g_xi2
     return out
+
+
+# ---------------------------------------------------------------- Matern
+
+
+def _matern_thetas(h, prior):
+    h = np.asarray(h, dtype=np.float64)
+    assert h.shape == (3,)
+    mu_sc, s_sc = lognormal_params(*prior.scale)
+    mu_ct, s_ct = lognormal_params(*prior.cutoff)
+    th_sc = np.exp(mu_sc + s_sc * h[0])
+    th_ct = np.exp(mu_ct + s_ct * h[1])
+    th_al = prior.loglogslope[0] + prior.loglogslope[1] * h[2]
+    return (th_sc, th_ct, th_al), (s_sc, s_ct, prior.loglogslope[1])
+
+
+def matern_forward(h, prior, bins):
+    """Matern amplitude per bin and its intermediates (see the module text)."""
+    (th_sc, th_ct, th_al), _ = _matern_thetas(h, prior)
+    k = np.exp(bins.centres)
+    L = np.log1p((k / th_ct) ** 2)          # ln(1 + (k / cutoff)^2)
+    a = np.exp(th_al * L / 4.0)
+    S = np.sum(bins.counts * a * a)
+    A = th_sc * a / np.sqrt(S)
+    return dict(A=A, a=a, S=S, L=L, k=k, theta=(th_sc, th_ct, th_al))
+
+
+def matern_jvp(h, dh, prior, bins):
+    (th_sc, th_ct, th_al), (s_sc, s_ct, s_al) = _matern_thetas(h, prior)
+    dh = np.asarray(dh, dtype=np.float64)
+    f = matern_forward(h, prior, bins)
+    a, S, L, k = f["a"], f["S"], f["L"], f["k"]
+    dsc = th_sc * s_sc * dh[0]
+    dct = th_ct * s_ct * dh[1]
+    dal = s_al * dh[2]
+    r = (k / th_ct) ** 2
+    # d ln a = dal L / 4 + (th_al / 4) d ln(1 + r),  d ln(1 + r) = -2 r / (1 + r) dct / th_ct
+    dlna = dal * L / 4.0 - (th_al / 2.0) * r / (1.0 + r) * dct / th_ct
+    da = a * dlna
+    dS = np.sum(bins.counts * 2.0 * a * da)
+    rs = 1.0 / np.sqrt(S)
+    return dsc * a * rs + th_sc * da * rs - th_sc * a * dS * rs ** 3 / 2.0
+
+
+def matern_vjp(h, gA, prior, bins):
+    (th_sc, th_ct, th_al), (s_sc, s_ct, s_al) = _matern_thetas(h, prior)
+    gA = np.asarray(gA, dtype=np.float64)
+    f = matern_forward(h, prior, bins)
+    a, S, L, k = f["a"], f["S"], f["L"], f["k"]
+    rs = 1.0 / np.sqrt(S)
+    ga_dot = np.sum(gA * a)
+    g_sc = ga_dot * rs
+    g_a = th_sc * rs * gA - th_sc * rs ** 3 * bins.counts * a * ga_dot
+    g_lna = g_a * a
+    r = (k / th_ct) ** 2
+    g_al = np.sum(g_lna * L / 4.0)
+    g_ct = np.sum(g_lna * (-(th_al / 2.0) * r / (1.0 + r) / th_ct))
+    return np.array([g_sc * th_sc * s_sc, g_ct * th_ct * s_ct, g_al * s_al])

@@ -23,6 +23,11 @@ import numpy as np
 AMP_PRIOR = dict(fluct=(1.0, 0.5), slope=(-3.0, 0.5), flex=(1.0, 0.5),
                  asp=(0.1, 0.05), offset_mean=0.0, offset_std=1.0, n_bins=256)
 
+# Prior (mean, std) pairs of the parametric Matern amplitude (scale and cutoff
+# log-normal, the power spectrum's log-log slope normal); offset ~ N(0, 1).
+MATERN_PRIOR = dict(scale=(1.0, 0.5), cutoff=(8.0, 2.0), loglogslope=(-4.0, 0.5),
+                    offset_mean=0.0, offset_std=1.0, n_bins=256)
+
 # Fixed 1-D spectrum (1 + (k/8)^2)^-1.5, unit variance, zero offset.
 FIXED_1D = dict(k0=8.0, gamma=1.5, variance=1.0, zero_mode=0.0)
 

@@ -163,3 +163,74 @@ def test_cf_offset_mode():
     xi = np.zeros(m.latent_size)
     xi[0] = 1.5
     np.testing.assert_allclose(m.forward(xi), 2.0 + 0.3 * 1.5, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- Matern amplitude
+#
+# Pinned by: central differences of the JVP, the JVP / VJP adjoint identity,
+# the normalisation invariant, a flat spectrum at zero slope and far below the
+# cutoff, and the power spectrum's log-log slope far above the cutoff (which
+# fixes the exponent and its sign).
+
+MPRIOR = amp.MaternPrior(n_bins=12)
+
+
+def test_matern_jvp_central_differences_and_adjoint():
+    bins = _bins()
+    g = np.random.default_rng(21)
+    h, dh = g.standard_normal((2, 3))
+    eps = 1e-6
+    fd = (amp.amplitude(h + eps * dh, MPRIOR, bins) - amp.amplitude(h - eps * dh, MPRIOR, bins)) / (2 * eps)
+    an = amp.jvp(h, dh, MPRIOR, bins)
+    assert np.max(np.abs(fd - an)) <= 1e-7 * np.max(np.abs(an))
+    gA = g.standard_normal(MPRIOR.n_bins)
+    lhs = np.dot(an, gA)
+    rhs = np.dot(dh, amp.vjp(h, gA, MPRIOR, bins))
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
+
+
+def test_matern_normalisation_invariant():
+    bins = _bins()
+    h = np.random.default_rng(22).standard_normal(3)
+    f = amp.forward(h, MPRIOR, bins)
+    th_sc = f["theta"][0]
+    assert abs(np.sum(bins.counts * f["A"] ** 2) - th_sc ** 2) <= 1e-13 * th_sc ** 2
+
+
+def test_matern_flat_limits():
+    """Zero slope, or a cutoff far above every |k|, gives a flat spectrum
+    A_b = theta_scale / sqrt(sum n_b)."""
+    bins = _bins()
+    mean, std = MPRIOR.loglogslope
+    for h in (np.array([0.3, -0.2, -mean / std]), np.array([0.3, 90.0, 0.5])):
+        f = amp.forward(h, MPRIOR, bins)
+        flat = f["theta"][0] / np.sqrt(bins.counts.sum())
+        np.testing.assert_allclose(f["A"], flat, rtol=1e-9)
+
+
+def test_matern_loglog_slope_above_cutoff():
+    """Far above the cutoff the power A^2 falls as |k|^slope."""
+    bins = _bins()
+    h = np.array([0.0, -60.0, 0.8])       # cutoff ~ 8 exp(-60 s_ln): far below every |k|
+    f = amp.forward(h, MPRIOR, bins)
+    slope = MPRIOR.loglogslope[0] + MPRIOR.loglogslope[1] * 0.8
+    lp = np.log(f["A"] ** 2)
+    d = np.diff(lp) / np.diff(bins.centres)
+    np.testing.assert_allclose(d, slope, rtol=1e-9)
+
+
+def test_cf_matern_model_jvp_fd_and_adjoint():
+    shape = (8, 4)
+    sp = tuple(1.0 / s for s in shape)
+    m = CFModel(shape, sp, prior=amp.MaternPrior(n_bins=6))
+    assert m.latent_size == 32 + 3
+    g = np.random.default_rng(23)
+    xp, v = g.standard_normal((2, m.latent_size))
+    ct = g.standard_normal(shape)
+    eps = 1e-6
+    fd = (m.forward(xp + eps * v) - m.forward(xp - eps * v)) / (2 * eps)
+    jv = m.jvp(xp, v)
+    assert np.max(np.abs(fd - jv)) <= 1e-7 * np.max(np.abs(jv))
+    lhs = np.sum(jv * ct)
+    rhs = np.dot(v, m.vjp(xp, ct))
+    assert abs(lhs - rhs) <= 1e-13 * np.sqrt(np.sum(jv ** 2) * np.sum(ct ** 2))
