@@ -30,6 +30,9 @@ of it listed per function:
                    (Sec. "Variational Inference", ``draw_linear_kwargs``).
 * ``icr``        - iterative charted refinement on a 2-D log-radial chart
                    (Sec. "Gaussian Processes", ICR paragraph).
+* ``kl``         - the KL energy of MGVI for fixed residual samples, its
+                   gradient, the sample-averaged metric and Newton-CG
+                   (Sec. "Variational Inference", the minimiser "M").
 
 It shares no code with ``paper_2402_16683_gb300`` and imports nothing from it.
 """
