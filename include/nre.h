@@ -77,14 +77,24 @@ int nre_version(void);
  *                        integrated Wiener process on n_bins log-|k| bins,
  *                        normalised to total variance theta_fluct^2.  Computed
  *                        in FP64 for both dtypes.
+ *  NRE_AMP_MATERN_MODEL  the parametric Matern kernel the same section names
+ *                        beside the non-parametric one: on the same n_bins
+ *                        log-|k| bins, a_b = (1 + (k_b / theta_cutoff)^2)^
+ *                        (theta_slope / 4) at the bin-centre wavenumbers
+ *                        k_b = exp(l_b), A_b = theta_scale a_b /
+ *                        sqrt(sum_b n_b a_b^2); theta_scale, theta_cutoff
+ *                        log-normal with the given (mean, std) of the variable,
+ *                        theta_slope (the power spectrum's log-log slope above
+ *                        the cutoff) normal; A_full[0] = offset_std.  FP64.
  *
  * Latent layout of one sample (float/double):
  *   [0, N)                         xi_field, harmonic C order
- *   [N, N + n_hyper)               POWER_MODEL only: xi_fluct, xi_slope,
- *                                  xi_flex, xi_asp, xi1[n_bins-1], xi2[n_bins-1]
+ *   [N, N + n_hyper)               POWER_MODEL: xi_fluct, xi_slope,
+ *                                  xi_flex, xi_asp, xi1[n_bins-1], xi2[n_bins-1];
+ *                                  MATERN_MODEL: xi_scale, xi_cutoff, xi_slope
  *   [latent_size, stride)          padding (stride is a multiple of 64)
  */
-enum { NRE_AMP_ARRAY = 0, NRE_AMP_MATERN_FIXED = 1, NRE_AMP_POWER_MODEL = 2 };
+enum { NRE_AMP_ARRAY = 0, NRE_AMP_MATERN_FIXED = 1, NRE_AMP_POWER_MODEL = 2, NRE_AMP_MATERN_MODEL = 3 };
 
 typedef struct {
   int kind;                 /* NRE_AMP_*                                      */
@@ -93,8 +103,10 @@ typedef struct {
   double fluct_mean, fluct_std, slope_mean, slope_std;   /* POWER_MODEL       */
   double flex_mean, flex_std, asp_mean, asp_std;         /* POWER_MODEL       */
   double offset_mean;       /* added to cf in position space (all kinds)      */
-  double offset_std;        /* POWER_MODEL: A_full[0]                          */
-  int n_bins;               /* POWER_MODEL: number of log-|k| bins (2..1024)  */
+  double offset_std;        /* POWER_ / MATERN_MODEL: A_full[0]                */
+  int n_bins;               /* POWER_ / MATERN_MODEL: log-|k| bins (2..1024)  */
+  double scale_mean, scale_std, cutoff_mean, cutoff_std;  /* MATERN_MODEL      */
+  double lls_mean, lls_std; /* MATERN_MODEL: log-log slope of the power        */
 } nre_cf_amp_params;
 
 typedef struct nre_cf_plan nre_cf_plan;
@@ -241,6 +253,28 @@ int mgvi_rhs(nre_metric *m, const void *xi_prime, const void *eta, void *b,
 int cg_solve(nre_metric *m, const void *b, void *x, int batch, double rtol,
              int maxiter, int *iters_out, double *relres_out,
              nre_stream_t stream);
+
+/* Sec. "Variational Inference" (the linear draw's CG tolerance), solved to a
+ * TRUE relative residual: x (FP64, [batch][stride]) with
+ *     ||b - M_hi x|| <= rtol ||b||  for every system,
+ * by residual correction: x_0 = 0; r_k = b - M_hi x_k in FP64; the inner CG of
+ * cg_solve on m_lo solves M_lo d = r_k to inner_rtol (recursive residual,
+ * inner_maxiter iterations at most, m_lo's preconditioner); x_{k+1} = x_k + d.
+ * m_hi is an FP64 metric and m_lo a metric of either dtype, both created at the
+ * same expansion point for the same model (same latent layout); the product of
+ * m_hi decides the residual, so an FP32 m_lo reaches residuals below its own
+ * operator error.  b: FP64 [batch][stride] (device); x: FP64 output.  At most
+ * max_outer correction passes (each one FP64 product; the residual of
+ * x_0 = 0 is b itself).  Systems that reach rtol are frozen.  HOST outputs
+ * (may be NULL): iters_out[batch] = inner CG iterations summed over the
+ * passes, relres_out[batch] = final true relative residuals, *outer_out =
+ * passes taken.  Synchronises `stream` once per pass.  Returns NRE_ENOTCONV if
+ * some system is above rtol after max_outer passes; NRE_EINVAL for a non-FP64
+ * m_hi, different layouts, rtol <= 0 or inner_rtol outside (0, 1). */
+int cg_solve_refined(nre_metric *m_lo, nre_metric *m_hi, const void *b, void *x,
+                     int batch, double rtol, int max_outer, double inner_rtol,
+                     int inner_maxiter, int *iters_out, double *relres_out,
+                     int *outer_out, nre_stream_t stream);
 
 /* ================================================================ tracing
  * Launch accounting for measurement tools.  nre_launch_count() counts every

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libnre.so")
 
 NRE_OK, NRE_EINVAL, NRE_ENOMEM, NRE_ECUDA, NRE_ENOTCONV, NRE_ETIMEDOUT, NRE_EBUSY, NRE_EAGAIN = range(8)
 NRE_F32, NRE_F64 = 0, 1
-NRE_AMP_ARRAY, NRE_AMP_MATERN_FIXED, NRE_AMP_POWER_MODEL = 0, 1, 2
+NRE_AMP_ARRAY, NRE_AMP_MATERN_FIXED, NRE_AMP_POWER_MODEL, NRE_AMP_MATERN_MODEL = 0, 1, 2, 3
 NRE_LIK_GAUSS, NRE_LIK_POISSON = 0, 1
 NRE_RESP_EXP, NRE_RESP_IDENTITY = 0, 1
 NRE_MODEL_CF, NRE_MODEL_ICR = 0, 1
@@ -36,7 +36,10 @@ class CFAmpParams(C.Structure):
                 ("flex_mean", C.c_double), ("flex_std", C.c_double),
                 ("asp_mean", C.c_double), ("asp_std", C.c_double),
                 ("offset_mean", C.c_double), ("offset_std", C.c_double),
-                ("n_bins", C.c_int)]
+                ("n_bins", C.c_int),
+                ("scale_mean", C.c_double), ("scale_std", C.c_double),
+                ("cutoff_mean", C.c_double), ("cutoff_std", C.c_double),
+                ("lls_mean", C.c_double), ("lls_std", C.c_double)]
 
 
 class ICRChartParams(C.Structure):
@@ -103,6 +106,8 @@ SIGNATURES = {
     "cg_solve": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                  C.POINTER(C.c_double), _P],
     "metric_set_precond": [_P, C.c_int, _P],
+    "cg_solve_refined": [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
+                         C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), _P],
     "nre_device_bytes": [_I64P],
     "serve_create": [C.POINTER(_P), C.POINTER(ServeCfg)],
     "serve_submit": [_P, C.POINTER(ServeReq), C.POINTER(C.c_uint64)],

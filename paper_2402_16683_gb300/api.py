@@ -72,6 +72,16 @@ def _amp_params(amplitude="power", prior=None, matern=None, offset_mean=0.0):
         a.asp_mean, a.asp_std = pr["asp"]
         a.offset_mean, a.offset_std = pr["offset_mean"], pr["offset_std"]
         a.n_bins = pr["n_bins"]
+    elif amplitude == "matern_model":
+        pr = dict(scale=(1.0, 0.5), cutoff=(8.0, 2.0), loglogslope=(-4.0, 0.5),
+                  offset_mean=0.0, offset_std=1.0, n_bins=256)
+        pr.update(prior or {})
+        a.kind = L.NRE_AMP_MATERN_MODEL
+        a.scale_mean, a.scale_std = pr["scale"]
+        a.cutoff_mean, a.cutoff_std = pr["cutoff"]
+        a.lls_mean, a.lls_std = pr["loglogslope"]
+        a.offset_mean, a.offset_std = pr["offset_mean"], pr["offset_std"]
+        a.n_bins = pr["n_bins"]
     else:
         raise ValueError(f"unknown amplitude {amplitude!r}")
     return a, arr
@@ -82,6 +92,8 @@ class CorrelatedField:
 
     amplitude: "power" (non-parametric power-spectrum model, ``prior`` dict with
     fluct / slope / flex / asp (mean, std) pairs, offset_mean, offset_std,
+    n_bins), "matern_model" (parametric Matern spectrum, ``prior`` dict with
+    scale / cutoff / loglogslope (mean, std) pairs, offset_mean, offset_std,
     n_bins), "matern" (fixed spectrum, ``matern`` dict k0 / gamma / variance /
     zero_mode) or a per-pixel numpy array (A_full, harmonic C order).
     """
@@ -304,6 +316,25 @@ class Metric:
         if st != L.NRE_OK and (st != L.NRE_ENOTCONV or raise_on_notconv):
             check(st)
         return x, list(it), list(rr), st
+
+    def cg_refined(self, hi, b, rtol=1e-5, max_outer=6, inner_rtol=1e-3, inner_maxiter=1000, x=None,
+                   raise_on_notconv=False):
+        """cg_solve_refined: solve to a true relative residual rtol of the FP64
+        metric ``hi`` (same model and expansion point), this metric running the
+        inner CG.  b, x: FP64 [B, stride].  Returns (x, inner iterations[B],
+        true relres[B], passes, status)."""
+        B = b.shape[0]
+        _need(b, torch.float64, (B, self.model.stride), "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        it = (C.c_int * B)()
+        rr = (C.c_double * B)()
+        outer = C.c_int(0)
+        st = L.load().cg_solve_refined(self.handle, hi.handle, _ptr(b), _ptr(x), B, float(rtol), int(max_outer),
+                                       float(inner_rtol), int(inner_maxiter), it, rr, C.byref(outer), _stream())
+        if st != L.NRE_OK and (st != L.NRE_ENOTCONV or raise_on_notconv):
+            check(st)
+        return x, list(it), list(rr), outer.value, st
 
 
 def _host_ptr(a, dtype, n, name):

@@ -12,6 +12,13 @@
 //   y_i = y_{i-1} + D_i (x_{i-1} + x_i)/2 + theta_flex sqrt(D_i^3/12 + theta_asp D_i) xi2_i,
 //   tau_i = theta_slope (l_i - l_0) + y_i,  a_i = exp(tau_i / 2),
 //   A_i = theta_fl a_i / sqrt(sum_b n_b a_b^2)   (n_b: non-zero modes in bin b).
+//
+// The parametric Matern kernel the same section names beside it, on the same
+// bins at the bin-centre wavenumbers k_i = exp(l_i) (reading of this library):
+//   theta_scale, theta_cutoff log-normal, theta_slope normal;
+//   a_i = (1 + (k_i / theta_cutoff)^2)^(theta_slope / 4),
+//   A_i = theta_scale a_i / sqrt(sum_b n_b a_b^2).
+// Its JVP and VJP are per-bin maps plus one block reduction each.
 #include "cf_internal.cuh"
 
 namespace nre {
@@ -232,6 +239,98 @@ __global__ void k_amp_vjp(AmpPrior pr, const double* state, int64_t ss, const do
   }
 }
 
+// ---------------------------------------------------------------- Matern
+// State of a sample (amp_state_size layout): header theta_scale (AS_THFL),
+// theta_slope (AS_THSL), theta_cutoff (AS_THFX), S; per bin a_i (as_a),
+// L_i = ln(1 + r_i) (as_c), A_i (as_A), r_i / (1 + r_i) (as_xi1) with
+// r_i = (k_i / theta_cutoff)^2.
+template <typename T>
+__global__ void k_amp_forward_matern(AmpPrior pr, const T* h, int64_t hs, double* state) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const T* hb = h + b * hs;
+  double* st = state + (int64_t)b * amp_state_size(nb);
+  const double th_sc = exp(pr.mu_sc + pr.s_sc * double(hb[0]));
+  const double th_ct = exp(pr.mu_ct + pr.s_ct * double(hb[1]));
+  const double th_al = pr.al_m + pr.al_s * double(hb[2]);
+  const bool act = i < nb;
+  const double k = act ? exp(pr.centres[i]) : 0.0;
+  const double r = (k / th_ct) * (k / th_ct);
+  const double L = log1p(r);
+  const double a = act ? exp(th_al * L / 4.0) : 0.0;
+  const double S = block_sum(act ? pr.counts[i] * a * a : 0.0, red);
+  if (act) {
+    st[as_a(nb) + i] = a;
+    st[as_c(nb) + i] = L;
+    st[as_A(nb) + i] = th_sc * a / sqrt(S);
+    st[as_xi1(nb) + i] = r / (1.0 + r);
+    st[as_xi2(nb) + i] = 0.0;
+  }
+  if (i == 0) {
+    st[AS_THFL] = th_sc;
+    st[AS_THSL] = th_al;
+    st[AS_THFX] = th_ct;
+    st[AS_THAS] = 0.0;
+    st[AS_S] = S;
+  }
+}
+
+// dA_i: d ln a_i = d theta_slope L_i / 4 - (theta_slope / 2) q_i d theta_cutoff / theta_cutoff
+// (q_i = r_i / (1 + r_i)), then the normalisation as in the power model.
+template <typename T>
+__global__ void k_amp_jvp_matern(AmpPrior pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
+                                 double* dA) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const double* st = state + b * ss;
+  const T* g = dh + b * dhs;
+  const double th_sc = st[AS_THFL], th_al = st[AS_THSL], th_ct = st[AS_THFX], S = st[AS_S];
+  const double dsc = th_sc * pr.s_sc * double(g[0]);
+  const double dct = th_ct * pr.s_ct * double(g[1]);
+  const double dal = pr.al_s * double(g[2]);
+  const bool act = i < nb;
+  const double a = act ? st[as_a(nb) + i] : 0.0;
+  const double L = act ? st[as_c(nb) + i] : 0.0;
+  const double q = act ? st[as_xi1(nb) + i] : 0.0;
+  const double da = a * (dal * L / 4.0 - (th_al / 2.0) * q * dct / th_ct);
+  const double dS = block_sum(act ? pr.counts[i] * 2.0 * a * da : 0.0, red);
+  const double rs = 1.0 / sqrt(S);
+  if (act) dA[(int64_t)b * nb + i] = dsc * a * rs + th_sc * da * rs - th_sc * a * dS * rs * rs * rs / 2.0;
+}
+
+template <typename T>
+__global__ void k_amp_vjp_matern(AmpPrior pr, const double* state, int64_t ss, const double* partials,
+                                 int nparts, const T* base, int64_t bhs, T* out, int64_t ohs, double* dot) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, i = threadIdx.x, nb = pr.nb;
+  const double* st = state + b * ss;
+  const bool act = i < nb;
+  const double gA = act ? sum_strided(partials + (int64_t)b * nparts * nb + i, nparts, nb) : 0.0;
+  const double th_sc = st[AS_THFL], th_al = st[AS_THSL], th_ct = st[AS_THFX], S = st[AS_S];
+  const double rs = 1.0 / sqrt(S);
+  const double a = act ? st[as_a(nb) + i] : 0.0;
+  const double L = act ? st[as_c(nb) + i] : 0.0;
+  const double q = act ? st[as_xi1(nb) + i] : 0.0;
+  const double n = act ? pr.counts[i] : 0.0;
+  const double ga_dot = block_sum(gA * a, red);
+  const double g_a = th_sc * rs * gA - th_sc * rs * rs * rs * n * a * ga_dot;
+  const double g_lna = g_a * a;
+  const double g_al = block_sum(g_lna * L / 4.0, red);
+  const double g_ct = block_sum(g_lna * (-(th_al / 2.0) * q / th_ct), red);
+  if (i == 0) {
+    T* o = out + b * ohs;
+    const T* bb = base ? base + b * bhs : nullptr;
+    const double g3[3] = {ga_dot * rs * th_sc * pr.s_sc, g_ct * th_ct * pr.s_ct, g_al * pr.al_s};
+    double dsum = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      const T oj = T((bb ? double(bb[j]) : 0.0) + g3[j]);
+      o[j] = oj;
+      if (bb) dsum += double(bb[j] * oj);
+    }
+    if (dot != nullptr) dot[(int64_t)b * kDotStride + kDotHyper] = dsum;
+  }
+}
+
 // Linearised amplitude model: the Jacobian at the expansion point,
 // Jt[h][i] = dA_i / dh (FP64, from the JVP along the unit vectors, so the
 // cumulative integration stays FP64), stored in FP32 both ways for the FP32
@@ -363,6 +462,13 @@ int amp_threads(int nb) { return (nb + 31) / 32 * 32; }
 
 AmpPrior amp_prior_of(const nre_cf_plan* p) {
   AmpPrior a;
+  a.kind = p->amp_kind;
+  a.mu_sc = p->mu_sc;
+  a.s_sc = p->s_sc;
+  a.mu_ct = p->mu_ct;
+  a.s_ct = p->s_ct;
+  a.al_m = p->al_m;
+  a.al_s = p->al_s;
   a.mu_fl = p->mu_fl;
   a.s_fl = p->s_fl;
   a.mu_fx = p->mu_fx;
@@ -380,7 +486,8 @@ AmpPrior amp_prior_of(const nre_cf_plan* p) {
 template <typename T>
 int amp_forward(const AmpPrior& pr, const T* h, int64_t hs, double* state, int B, cudaStream_t st) {
   prof_begin("amp_forward", (double)B * pr.nb * (2 * sizeof(T) + 5 * 8), st);
-  k_amp_forward<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, h, hs, state);
+  if (pr.kind == NRE_AMP_MATERN_MODEL) k_amp_forward_matern<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, h, hs, state);
+  else k_amp_forward<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, h, hs, state);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -390,7 +497,8 @@ template <typename T>
 int amp_jvp(const AmpPrior& pr, const double* state, int64_t ss, const T* dh, int64_t dhs,
             double* dA, int B, cudaStream_t st) {
   prof_begin("amp_jvp", (double)B * pr.nb * (2 * sizeof(T) + 8) + (ss ? B : 1) * pr.nb * 40.0, st);
-  k_amp_jvp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, dh, dhs, dA);
+  if (pr.kind == NRE_AMP_MATERN_MODEL) k_amp_jvp_matern<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, dh, dhs, dA);
+  else k_amp_jvp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, dh, dhs, dA);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -402,8 +510,11 @@ int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* p
             cudaStream_t st, double* dot) {
   prof_begin("amp_vjp", (double)B * pr.nb * (8.0 * nparts + (base_h ? 4 : 2) * sizeof(T)) +
                             (ss ? B : 1) * pr.nb * 40.0, st);
-  k_amp_vjp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, partials, nparts, base_h, bhs,
-                                                  out_h, ohs, dot);
+  if (pr.kind == NRE_AMP_MATERN_MODEL)
+    k_amp_vjp_matern<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, partials, nparts, base_h, bhs, out_h, ohs,
+                                                         dot);
+  else
+    k_amp_vjp<T><<<B, amp_threads(pr.nb), 0, st>>>(pr, state, ss, partials, nparts, base_h, bhs, out_h, ohs, dot);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;

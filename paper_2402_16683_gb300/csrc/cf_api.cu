@@ -29,7 +29,7 @@ int ensure(DevBuf& b, size_t bytes) {
 template <typename T>
 AmpView<T> amp_view(const nre_cf_plan* p, const double* abin, int64_t astride) {
   AmpView<T> v{};
-  v.mode = p->amp_kind == NRE_AMP_POWER_MODEL ? AMPV_MODEL : AMPV_FIXED;
+  v.mode = binned_model(p) ? AMPV_MODEL : AMPV_FIXED;
   v.afull = p->afull.as<T>();
   v.abin = abin;
   v.astride = astride;
@@ -196,7 +196,7 @@ int cf_forward_t(nre_cf_plan* p, const T* xi, T* s, int B, cudaStream_t st) {
   epi.y = s;
   epi.ys = N;
   epi.offset = p->offset_mean;
-  if (p->amp_kind == NRE_AMP_POWER_MODEL) {
+  if (binned_model(p)) {
     const int SS = amp_state_size(p->n_bins);
     NRE_TRY(ensure(p->ws_state, (size_t)B * SS * sizeof(double)));
     double* state = p->ws_state.as<double>();
@@ -223,7 +223,7 @@ int cf_jvp_t(nre_cf_plan* p, const T* xi_p, const T* v, T* jv, int B, cudaStream
   epi.mode = EPI_BUF;
   epi.y = jv;
   epi.ys = N;
-  if (p->amp_kind == NRE_AMP_POWER_MODEL) {
+  if (binned_model(p)) {
     const int nb = p->n_bins, SS = amp_state_size(nb);
     NRE_TRY(ensure(p->ws_state, (size_t)B * SS * sizeof(double)));
     NRE_TRY(ensure(p->ws_dA, (size_t)B * nb * sizeof(double)));
@@ -257,7 +257,7 @@ int cf_vjp_t(nre_cf_plan* p, const T* xi_p, const T* ct, T* g, int B, cudaStream
   epi.mode = EPI_AMP;
   epi.y = g;
   epi.ys = p->stride;
-  if (p->amp_kind == NRE_AMP_POWER_MODEL) {
+  if (binned_model(p)) {
     const int nb = p->n_bins, SS = amp_state_size(nb);
     NRE_TRY(ensure(p->ws_state, (size_t)B * SS * sizeof(double)));
     NRE_TRY(ensure(p->ws_part, (size_t)B * max_parts(p) * nb * sizeof(double)));
@@ -315,7 +315,7 @@ int cf_create(nre_cf_plan** plan, int ndim, const int64_t* shape, const double* 
   double lbox;
   NRE_TRY(check_geometry(ndim, shape, spacing, &lbox));
   if (dtype != NRE_F32 && dtype != NRE_F64) return set_error(NRE_EINVAL, "dtype must be NRE_F32 or NRE_F64");
-  if (amp->kind < NRE_AMP_ARRAY || amp->kind > NRE_AMP_POWER_MODEL)
+  if (amp->kind < NRE_AMP_ARRAY || amp->kind > NRE_AMP_MATERN_MODEL)
     return set_error(NRE_EINVAL, "unknown amplitude kind %d", amp->kind);
   nre_cf_plan* p = new nre_cf_plan();
   p->ndim = ndim;
@@ -361,18 +361,31 @@ int cf_create(nre_cf_plan** plan, int ndim, const int64_t* shape, const double* 
   } else {
     const int nb = amp->n_bins;
     if (nb < 2 || nb > 1024) return fail(set_error(NRE_EINVAL, "n_bins must be in [2, 1024]"));
-    if (!(amp->fluct_mean > 0 && amp->fluct_std > 0 && amp->flex_mean > 0 && amp->flex_std > 0 &&
-          amp->asp_mean > 0 && amp->asp_std > 0 && amp->slope_std >= 0))
-      return fail(set_error(NRE_EINVAL, "log-normal hyper-parameters need positive mean and std"));
+    if (amp->kind == NRE_AMP_POWER_MODEL) {
+      if (!(amp->fluct_mean > 0 && amp->fluct_std > 0 && amp->flex_mean > 0 && amp->flex_std > 0 &&
+            amp->asp_mean > 0 && amp->asp_std > 0 && amp->slope_std >= 0))
+        return fail(set_error(NRE_EINVAL, "log-normal hyper-parameters need positive mean and std"));
+    } else if (!(amp->scale_mean > 0 && amp->scale_std > 0 && amp->cutoff_mean > 0 && amp->cutoff_std > 0 &&
+                 amp->lls_std >= 0)) {
+      return fail(set_error(NRE_EINVAL, "Matern scale / cutoff need positive mean and std, slope std >= 0"));
+    }
     if (qmax > 65535 * 4096)  // unreachable for shapes <= 4096^2 but keeps the LUT bounded
       return fail(set_error(NRE_EINVAL, "grid too large for the bin table"));
     p->n_bins = nb;
-    p->n_hyper = 4 + 2 * (nb - 1);
-    lognormal(amp->fluct_mean, amp->fluct_std, &p->mu_fl, &p->s_fl);
-    lognormal(amp->flex_mean, amp->flex_std, &p->mu_fx, &p->s_fx);
-    lognormal(amp->asp_mean, amp->asp_std, &p->mu_as, &p->s_as);
-    p->sl_m = amp->slope_mean;
-    p->sl_s = amp->slope_std;
+    if (amp->kind == NRE_AMP_POWER_MODEL) {
+      p->n_hyper = 4 + 2 * (nb - 1);
+      lognormal(amp->fluct_mean, amp->fluct_std, &p->mu_fl, &p->s_fl);
+      lognormal(amp->flex_mean, amp->flex_std, &p->mu_fx, &p->s_fx);
+      lognormal(amp->asp_mean, amp->asp_std, &p->mu_as, &p->s_as);
+      p->sl_m = amp->slope_mean;
+      p->sl_s = amp->slope_std;
+    } else {
+      p->n_hyper = 3;  // xi_scale, xi_cutoff, xi_slope
+      lognormal(amp->scale_mean, amp->scale_std, &p->mu_sc, &p->s_sc);
+      lognormal(amp->cutoff_mean, amp->cutoff_std, &p->mu_ct, &p->s_ct);
+      p->al_m = amp->lls_mean;
+      p->al_s = amp->lls_std;
+    }
     std::vector<int> boq;
     double lmin, dl;
     log_bins(qmax, lbox, nb, boq, &lmin, &dl);

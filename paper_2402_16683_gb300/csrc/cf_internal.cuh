@@ -142,10 +142,12 @@ struct Epi {
   int64_t ps;
   int bins;           // accumulate the per-bin sums
   AmpView<T> av;
-  // EPI_AMP with bins: when set, the per-bin sums go into gsum[b][nb] in place
-  // (zeroed before the sweep; FP64 atomic adds of the per-CTA sums) instead
-  // of per-CTA partials, so that the reader sums nothing
+  // EPI_AMP with bins: when set, the complete per-bin sums go into gsum[b][nb]
+  // (so that the reader sums nothing): every CTA writes its partial, and the
+  // last CTA of sample b to finish (counter gcnt[b], zero on entry and left
+  // zero) adds the partials in a fixed order
   double* gsum;
+  unsigned* gcnt;
   // EPI_AMP with base, last sweep of a metric product: per-CTA partials of
   // sum(base * y) at dot[b * kDotStride + cta] (row sweeps of 2-D / 3-D grids;
   // other sweeps leave them to a separate reduction)
@@ -209,41 +211,66 @@ struct Epi {
     store(b, flat, v0, bn[0], c[0]);
     store(b, flat + 1, v1, bn[1], c[1]);
   }
-  __device__ __forceinline__ void store(int b, int64_t flat, T val, double* hist) const {
-    int bn;
-    T c;
-    store(b, flat, val, bn, c);
-    if (bn >= 0) atomicAdd(&hist[bn], double(c));
-  }
 };
 
-// Middle operation between the two transforms of the metric: t = w * y.
+// Middle operation between the two transforms of the metric: t = w * y, the
+// weights of sample b at w + b * ws (ws = 0: one weight array for the batch;
+// ws = N: a linearisation point per sample, as in the KL's averaged metric).
 template <typename T>
 struct Mid {
-  const T* w;  // [N]
-  __device__ __forceinline__ T apply(int64_t flat, T y) const { return __ldg(&w[flat]) * y; }
-  __device__ __forceinline__ typename CplxT<T>::type apply2(int64_t flat, T y0, T y1) const {
+  const T* w;  // [N] or [B][N]
+  int64_t ws;
+  __device__ __forceinline__ T at(int b, int64_t flat) const { return __ldg(&w[b * ws + flat]); }
+  __device__ __forceinline__ T apply(int b, int64_t flat, T y) const { return at(b, flat) * y; }
+  __device__ __forceinline__ typename CplxT<T>::type apply2(int b, int64_t flat, T y0, T y1) const {
     typedef typename CplxT<T>::type C;
-    const C ww = __ldg(reinterpret_cast<const C*>(w + flat));
+    const C ww = __ldg(reinterpret_cast<const C*>(w + b * ws + flat));
     return cmake<C>(ww.x * y0, ww.y * y1);
   }
 };
 
-// Arguments of one row sweep (last axis, length L).
-// A CTA's per-bin sums: into epi.gsum (atomically) or as partial `part` of
-// nparts for sample b.  Called by all threads after the sums are complete.
+// A CTA's per-bin sums, from nreg warp-private histograms (region r at
+// hist + r * rstride, folded in region order in FP64), as partial `part` of
+// nparts for sample b at partials[(b * nparts + part) * nb]; with e.gsum the
+// last CTA of sample b then adds the nparts partials in a fixed order into
+// e.gsum[b * nb] (see Epi::gsum).  Called by all threads of the CTA after its
+// last histogram update, with a __syncthreads() before.
 template <typename T, typename H>
-__device__ __forceinline__ void store_bins(const Epi<T>& e, double* partials, int b, int nparts, int part,
-                                           const H* hist, int nb) {
-  if (e.gsum != nullptr) {
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-      if (hist[i] != H(0)) atomicAdd(&e.gsum[(int64_t)b * nb + i], double(hist[i]));
-  } else {
-    double* dst = partials + ((int64_t)b * nparts + part) * nb;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = hist[i];
+__device__ __forceinline__ void fold_bins(const Epi<T>& e, double* partials, int b, int nparts, int part,
+                                          const H* hist, int nreg, int rstride, int nb) {
+  double* dst = partials + ((int64_t)b * nparts + part) * nb;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < nreg; ++r) s += double(hist[r * rstride + i]);
+    dst[i] = s;
   }
+  if (e.gsum == nullptr) return;
+  __shared__ bool s_last;
+  __threadfence();  // this CTA's partial before its arrival
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&e.gcnt[b], 1u) == (unsigned)(nparts - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the other CTAs' partials from L2 (ld.global.cg: not through this SM's L1),
+  // eight loads in flight per thread, added in a fixed order
+  const double* src = partials + (int64_t)b * nparts * nb;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int c = 0;
+    for (; c + 8 <= nparts; c += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += __ldcg(&src[(int64_t)(c + u) * nb + i]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c + u < nparts) acc[u] += __ldcg(&src[(int64_t)(c + u) * nb + i]);
+    e.gsum[(int64_t)b * nb + i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  }
+  if (threadIdx.x == 0) e.gcnt[b] = 0u;
 }
 
+// Arguments of one row sweep (last axis, length L).
 template <typename T>
 struct RowArgs {
   int L, log2L, log2Lmax;
@@ -291,6 +318,8 @@ struct nre_cf_plan {
   int64_t latent = 0, stride = 0;
   // prior of the power model: log-normal (mu, s) and slope (mean, std)
   double mu_fl = 0, s_fl = 0, mu_fx = 0, s_fx = 0, mu_as = 0, s_as = 0, sl_m = 0, sl_s = 0;
+  // prior of the Matern model: scale and cutoff log-normal, slope (mean, std)
+  double mu_sc = 0, s_sc = 0, mu_ct = 0, s_ct = 0, al_m = 0, al_s = 0;
   int n_groups = 0, G = 1;
   nre::DevBuf tw;        // complex twiddles, Lmax entries, plan dtype
   nre::DevBuf afull;     // fixed kinds: A_full [N], plan dtype
@@ -305,9 +334,17 @@ struct nre_cf_plan {
 
 namespace nre {
 
+// Amplitude models with hyper-parameters on log-|k| bins (the power model and
+// the Matern model): every per-bin table, bin sum and Jacobian path serves both.
+inline bool binned_model(const nre_cf_plan* p) {
+  return p->amp_kind == NRE_AMP_POWER_MODEL || p->amp_kind == NRE_AMP_MATERN_MODEL;
+}
+
 // Amplitude-model kernels (amp.cu)
 struct AmpPrior {
-  double mu_fl, s_fl, mu_fx, s_fx, mu_as, s_as, sl_m, sl_s;
+  int kind;  // NRE_AMP_POWER_MODEL or NRE_AMP_MATERN_MODEL
+  double mu_fl, s_fl, mu_fx, s_fx, mu_as, s_as, sl_m, sl_s;  // power model
+  double mu_sc, s_sc, mu_ct, s_ct, al_m, al_s;               // Matern model
   const double* centres;
   const double* counts;
   int nb;

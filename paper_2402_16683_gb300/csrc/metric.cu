@@ -36,7 +36,7 @@ namespace nre {
 template <typename T>
 AmpView<T> metric_view(const nre_metric* m) {
   const nre_cf_plan* p = m->cf;
-  if (p->amp_kind != NRE_AMP_POWER_MODEL) return amp_view<T>(p, nullptr, 0);
+  if (!binned_model(p)) return amp_view<T>(p, nullptr, 0);
   AmpView<T> v = amp_view<T>(p, m->state.as<double>() + as_A(p->n_bins), 0);
   v.mode = AMPV_PIX;
   v.afull = m->apix.as<T>();
@@ -84,7 +84,7 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   epi.response = m->lik.response;
   epi.sig_or_scale = m->lik.sig_or_scale;
   epi.mask = m->mask.p ? m->mask.as<T>() : nullptr;
-  if (p->amp_kind == NRE_AMP_POWER_MODEL) {
+  if (binned_model(p)) {
     const int nb = p->n_bins;
     NRE_TRY(ensure(m->state, amp_state_size(nb) * sizeof(double)));
     NRE_TRY(ensure(m->dA, (size_t)m->max_batch * nb * sizeof(double)));
@@ -100,6 +100,11 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
       NRE_TRY(ensure(m->amp_eye, (size_t)nh * nh * sizeof(T)));
       NRE_TRY(ensure(m->amp_Jt, (size_t)nh * nb * sizeof(double)));
       NRE_TRY(ensure(m->gsum, (size_t)m->max_batch * nb * sizeof(double)));
+      const size_t cnt = (size_t)m->max_batch * sizeof(unsigned);
+      if (m->gcnt.bytes < cnt) {
+        NRE_TRY(ensure(m->gcnt, cnt));
+        NRE_TRY_CUDA(cudaMemsetAsync(m->gcnt.p, 0, cnt, st));  // the sweeps leave them zero
+      }
       NRE_TRY(amp_jacobian<T>(amp_prior_of(p), m->state.as<double>(), nh, m->amp_eye.as<T>(),
                               m->amp_Jt.as<double>(), m->amp_G.as<float>(), m->amp_Gt.as<float>(), st));
       m->amp_lin = true;
@@ -136,7 +141,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
   epi.bs = S;
   epi.dot = dot;
   Mid<T> mid{m->w.as<T>()};
-  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const bool model = binned_model(p);
   const int nb = p->n_bins;
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
   hyper_in_cg = hyper_in_cg && model && m->amp_lin;
@@ -157,7 +162,10 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
     epi.bins = 1;
     epi.xi_p = xp;
     epi.ps = 0;
-    if (m->amp_lin) epi.gsum = m->gsum.as<double>();
+    if (m->amp_lin) {
+      epi.gsum = m->gsum.as<double>();
+      epi.gcnt = m->gcnt.as<unsigned>();
+    }
   } else {
     pro.av = amp_view<T>(p, nullptr, 0);
     epi.av = pro.av;
@@ -186,10 +194,15 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
       eh.y += (int64_t)b0 * epi.ys;
       if (eh.base) eh.base += (int64_t)b0 * epi.bs;
       if (eh.ps) eh.xi_p += (int64_t)b0 * eh.ps;
-      if (eh.gsum) eh.gsum += (int64_t)b0 * nb;
+      if (eh.gsum) {
+        eh.gsum += (int64_t)b0 * nb;
+        eh.gcnt += b0;
+      }
       if (eh.dot) eh.dot += (int64_t)b0 * kDotStride;
+      // each half's CTA partials in its own slab of the partials buffer
+      double* hpart = model ? m->part.as<double>() + (int64_t)b0 * max_parts(p) * nb : nullptr;
       NRE_TRY(run_hartley<T>(p, Bh, ph, eh, &mid, m->tmp0.as<T>() + (int64_t)b0 * N,
-                             m->tmp1.as<T>() + (int64_t)b0 * N, nullptr, &np, h ? m->side : st));
+                             m->tmp1.as<T>() + (int64_t)b0 * N, hpart, &np, h ? m->side : st));
     }
     NRE_TRY_CUDA(cudaEventRecord(m->ev_join, m->side));
     NRE_TRY_CUDA(cudaStreamWaitEvent(st, m->ev_join, 0));
@@ -221,7 +234,7 @@ int cf_mgvi_rhs(nre_metric* m, const T* xi_prime, const T* eta, T* b, int B, cud
   epi.ys = S;
   epi.base = xi_prime;
   epi.bs = S;
-  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const bool model = binned_model(p);
   if (model) {
     epi.av = metric_view<T>(m);
     epi.bins = 1;

@@ -32,7 +32,8 @@ struct nre_metric {
   // FP32 power model: the amplitude Jacobian at xi_p (see amp_jacobian)
   bool amp_lin = false;
   nre::DevBuf amp_G, amp_Gt, amp_eye, amp_Jt;
-  nre::DevBuf gsum;  // [max_batch][n_bins] in-place bin sums of the last sweep
+  nre::DevBuf gsum;  // [max_batch][n_bins] complete bin sums of the last sweep
+  nre::DevBuf gcnt;  // [max_batch] unsigned arrival counters of those sums (zero between sweeps)
   nre::DevBuf tmp0, tmp1, part;
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;
@@ -50,6 +51,9 @@ struct nre_metric {
   nre::DevBuf pc_invD, pc_e;          // per pixel: 1 / D and A xi_p / D
   nre::DevBuf pc_Gt;                  // float [n_bins][n_hyper]: G transposed
   nre::DevBuf pc_cdev;                // double: pc_c on the device
+  // residual correction (refine.cu): FP64 metric: residual, product, partials;
+  // low precision metric: right-hand side and correction of the inner solve
+  nre::DevBuf rf_r, rf_q, rf_part;
   // second stream of a metric product split into two half batches (metric.cu)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -54,7 +54,7 @@ template <typename T>
 int forward_t(nre_cf_plan* p, const T* xi, T* s, int B, cudaStream_t st) {
   using namespace nre;
   const int64_t N = p->N;
-  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const bool model = binned_model(p);
   const size_t tmp = align256((size_t)B * N * sizeof(T));
   const int ntmp = p->ndim == 3 ? 2 : (p->ndim == 2 ? 1 : 0);
   const int SS = model ? amp_state_size(p->n_bins) : 0;

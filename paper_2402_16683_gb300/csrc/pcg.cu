@@ -33,6 +33,14 @@ enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = C
 // Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
 // least 4 vectors per thread and at most 64 blocks.
+// Dynamic shared memory above the 48 KB default (warp-private histograms of
+// up to 1024 bins).
+template <typename K>
+int pc_smem(K k, size_t bytes) {
+  if (bytes > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return NRE_OK;
+}
+
 int pc_blocks(int64_t n, int B) {
   int64_t nb = (4 * (int64_t)sm_count() + B - 1) / B;
   const int64_t cap = (n + PC_THREADS * 16 - 1) / (PC_THREADS * 16);
@@ -105,11 +113,18 @@ __device__ __forceinline__ void bins_add(const PCArgs<T>& pc, int64_t i, const T
   add_slots<W, T>(key, val, hist);
 }
 
+// The block's bin sums from its warps' private histograms (hist + w nb),
+// folded in warp order, as partial blockIdx.x of system b.
 template <typename T>
 __device__ __forceinline__ void bins_out(const PCArgs<T>& pc, int b, const double* hist) {
   __syncthreads();
   double* dst = pc.bin_part + ((int64_t)b * gridDim.x + blockIdx.x) * pc.nb;
-  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) dst[i] = hist[i];
+  const int nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += hist[w * pc.nb + i];
+    dst[i] = t;
+  }
 }
 
 // x = 0, r = b; partials of r.r and of the bins of r.
@@ -119,7 +134,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T*
   extern __shared__ double hist[];
   constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
+  // warp-private bin histograms of nb entries (see warp_run_add)
+  for (int i = threadIdx.x; i < (PC_THREADS / 32) * pc.nb; i += blockDim.x) hist[i] = 0.0;
+  double* whist = hist + (threadIdx.x >> 5) * pc.nb;
   __syncthreads();
   const int64_t off = (int64_t)b * S;
   RunSum<T> acc;
@@ -150,7 +167,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T*
       }
     }
     acc.add(run);
-    if (pc.nb > 0) bins_add(pc, i, v, hist);
+    if (pc.nb > 0) bins_add(pc, i, v, whist);
   });
   partial_out(acc, rr_part);
   if (pc.nb > 0) bins_out(pc, b, hist);
@@ -165,7 +182,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
   extern __shared__ double hist[];
   constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
+  // warp-private bin histograms of nb entries (see warp_run_add)
+  for (int i = threadIdx.x; i < (PC_THREADS / 32) * pc.nb; i += blockDim.x) hist[i] = 0.0;
+  double* whist = hist + (threadIdx.x >> 5) * pc.nb;
   __syncthreads();
   const double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
@@ -214,7 +233,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
       }
     }
     acc.add(run);
-    if (pc.nb > 0) bins_add(pc, i, v, hist);
+    if (pc.nb > 0) bins_add(pc, i, v, whist);
   });
   partial_out(acc, rr_part);
   if (pc.nb > 0) bins_out(pc, b, hist);
@@ -433,30 +452,52 @@ __global__ void k_pc_pix(PCArgs<T> pc, T* invD, T* e) {
 }
 
 // U_b = sum_{k in b} xi_p[k]^2 / D_k (bins of the expansion point), and
-// sum w for c = N mean(w).
+// sum w for c = N mean(w): per block into part[blockIdx.x][1 + nb] (entry 0 the
+// weight sum), from warp-private histograms folded in warp order; the trip
+// count is uniform over the block (warp reductions of the bins).
 template <typename T>
-__global__ void k_pc_setup(const T* w, int64_t N, PCArgs<T> pc, double* U, double* wsum) {
+__global__ void __launch_bounds__(PC_THREADS) k_pc_setup(const T* w, int64_t N, PCArgs<T> pc, double* part) {
   extern __shared__ double hist[];
-  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) hist[i] = 0.0;
+  const int nbh = (pc.nb > 0 && pc.c > 0.0) ? pc.nb : 0;
+  double* whist = hist + (threadIdx.x >> 5) * nbh;
+  for (int i = threadIdx.x; i < (PC_THREADS / 32) * nbh; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    acc += double(w[i]);
-    if (pc.nb > 0 && pc.c > 0.0) {
-      const int bn = pc.av.bin(i);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < N; i0 += step) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool act = i < N;
+    if (act) acc += double(w[i]);
+    if (nbh > 0) {
+      const int bn = act ? pc.av.bin(i) : -1;
+      double c = 0.0;
       if (bn >= 0) {
         const double A = double(pc.av.amp(0, i, bn));
         const double xp = double(pc.xi_p[i]);
-        atomicAdd(&hist[bn], xp * xp / (1.0 + pc.c * A * A));
+        c = xp * xp / (1.0 + pc.c * A * A);
       }
+      warp_run_add(bn, c, whist);
     }
   }
   __shared__ double red[PC_THREADS / 32];
   const double t = block_sum(acc, red);
-  if (threadIdx.x == 0) atomicAdd(wsum, t);
+  double* dst = part + (int64_t)blockIdx.x * (1 + pc.nb);
+  if (threadIdx.x == 0) dst[0] = t;
   __syncthreads();
-  if (pc.nb > 0 && pc.c > 0.0)
-    for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) atomicAdd(&U[i], hist[i]);
+  for (int i = threadIdx.x; i < pc.nb; i += blockDim.x) {
+    double u = 0.0;
+    for (int wi = 0; wi < (nbh > 0 ? PC_THREADS / 32 : 0); ++wi) u += hist[wi * nbh + i];
+    dst[1 + i] = u;
+  }
+}
+
+// out[j] = sum over blocks (in block order) of part[blk][j], j < nj.
+__global__ void k_pc_setup_sum(const double* part, int nblk, int nj, double* out) {
+  for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * nj + j];
+    out[j] = s;
+  }
 }
 
 template <typename T>
@@ -467,7 +508,7 @@ PCArgs<T> pc_args(nre_metric* m) {
   a.c = m->pc_c;
   a.cdev = m->pc_cdev.as<double>();
   a.xi_p = m->xi_p.as<T>();
-  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const bool model = binned_model(p);
   a.av = metric_view<T>(m);
   a.nb = model ? p->n_bins : 0;
   a.invD = m->pc_invD.as<T>();
@@ -519,17 +560,21 @@ template <typename T>
 int setup_t(nre_metric* m, cudaStream_t st) {
   nre_cf_plan* p = m->cf;
   const int64_t N = p->N;
-  const bool model = p->amp_kind == NRE_AMP_POWER_MODEL;
+  const bool model = binned_model(p);
   const int nb = model ? p->n_bins : 0, nh = model ? p->n_hyper : 0;
   DevBuf& dbuf = m->pc_tmp;  // metric-owned, so a re-setup allocates nothing
-  NRE_TRY(ensure(dbuf, (size_t)(1 + nb) * sizeof(double)));
-  NRE_TRY_CUDA(cudaMemsetAsync(dbuf.p, 0, (size_t)(1 + nb) * sizeof(double), st));
+  // [0, 1 + nb): the sums; then one row of 1 + nb per block of k_pc_setup
+  const int sblk = sm_count();
+  NRE_TRY(ensure(dbuf, (size_t)(1 + sblk) * (1 + nb) * sizeof(double)));
+  double* spart = dbuf.as<double>() + (1 + nb);
   // pass 1: mean weight
   PCArgs<T> a = pc_args<T>(m);
   a.c = 0.0;
   prof_begin("pc_setup", (double)N * sizeof(T), st);
-  k_pc_setup<T><<<sm_count(), PC_THREADS, (size_t)(nb > 0 ? nb : 1) * sizeof(double), st>>>(
-      m->w.as<T>(), N, a, dbuf.as<double>() + 1, dbuf.as<double>());
+  NRE_TRY(pc_smem(k_pc_setup<T>, (size_t)(PC_THREADS / 32) * (nb > 0 ? nb : 1) * sizeof(double)));
+  k_pc_setup<T><<<sblk, PC_THREADS, (size_t)(PC_THREADS / 32) * (nb > 0 ? nb : 1) * sizeof(double), st>>>(
+      m->w.as<T>(), N, a, spart);
+  k_pc_setup_sum<<<1, 256, 0, st>>>(spart, sblk, 1 + nb, dbuf.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();
   double wsum = 0.0;
@@ -549,11 +594,11 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   NRE_CHECK_LAUNCH();
   if (!model) return NRE_OK;
   // pass 2: U_b with the final c
-  NRE_TRY_CUDA(cudaMemsetAsync(dbuf.p, 0, (size_t)(1 + nb) * sizeof(double), st));
   a.c = m->pc_c;
   prof_begin("pc_setup", (double)N * 2 * sizeof(T), st);
-  k_pc_setup<T><<<sm_count(), PC_THREADS, (size_t)nb * sizeof(double), st>>>(m->w.as<T>(), N, a,
-                                                                     dbuf.as<double>() + 1, dbuf.as<double>());
+  k_pc_setup<T><<<sblk, PC_THREADS, (size_t)(PC_THREADS / 32) * nb * sizeof(double), st>>>(m->w.as<T>(), N, a,
+                                                                                          spart);
+  k_pc_setup_sum<<<1, 256, 0, st>>>(spart, sblk, 1 + nb, dbuf.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();
   // amplitude Jacobian G[h][b] = dA_b / dh: JVPs along the unit vectors
@@ -625,7 +670,7 @@ PCGWork<T> pcg_work(nre_metric* m, int B) {
   w.pc.nb = w.nb;
   w.pc.bin_part = w.nb > 0 ? m->pc_part.as<double>() : nullptr;
   w.pc.gz = w.nb > 0 ? m->pc_gz.as<double>() : nullptr;
-  w.hsm = (size_t)(w.nb > 0 ? w.nb : 1) * sizeof(double);
+  w.hsm = (size_t)(PC_THREADS / 32) * (w.nb > 0 ? w.nb : 1) * sizeof(double);  // warp-private histograms
   w.hyp_sm = (size_t)(w.nb + 2 * w.nh) * sizeof(float);
   return w;
 }
@@ -669,6 +714,7 @@ int pcg_begin_t(nre_metric* m, const T* b, T* x, int B, double rtol, cudaStream_
   const PCGWork<T> w = pcg_work<T>(m, B);
   const double vb = (double)B * n * sizeof(T);
   prof_begin("pcg_init", 3.0 * vb, st);
+  NRE_TRY(pc_smem(k_pcg_init<T>, w.hsm));
   k_pcg_init<T><<<dim3(nblk, B), PC_THREADS, w.hsm, st>>>(b, x, w.r, n, S, w.part_rr, w.pc);
   prof_end(st);
   NRE_CHECK_LAUNCH();
@@ -690,6 +736,7 @@ int pcg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t 
     // p.q comes fused with the metric product (kDotStride partials per system)
     NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, m->cg_dot.as<double>()));
     prof_begin("pcg_update", 6 * vb, st);
+    NRE_TRY(pc_smem(k_pcg_update<T>, w.hsm));
     k_pcg_update<T><<<grid, PC_THREADS, w.hsm, st>>>(x, w.r, w.p, w.q, n, S, w.sc, m->cg_dot.as<double>(),
                                                       kDotStride, w.part_rr, w.pc);
     prof_end(st);

@@ -210,15 +210,19 @@ __device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8]
 
 // Sum `val` over the runs of equal `key` among the lanes of a warp (runs are
 // maximal ranges of consecutive lanes with the same key) and add each run's
-// total to hist[key] from its last lane.  key < 0: no contribution.
-// The run sums are formed in V (the plan's value type: FP32 products of FP32
-// data are summed over at most 32 lanes) and added to hist in H: the register
-// sweeps keep a CTA's sums in V (shared-memory FP32 atomics for FP32 plans:
-// FP64 adds and conversions per run cost more than the rest of the epilogue
-// on this part, whose FP64 rate is a small fraction of its FP32 rate) and
-// fold them into FP64 once per CTA; the other callers pass FP64 sums.
+// total to whist[key] from its last lane.  key < 0: no contribution.
+// whist is a histogram that only this warp writes (a warp-private region of
+// shared memory), so no atomics are needed and the result does not depend on
+// how warps or CTAs are scheduled: runs of the same key that are not adjacent
+// are added one after another in lane order (ranked with __match_any_sync),
+// and successive calls add in program order.  The caller folds the warps'
+// histograms in a fixed order (fold_bins).  The run sums are formed in V (the
+// plan's value type: FP32 products of FP32 data are summed over at most 32
+// lanes) and added to whist in H (FP32 for FP32 plans: an FP64 add and
+// conversion per run costs more than the rest of the epilogue on this part,
+// whose FP64 rate is a small fraction of its FP32 rate).
 template <typename V, typename H>
-__device__ __forceinline__ void warp_run_add(int key, V val, H* hist) {
+__device__ __forceinline__ void warp_run_add(int key, V val, H* whist) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int prev = __shfl_up_sync(full, key, 1);
@@ -233,12 +237,29 @@ __device__ __forceinline__ void warp_run_add(int key, V val, H* hist) {
     if (lane - o >= seg) val += ov;
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (tail && key >= 0) atomicAdd(&hist[key], H(val));
+  const bool act = tail && key >= 0;
+  __syncwarp();  // earlier calls' writes by other lanes are visible
+  // Keys monotone along the lanes (the sweeps' usual case: consecutive |k|)
+  // give every run its own key, and the tails add at once.
+  const bool mono = __all_sync(full, lane == 0 || prev <= key) || __all_sync(full, lane == 0 || prev >= key);
+  if (mono) {
+    if (act) whist[key] += H(val);
+  } else {
+    // tails of other runs with the same key (inactive lanes get unique keys)
+    const unsigned same = __match_any_sync(full, act ? key : -1 - lane);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    for (int r = 0; __any_sync(full, act && rank >= r); ++r) {
+      if (act && rank == r) whist[key] += H(val);
+      __syncwarp();
+    }
+  }
+  __syncwarp();
 }
 
 // Adds the contributions c[s] of slots with bins bn[s] (all into the same
-// histogram): slots sharing a bin are summed first, then each distinct bin is
-// reduced over the warp.  Must be called by all lanes of the warp.
+// warp-private histogram): slots sharing a bin are summed first, then each
+// distinct bin is reduced over the warp.  Must be called by all lanes of the
+// warp.
 template <int S, typename V, typename H>
 __device__ __forceinline__ void add_slots(const int (&bn)[S], const V (&c)[S], H* hist) {
 #pragma unroll

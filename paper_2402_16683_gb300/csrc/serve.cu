@@ -71,15 +71,15 @@ int request_geom(const nre_serve_req* r, Geom* g) {
     g->qmax += (n / 2) * (n / 2);
     g->Lmax = std::max<int>(g->Lmax, (int)n);
   }
-  if (r->amp.kind == NRE_AMP_POWER_MODEL) {
+  if (r->amp.kind == NRE_AMP_POWER_MODEL || r->amp.kind == NRE_AMP_MATERN_MODEL) {
     if (r->amp.n_bins < 2 || r->amp.n_bins > 1024) return set_error(NRE_EINVAL, "n_bins must be in [2, 1024]");
     g->nb = r->amp.n_bins;
-    g->nh = 4 + 2 * (g->nb - 1);
+    g->nh = r->amp.kind == NRE_AMP_POWER_MODEL ? 4 + 2 * (g->nb - 1) : 3;
   } else if (r->amp.kind == NRE_AMP_MATERN_FIXED) {
     g->nb = 0;
     g->nh = 0;
   } else {
-    return set_error(NRE_EINVAL, "serving takes POWER_MODEL or MATERN_FIXED amplitudes");
+    return set_error(NRE_EINVAL, "serving takes POWER_MODEL, MATERN_MODEL or MATERN_FIXED amplitudes");
   }
   g->latent = g->N + g->nh;
   g->S = round_up(g->latent, 64);
@@ -136,7 +136,9 @@ struct Key {
            a.zero_mode == c.zero_mode && a.fluct_mean == c.fluct_mean && a.fluct_std == c.fluct_std &&
            a.slope_mean == c.slope_mean && a.slope_std == c.slope_std && a.flex_mean == c.flex_mean &&
            a.flex_std == c.flex_std && a.asp_mean == c.asp_mean && a.asp_std == c.asp_std &&
-           a.offset_mean == c.offset_mean && a.offset_std == c.offset_std && a.n_bins == c.n_bins;
+           a.offset_mean == c.offset_mean && a.offset_std == c.offset_std && a.n_bins == c.n_bins &&
+           a.scale_mean == c.scale_mean && a.scale_std == c.scale_std && a.cutoff_mean == c.cutoff_mean &&
+           a.cutoff_std == c.cutoff_std && a.lls_mean == c.lls_mean && a.lls_std == c.lls_std;
   }
 };
 

@@ -31,12 +31,23 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
   const LayRow lay{LayRow::stride(L)};
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufB = bufA + nl * lay.ls;
+  // warp-private bin histograms: per warp nhist regions of nb (see warp_run_add)
   double* hist = reinterpret_cast<double*>(bufB + nl * lay.ls);
   const int nhist = (PM == 1) ? 2 * a.nU : 1;
+  constexpr int NW = SWEEP_THREADS / 32;
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  double* whist = hist + (threadIdx.x >> 5) * nhist * a.nb;
   if (bins)
-    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * nhist * a.nb; i += blockDim.x) hist[i] = 0.0;
   const int bsample = (PM == 1) ? 0 : blockIdx.y;
+  // output of one value; with bins its contribution goes to key keybase + bin
+  // (every lane of the warp calls this, `ok` false for lanes without output)
+  auto put = [&](int sb, int64_t flat, T val, int keybase, bool ok) {
+    int bn = -1;
+    T c = T(0);
+    if (ok) a.epi.store(sb, flat, val, bn, c);
+    if (bins) warp_run_add(bn >= 0 ? keybase + bn : -1, c, whist);
+  };
 
   for (int u0 = blockIdx.x * a.nU; u0 < a.n_units; u0 += gridDim.x * a.nU) {
     // ---- load (prologue)
@@ -69,35 +80,38 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
         C z = Z[lay.idx(u, x)], zm = Z[lay.idx(u, xm)];
         T ha[2], hb[2];
         hartley_unpack<T>(z, zm, ha, hb);
-        const T w0 = a.mid.w[x], w1 = a.mid.w[xm];
-        Z[lay.idx(u, x)] = cmake<C>(w0 * ha[0], w0 * hb[0]);
-        if (xm != x) Z[lay.idx(u, xm)] = cmake<C>(w1 * ha[1], w1 * hb[1]);
+        // the pair's samples 2 unit (real part) and 2 unit + 1 (imaginary part)
+        const int sa = 2 * (u0 + u) < a.B ? 2 * (u0 + u) : a.B - 1;
+        const int sb = sa + 1 < a.B ? sa + 1 : sa;
+        Z[lay.idx(u, x)] = cmake<C>(a.mid.at(sa, x) * ha[0], a.mid.at(sb, x) * hb[0]);
+        if (xm != x) Z[lay.idx(u, xm)] = cmake<C>(a.mid.at(sa, xm) * ha[1], a.mid.at(sb, xm) * hb[1]);
       }
       __syncthreads();
       C* other = (Z == bufA) ? bufB : bufA;
       Z = block_fft(Z, other, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
     }
-    // ---- unpack, P, epilogue
-    for (int q = threadIdx.x; q < a.nU * (Lh + 1); q += blockDim.x) {
-      const int u = q / (Lh + 1), x = q - u * (Lh + 1);
+    // ---- unpack, P, epilogue (trip count uniform over the block: the bin
+    // sums reduce over whole warps)
+    const int nq = a.nU * (Lh + 1);
+    for (int q0 = 0; q0 < nq; q0 += blockDim.x) {
+      const int q = q0 + threadIdx.x;
+      const int u = q < nq ? q / (Lh + 1) : 0, x = q < nq ? q - u * (Lh + 1) : 0;
       const int unit = u0 + u;
-      if (unit >= a.n_units) continue;
+      const bool act = q < nq && unit < a.n_units;
       const int xm = (L - x) & (L - 1);
       if (PM == 1) {
         T ha[2], hb[2];
         hartley_unpack<T>(Z[lay.idx(u, x)], Z[lay.idx(u, xm)], ha, hb);
         const int s0 = 2 * unit;
-        double* h0 = hist + (2 * u) * a.nb;
-        a.epi.store(s0, x, ha[0], h0);
-        if (xm != x) a.epi.store(s0, xm, ha[1], h0);
-        if (s0 + 1 < a.B) {
-          a.epi.store(s0 + 1, x, hb[0], h0 + a.nb);
-          if (xm != x) a.epi.store(s0 + 1, xm, hb[1], h0 + a.nb);
-        }
+        const int k0 = (2 * u) * a.nb;
+        put(s0, x, ha[0], k0, act);
+        put(s0, xm, ha[1], k0, act && xm != x);
+        put(s0 + 1, x, hb[0], k0 + a.nb, act && s0 + 1 < a.B);
+        put(s0 + 1, xm, hb[1], k0 + a.nb, act && s0 + 1 < a.B && xm != x);
       } else if (PM == 2) {
         T R[2][2];
         hartley_unpack<T>(Z[lay.idx(u, x)], Z[lay.idx(u, xm)], R[0], R[1]);
-        const bool f0 = a.gflags[unit] & 1;
+        const bool f0 = act && (a.gflags[unit] & 1);
         const T half = T(0.5);
         T V[2][2];
 #pragma unroll
@@ -108,15 +122,15 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const int64_t row = a.grows[unit * 2 + s];
-          a.epi.store(bsample, row * L + x, V[s][0], hist);
-          if (xm != x) a.epi.store(bsample, row * L + xm, V[s][1], hist);
+          const int64_t row = act ? a.grows[unit * 2 + s] : 0;
+          put(bsample, row * L + x, V[s][0], 0, act);
+          put(bsample, row * L + xm, V[s][1], 0, act && xm != x);
         }
       } else {
         T R[4][2];
         hartley_unpack<T>(Z[lay.idx(2 * u, x)], Z[lay.idx(2 * u, xm)], R[0], R[1]);
         hartley_unpack<T>(Z[lay.idx(2 * u + 1, x)], Z[lay.idx(2 * u + 1, xm)], R[2], R[3]);
-        const int fl = a.gflags[unit];
+        const int fl = act ? a.gflags[unit] : 0;
         const bool f0 = fl & 1, f1 = fl & 2;
         const T half = T(0.5);
         T V[4][2];
@@ -129,23 +143,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_row_sweep(RowArgs<T> a) {
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          const int64_t row = a.grows[unit * 4 + s];
-          a.epi.store(bsample, row * L + x, V[s][0], hist);
-          if (xm != x) a.epi.store(bsample, row * L + xm, V[s][1], hist);
+          const int64_t row = act ? a.grows[unit * 4 + s] : 0;
+          put(bsample, row * L + x, V[s][0], 0, act);
+          put(bsample, row * L + xm, V[s][1], 0, act && xm != x);
         }
       }
     }
     __syncthreads();
   }
   if (bins) {
+    __syncthreads();
     if (PM == 1) {
+      // one CTA holds every pixel of its sample pairs: complete sums, the
+      // warps' histograms folded in warp order
       for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
         const int hs = i / a.nb, bn = i - hs * a.nb;
         const int sample = 2 * (blockIdx.x * a.nU) + hs;
-        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = hist[i];
+        double tot = 0.0;
+        for (int w = 0; w < NW; ++w) tot += hist[w * nhist * a.nb + i];
+        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = tot;
       }
     } else {
-      store_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, a.nb);
+      fold_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, NW, a.nb, a.nb);
     }
   }
 }
@@ -159,11 +178,19 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_col_sweep(ColArgs<T> a) {
   const LayCol lay{nl};
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufB = bufA + nl * L;
-  double* hist = reinterpret_cast<double*>(bufB + nl * L);
+  double* hist = reinterpret_cast<double*>(bufB + nl * L);  // warp-private regions of nb
+  constexpr int NW = SWEEP_THREADS / 32;
+  double* whist = hist + (threadIdx.x >> 5) * a.nb;
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
   if (bins)
-    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * a.nb; i += blockDim.x) hist[i] = 0.0;
   const int b = blockIdx.y;
+  auto put = [&](int64_t flat, T val, bool ok) {
+    int bn = -1;
+    T c = T(0);
+    if (ok) a.epi.store(b, flat, val, bn, c);
+    if (bins) warp_run_add(bn, c, whist);
+  };
 
   for (int64_t unit = blockIdx.x; unit < a.n_units; unit += gridDim.x) {
     const int64_t o = unit / a.nblk;
@@ -184,31 +211,33 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_col_sweep(ColArgs<T> a) {
         hartley_unpack<T>(Z[lay.idx(p, l)], Z[lay.idx(p, lm)], ha, hb);
         const int64_t f0 = base + (int64_t)l * a.inner + 2 * p;
         const int64_t f1 = base + (int64_t)lm * a.inner + 2 * p;
-        Z[lay.idx(p, l)] = cmake<C>(a.mid.apply(f0, ha[0]), a.mid.apply(f0 + 1, hb[0]));
-        if (lm != l) Z[lay.idx(p, lm)] = cmake<C>(a.mid.apply(f1, ha[1]), a.mid.apply(f1 + 1, hb[1]));
+        Z[lay.idx(p, l)] = cmake<C>(a.mid.apply(b, f0, ha[0]), a.mid.apply(b, f0 + 1, hb[0]));
+        if (lm != l) Z[lay.idx(p, lm)] = cmake<C>(a.mid.apply(b, f1, ha[1]), a.mid.apply(b, f1 + 1, hb[1]));
       }
       __syncthreads();
       C* other = (Z == bufA) ? bufB : bufA;
       Z = block_fft(Z, other, nl, L, a.log2L, a.tw, a.log2Lmax, lay);
     }
-    for (int q = threadIdx.x; q < nl * (Lh + 1); q += blockDim.x) {
-      const int l = q / nl, p = q - l * nl;
+    const int nq = nl * (Lh + 1);
+    for (int q0 = 0; q0 < nq; q0 += blockDim.x) {  // uniform trip count (warp bin sums)
+      const int q = q0 + threadIdx.x;
+      const bool act = q < nq;
+      const int l = act ? q / nl : 0, p = act ? q - l * nl : 0;
       const int lm = (L - l) & (L - 1);
       T ha[2], hb[2];
       hartley_unpack<T>(Z[lay.idx(p, l)], Z[lay.idx(p, lm)], ha, hb);
       const int64_t f0 = base + (int64_t)l * a.inner + 2 * p;
-      a.epi.store(b, f0, ha[0], hist);
-      a.epi.store(b, f0 + 1, hb[0], hist);
-      if (lm != l) {
-        const int64_t f1 = base + (int64_t)lm * a.inner + 2 * p;
-        a.epi.store(b, f1, ha[1], hist);
-        a.epi.store(b, f1 + 1, hb[1], hist);
-      }
+      const int64_t f1 = base + (int64_t)lm * a.inner + 2 * p;
+      put(f0, ha[0], act);
+      put(f0 + 1, hb[0], act);
+      put(f1, ha[1], act && lm != l);
+      put(f1 + 1, hb[1], act && lm != l);
     }
     __syncthreads();
   }
   if (bins) {
-    store_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, a.nb);
+    __syncthreads();
+    fold_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, NW, a.nb, a.nb);
   }
 }
 
@@ -300,7 +329,7 @@ int col_sweep_reg(ColArgs<T> a, int64_t outer, bool mid, int B, bool bins, int* 
                   int64_t N, bool* handled) {
   *handled = false;
   NRE_L_SWITCH(a.log2L, {
-    if (ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0) > 200 * 1024) return NRE_OK;
+    if (ColSmem<T, L>::bytes(a.nb, bins ? (ColShape<L, sizeof(T)>::NT / 32) * a.nb : 0) > 200 * 1024) return NRE_OK;
     constexpr int CW = ColShape<L, sizeof(T)>::W;
     a.W = CW < a.inner ? CW : (int)a.inner;
     a.nblk = a.inner / a.W;
@@ -361,8 +390,9 @@ int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
   if (D == 1) {
     a.n_units = (B + 1) / 2;
     a.nU = nl < a.n_units ? nl : a.n_units;
-    // keep the per-sample histograms (2 per unit) within 48 KB of shared memory
-    const int hist_cap = (epi.mode == EPI_AMP && epi.bins) ? 3072 / a.nb : nl;
+    // keep the per-sample histograms (2 per unit, one copy per warp) within
+    // 48 KB of shared memory
+    const int hist_cap = (epi.mode == EPI_AMP && epi.bins) ? 3072 / (2 * (SWEEP_THREADS / 32) * a.nb) : nl;
     if (a.nU > hist_cap) a.nU = hist_cap < 1 ? 1 : hist_cap;
     grid = dim3((a.n_units + a.nU - 1) / a.nU, 1);
     nhist = 2 * a.nU;
@@ -378,7 +408,7 @@ int row_sweep(const nre_cf_plan* p, int B, const Pro<T>& pro, const Epi<T>& epi,
     *nparts = gx;
   }
   const int nlines = a.nU * ((D == 3) ? 2 : 1);
-  const size_t smem = row_smem<T>(a.L, nlines, epi.mode == EPI_AMP && epi.bins ? nhist : 0, a.nb);
+  const size_t smem = row_smem<T>(a.L, nlines, epi.mode == EPI_AMP && epi.bins ? (SWEEP_THREADS / 32) * nhist : 0, a.nb);
   if (D == 1) {
     return mid ? launch_row<T, 1, true>(a, grid, smem, st, p->N) : launch_row<T, 1, false>(a, grid, smem, st, p->N);
   }
@@ -418,7 +448,7 @@ int col_sweep(const nre_cf_plan* p, int axis, int B, const Pro<T>& pro, const Ep
   int64_t gx = a.n_units < kMaxGridX ? a.n_units : kMaxGridX;
   *nparts = (int)gx;
   const size_t smem = (size_t)2 * (a.W / 2) * a.L * sizeof(typename CplxT<T>::type) +
-                      (epi.mode == EPI_AMP && epi.bins ? (size_t)a.nb * sizeof(double) : 0);
+                      (epi.mode == EPI_AMP && epi.bins ? (size_t)(SWEEP_THREADS / 32) * a.nb * sizeof(double) : 0);
   dim3 grid((unsigned)gx, B);
   return mid ? launch_col<T, true>(a, grid, smem, st, p->N) : launch_col<T, false>(a, grid, smem, st, p->N);
 }

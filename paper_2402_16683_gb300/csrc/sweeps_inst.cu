@@ -76,22 +76,19 @@ template <typename T, int L>
 int row_reg_plan(RowArgs<T>& a, int B, bool bins, dim3* grid, size_t* smem, int* nparts) {
   constexpr int NU = RowShape<L>::NU;
   const bool sbase = a.epi.mode == EPI_AMP && a.epi.base != nullptr;
-  int nhist;
   if (a.pm == 1) {
     a.n_units = (B + 1) / 2;
     *grid = dim3((a.n_units + NU - 1) / NU, 1);  // one group per CTA: histograms per sample
-    nhist = 2 * NU;
     *nparts = 1;
-  } else {
-    nhist = 1;
   }
   a.nU = NU;
   const int pm = a.pm;
   const int ek = pm == 1 ? SK_GEN : epi_kind(a.epi);
   const bool bstaged = sbase && !row_direct_base(RowShape<L>::NT, pm, ek, sizeof(T), L);
-  *smem = pm == 1   ? RowSmem<T, L, 1>::bytes(bstaged, a.nb, bins ? nhist * a.nb : 0)
-          : pm == 2 ? RowSmem<T, L, 2>::bytes(bstaged, a.nb, bins ? a.nb : 0)
-                    : RowSmem<T, L, 3>::bytes(bstaged, a.nb, bins ? a.nb : 0);
+  const int hreg = RowShape<L>::hist_regions(pm);  // warp-private bin histograms
+  *smem = pm == 1   ? RowSmem<T, L, 1>::bytes(bstaged, a.nb, bins ? hreg * a.nb : 0)
+          : pm == 2 ? RowSmem<T, L, 2>::bytes(bstaged, a.nb, bins ? hreg * a.nb : 0)
+                    : RowSmem<T, L, 3>::bytes(bstaged, a.nb, bins ? hreg * a.nb : 0);
   if (pm != 1) {
     const int gx = persistent_gx((a.n_units + NU - 1) / NU, B,
                                  resident_ctas(row_min_ctas(RowShape<L>::NT, pm, ek, sizeof(T), L), *smem));
@@ -104,7 +101,7 @@ int row_reg_plan(RowArgs<T>& a, int B, bool bins, dim3* grid, size_t* smem, int*
 template <typename T, int L>
 int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_t st, int64_t N) {
   constexpr int NT = ColShape<L, sizeof(T)>::NT;
-  const size_t smem = ColSmem<T, L>::bytes(a.nb, bins ? a.nb : 0);
+  const size_t smem = ColSmem<T, L>::bytes(a.nb, bins ? (NT / 32) * a.nb : 0);  // warp-private histograms
   const int gx = persistent_gx(a.n_units, B, resident_ctas(col_min_ctas(NT, sizeof(T)), smem));
   *nparts = gx;
   if (smem > 200 * 1024) return set_error(NRE_EINVAL, "column sweep of length %d needs %zu bytes of shared memory", L, smem);

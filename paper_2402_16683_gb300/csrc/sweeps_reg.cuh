@@ -23,8 +23,9 @@
 // The threads of one line synchronise with warp or named barriers only.
 // Per-bin amplitude tables (A and the tangent's dA) of the CTA's sample sit in
 // shared memory; only the int16 bin index is read per pixel.  Log-|k| bin sums
-// of the epilogue are reduced over runs of equal bins within each warp before
-// one shared-memory atomic per run.
+// of the epilogue are reduced over runs of equal bins within each warp and
+// added to the warp's own histogram (no atomics); the CTA folds its warps'
+// histograms in order into one FP64 partial per sample (fold_bins).
 #pragma once
 
 #include "cf_internal.cuh"
@@ -37,6 +38,11 @@ struct RowShape {
   static constexpr int T8 = L / 8;
   static constexpr int NT = T8 > 256 ? T8 : 256;
   static constexpr int NU = NT / T8;  // units per CTA iteration
+  static constexpr int NW = NT / 32;  // warps
+  // Warp-private bin histograms (regions of nb entries): D >= 2 one per warp;
+  // D = 1 two per unit (one per sample of the pair) while a unit fits in one
+  // warp, else two per warp (the unit's warps fold theirs in order).
+  __host__ __device__ static constexpr int hist_regions(int pm) { return pm == 1 ? (T8 <= 32 ? 2 * NU : 2 * NW) : NW; }
 };
 
 // Column tiles: NL complex lines (2 NL grid columns) per CTA.  FP32 tiles of
@@ -164,9 +170,15 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   const int nbp = (a.nb + 3) / 4 * 4;
   T* sA = bstage + (bstaged ? SM::XSZ : 0);
   T* sdA = sA + nbp;
-  T* hist = sdA + nbp;  // per-bin sums of the CTA in T (FP32: see warp_run_add)
+  T* hist = sdA + nbp;  // warp-private per-bin sums in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
-  const int nhist = (PM == 1) ? 2 * NU : 1;
+  constexpr int NW = RowShape<L>::NW, WPU = T8 > 32 ? T8 / 32 : 1;  // warps, warps per unit
+  const int nhreg = RowShape<L>::hist_regions(PM);
+  const int warp = threadIdx.x >> 5;
+  // this warp's histogram: D >= 2 region `warp`; D = 1 with units inside one
+  // warp the regions 2u, 2u + 1 of its units (keys offset by 2u nb), else the
+  // two regions of the warp
+  T* whist = PM == 1 ? (T8 <= 32 ? hist : hist + warp * 2 * a.nb) : hist + warp * a.nb;
   const int bsample = (PM == 1) ? 0 : blockIdx.y;
   const Pro<T>& pro = a.pro;
   const Epi<T>& epi = a.epi;
@@ -176,7 +188,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   const T* stab = use_tab ? sA : nullptr;
   const T* stdA = use_dA ? sdA : nullptr;
   if (bins)
-    for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) hist[i] = T(0);
+    for (int i = threadIdx.x; i < nhreg * a.nb; i += blockDim.x) hist[i] = T(0);
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
 
@@ -313,8 +325,10 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
         const int x = t + T8 * s;
         T ha[2], hb[2];
         hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
-        const T w = a.mid.w[x];
-        v[0][s] = cmake<C>(w * ha[0], w * hb[0]);
+        // samples of the pair (clamped into the batch: lanes of a missing
+        // sample carry zeros)
+        const int sa = samp[0] < a.B ? samp[0] : a.B - 1, sb = samp[1] < a.B ? samp[1] : a.B - 1;
+        v[0][s] = cmake<C>(a.mid.at(sa, x) * ha[0], a.mid.at(sb, x) * hb[0]);
       }
       reg_fft<C, L, LPU>(v, smc, tw, t, sync);
     }
@@ -391,7 +405,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
             c[sl] = xv[s][sl] * val[s][sl];
             kb[sl] = b_;
           }
-          add_slots<SLOTS, T>(kb, c, hist);  // the TAB epilogue always sums the bins
+          add_slots<SLOTS, T>(kb, c, whist);  // the TAB epilogue always sums the bins
         }
       }
       if (dot) dacc.add(dsum);
@@ -425,9 +439,10 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
         if (sval[0]) put(samp[0], 0, x, ha[0], sbase ? BV[x] : T(0), bn[0], c[0]);
         if (sval[1]) put(samp[1], 0, x, hb[0], sbase ? BV[L + x] : T(0), bn[1], c[1]);
         if (bins) {
-          warp_run_add(bn[0] >= 0 ? (2 * u) * a.nb + bn[0] : -1, c[0], hist);
+          const int ub = T8 <= 32 ? 2 * u : 0;  // the unit's regions within whist
+          warp_run_add(bn[0] >= 0 ? ub * a.nb + bn[0] : -1, c[0], whist);
           if (__any_sync(0xffffffffu, bn[1] >= 0))
-            warp_run_add(bn[1] >= 0 ? (2 * u + 1) * a.nb + bn[1] : -1, c[1], hist);
+            warp_run_add(bn[1] >= 0 ? (ub + 1) * a.nb + bn[1] : -1, c[1], whist);
         }
       } else if (PM == 2) {
         T R[2][2];
@@ -441,7 +456,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
           const T val = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
           if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
         }
-        if (bins) add_slots<2, T>(bn, c, hist);
+        if (bins) add_slots<2, T>(bn, c, whist);
       } else {
         T R[4][2];
         hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
@@ -457,7 +472,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
                                 pick4(R, sl, f0, f1, 1));
           if (valid) put(bsample, row[sl], x, val, sbase ? BV[sl * L + x] : T(0), bn[sl], c[sl]);
         }
-        if (bins) add_slots<4, T>(bn, c, hist);
+        if (bins) add_slots<4, T>(bn, c, whist);
       }
     }
     if (dot) dacc.add(dsum);
@@ -475,13 +490,21 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   if (bins) {
     __syncthreads();
     if (PM == 1) {
-      for (int i = threadIdx.x; i < nhist * a.nb; i += blockDim.x) {
-        const int hs = i / a.nb, bn = i - hs * a.nb;
+      // one CTA holds every pixel of its sample pairs: complete sums
+      for (int i = threadIdx.x; i < 2 * NU * a.nb; i += blockDim.x) {
+        const int hs = i / a.nb, bn = i - hs * a.nb;  // hs = 2 (unit) + slot
         const int sample = 2 * (blockIdx.x * NU) + hs;
-        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = hist[i];
+        double tot;
+        if (T8 <= 32) {
+          tot = double(hist[i]);
+        } else {
+          tot = 0.0;
+          for (int w = 0; w < WPU; ++w) tot += double(hist[((hs >> 1) * WPU + w) * 2 * a.nb + (hs & 1) * a.nb + bn]);
+        }
+        if (sample < a.B) (a.epi.gsum ? a.epi.gsum : a.partials)[(int64_t)sample * a.nb + bn] = tot;
       }
     } else {
-      store_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, a.nb);
+      fold_bins(a.epi, a.partials, bsample, gridDim.x, blockIdx.x, hist, NW, a.nb, a.nb);
     }
   }
 }
@@ -515,8 +538,10 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
   C* lines_own = reinterpret_cast<C*>(xin + 2 * SM::XS);  // used when !SM::ALIAS
   T* sA = xin + 2 * SM::XS + (SM::ALIAS ? 0 : SM::LNSZ);
   T* sdA = sA + nbp;
-  T* hist = sdA + nbp;  // per-bin sums of the CTA in T (FP32: see warp_run_add)
+  T* hist = sdA + nbp;  // warp-private per-bin sums in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
+  constexpr int NW = ColShape<L, sizeof(T)>::NT / 32;
+  T* whist = hist + (threadIdx.x >> 5) * a.nb;
   const int b = blockIdx.y;
   const Pro<T>& pro = a.pro;
   const Epi<T>& epi = a.epi;
@@ -526,7 +551,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
   const T* stab = use_tab ? sA : nullptr;
   const T* stdA = use_dA ? sdA : nullptr;
   if (bins)
-    for (int i = threadIdx.x; i < a.nb; i += blockDim.x) hist[i] = T(0);
+    for (int i = threadIdx.x; i < NW * a.nb; i += blockDim.x) hist[i] = T(0);
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
   const LineSync<T8> sync{1 + u};
   // W, the chunks per tile row and the tiles per outer index are powers of two:
@@ -587,7 +612,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
         T ha[2], hb[2];
         hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
         const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
-        v[0][s] = lval ? a.mid.apply2(flat, ha[0], hb[0]) : cmake<C>(T(0), T(0));
+        v[0][s] = lval ? a.mid.apply2(b, flat, ha[0], hb[0]) : cmake<C>(T(0), T(0));
       }
       reg_fft<C, L, 1>(v, smc, tw, t, sync);
     }
@@ -618,7 +643,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
           if (act)
             epi.store_b(b, flat + e, src[e],
                         (epi.mode == EPI_AMP && epi.base) ? epi.base[b * epi.bs + flat + e] : T(0), bn, cc, stab);
-          if (bins) warp_run_add(bn, cc, hist);
+          if (bins) warp_run_add(bn, cc, whist);
         }
       }
     }
@@ -627,7 +652,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
   cp_wait<0>();
   if (bins) {
     __syncthreads();
-    store_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, a.nb);
+    fold_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, NW, a.nb, a.nb);
   }
 }
 

@@ -21,6 +21,13 @@ def cf_pair(shape, kind, dtype, n_bins=256, prior=None, spacing=None):
     if kind == "matern":
         plan = nre.CorrelatedField(shape, sp, amplitude="matern", matern=synth.FIXED_1D, dtype=tdtype(dtype))
         om = CFModel(shape, sp, fixed_amp=matern_fixed_amplitude(shape, sp, **synth.FIXED_1D))
+    elif kind == "matern_model":
+        pr = dict(synth.MATERN_PRIOR)
+        pr["n_bins"] = n_bins
+        if prior:
+            pr.update(prior)
+        plan = nre.CorrelatedField(shape, sp, amplitude="matern_model", prior=pr, dtype=tdtype(dtype))
+        om = CFModel(shape, sp, prior=oamp.MaternPrior(**pr))
     else:
         pr = dict(synth.AMP_PRIOR)
         pr["n_bins"] = n_bins

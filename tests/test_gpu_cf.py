@@ -37,6 +37,13 @@ CASES = [
     ((2048, 16), "power", "f32", 256),
     ((8, 1024), "matern", "f32", 256),
     ((512, 8), "power", "f32", 256),
+    # the parametric Matern amplitude (three hyper-parameters on the log-|k| bins)
+    ((256,), "matern_model", "f64", 64),
+    ((32, 16), "matern_model", "f64", 256),
+    ((8, 16, 32), "matern_model", "f64", 32),
+    ((4096,), "matern_model", "f32", 256),
+    ((128, 256), "matern_model", "f32", 256),
+    ((32, 32, 64), "matern_model", "f32", 256),
 ]
 
 
