@@ -33,6 +33,9 @@ of it listed per function:
 * ``kl``         - the KL energy of MGVI for fixed residual samples, its
                    gradient, the sample-averaged metric and Newton-CG
                    (Sec. "Variational Inference", the minimiser "M").
+* ``geovi``      - the geoVI nonlinear update of a sample residual: Newton
+                   iterations on the coordinate equation of the likelihood's
+                   standardising transform (Sec. "Variational Inference", "SN").
 
 It shares no code with ``paper_2402_16683_gb300`` and imports nothing from it.
 """
