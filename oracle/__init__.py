@@ -30,6 +30,8 @@ of it listed per function:
                    (Sec. "Variational Inference", ``draw_linear_kwargs``).
 * ``icr``        - iterative charted refinement on a 2-D log-radial chart
                    (Sec. "Gaussian Processes", ICR paragraph).
+* ``icr3``       - iterative charted refinement on a 3-D spherical log-radial
+                   chart (3x3x3 neighbourhoods, 2x2x2 children).
 * ``kl``         - the KL energy of MGVI for fixed residual samples, its
                    gradient, the sample-averaged metric and Newton-CG
                    (Sec. "Variational Inference", the minimiser "M").
