@@ -69,7 +69,10 @@ class KLProblem:
     def weight(self, cf):
         if self.lik[0] == "poisson":
             return poisson_weight(cf, self.lik[1])
-        return gaussian_weight(cf, self.lik[1], mask=self.lik[2], response=self.lik[3])
+        mask = self.lik[2]
+        if mask is not None:
+            mask = np.asarray(mask, dtype=np.float64).reshape(cf.shape)
+        return gaussian_weight(cf, self.lik[1], mask=mask, response=self.lik[3])
 
     # KL ---------------------------------------------------------------------
     def points(self, xi_bar):

@@ -72,8 +72,11 @@ def _linear_gauss(seed=5):
     return p, A, mask, data, g
 
 
-def test_metric_is_exact_hessian_of_linear_gaussian():
+@pytest.mark.parametrize("flat_mask", [False, True])
+def test_metric_is_exact_hessian_of_linear_gaussian(flat_mask):
     p, A, mask, data, g = _linear_gauss()
+    if flat_mask:  # a per-pixel mask given in flat (C) order
+        p = KLProblem(p.model, ("gauss", 0.25, mask.ravel(), "identity"), data.ravel(), p.deltas)
     xb = g.standard_normal(p.model.latent_size)
     for _ in range(3):
         v = g.standard_normal(p.model.latent_size)
