@@ -171,7 +171,17 @@ int cf_bin_map(int ndim, const int64_t *shape, const double *spacing,
  * Latent layout: xi_0, ..., xi_L (each n_l x n_l, C order), then padding to
  * `stride`.  Output: the finest level, n_L x n_L.
  */
-typedef struct { int n0; double r_min, r_max; } icr_chart_params;
+/* ndim 0 or 2: the 2-D log-radial chart above.  ndim 3: a spherical
+ * log-radial chart (a reading of the paper's 3-D setting): level l has
+ * n_l = n0 2^l points per axis at (u, v, t) = ((i,j,k) + 1/2) / n_l, radius
+ * r = r_min (r_max/r_min)^u, polar angle pi v, azimuth 2 pi t; each coarse
+ * voxel's 3x3x3 neighbourhood (radial and polar windows clamped to the chart,
+ * azimuth periodic, order 9a + 3b + c) predicts its 2x2x2 children (order
+ * 4a + 2b + c) with R = K_fc K_cc^-1 (8 x 27) and chol(K_ff - R K_cf), per
+ * (level, radial row, polar row); level 0 is chol(K0) over the n0^3 points.
+ * Latent: xi_0, ..., xi_L, each n_l^3 in C order; output the finest level.
+ * 3-D limits: n0 in [3, 8], n0 2^n_levels <= 512. */
+typedef struct { int n0; double r_min, r_max; int ndim; } icr_chart_params;
 typedef struct { double rho, var; } icr_kernel_params;
 typedef struct nre_icr_plan nre_icr_plan;
 
@@ -276,6 +286,79 @@ int cg_solve_refined(nre_metric *m_lo, nre_metric *m_hi, const void *b, void *x,
                      int inner_maxiter, int *iters_out, double *relres_out,
                      int *outer_out, nre_stream_t stream);
 
+/* Sec. "Variational Inference": the geoVI nonlinear update of sample
+ * residuals (the example's minimiser "SN": xtol, maxiter = 5).  Reading used
+ * here: with t the likelihood's standardising transform (Gaussian
+ * t = sqrt(mask) R(cf) / sigma, Poisson t = 2 sqrt(lambda)) and J_p the
+ * Jacobian of xi -> t(cf(xi)) at the metric's expansion point p, each residual
+ * delta[b] solves
+ *     F(delta) = delta + J_p^T [t(cf(p + delta)) - t(cf(p))] - b = 0
+ * by Newton iterations delta <- delta - M_p^-1 F(delta) (cg_solve on m with its
+ * preconditioner, to cg_rtol / cg_maxiter), until mean_i |step_i| <= xtol for
+ * every system or maxiter iterations.  delta: [batch][stride], on entry the
+ * starting residuals (usually the linear ones, M_p^-1 b), on exit the updated
+ * ones; b: [batch][stride] (for the antithetic partner pass -b).  HOST outputs
+ * (may be NULL): iters_out[batch] (first iteration whose step met xtol, else
+ * the iterations run), step_out[batch] (the last mean |step|).  m must be a
+ * correlated-field metric. */
+int geovi_update(nre_metric *m, const void *b, void *delta, int batch,
+                 double xtol, int maxiter, double cg_rtol, int cg_maxiter,
+                 int *iters_out, double *step_out, nre_stream_t stream);
+
+/* ============================================================ KL minimisation
+ * Sec. "Variational Inference": MGVI alternates between drawing samples and
+ * minimising the KL divergence; the example's KL minimiser "M" is a Newton-CG
+ * (kl_kwargs: xtol, maxiter = 35).  Reading used here, for a correlated-field
+ * plan, a likelihood and its data:
+ *   samples xi_s = xi_bar + delta_s (s < n_samples) with the residual samples
+ *   delta_s held fixed (e.g. the antithetic pairs +-M^-1 b of the linear draw);
+ *   E(xi_bar) = (1/S) sum_s [NLL(d | cf(xi_s)) + |xi_s|^2 / 2] with
+ *     Poisson NLL = sum lambda - d ln lambda (lambda = scale exp(cf)),
+ *     Gaussian NLL = sum mask (d - R(cf))^2 / (2 sigma^2);
+ *   grad E = (1/S) sum_s [xi_s + J_s^T dNLL/dcf(xi_s)];
+ *   Newton curvature: Mbar = I + (1/S) sum_s J_s^T W_s J_s (Fisher weights at
+ *   each xi_s);
+ *   one Newton-CG step: D = -Mbar^-1 grad E by cg_solve on Mbar, backtracking
+ *   line search (alpha = 1, halved while E does not decrease, at most 30
+ *   times; no decrease: the position stays and the step is 0), xi_bar +=
+ *   alpha D;  kl_minimize stops once mean_i |alpha D_i| <= xtol or after
+ *   maxiter steps.
+ * Energies are FP64 sums; vectors are in the plan's dtype.
+ */
+typedef struct nre_kl nre_kl;
+/* data: HOST doubles [n_data = N] (counts or observations, harmonic grid order
+ * of the model output); deltas: DEVICE [n_samples][stride] in the plan dtype
+ * (copied).  The plan and likelihood must outlive the KL object. */
+int kl_create(nre_kl **kl, nre_cf_plan *plan, const nre_lik *lik,
+              const double *data, int64_t n_data, const void *deltas,
+              int n_samples, nre_stream_t stream);
+int kl_destroy(nre_kl *kl);
+/* Move to xi_bar (device [stride]): the points, their Fisher weights and
+ * amplitude states, the energy (*energy, host, may be NULL) and the gradient. */
+int kl_set_position(nre_kl *kl, const void *xi_bar, double *energy,
+                    nre_stream_t stream);
+/* Energy (host) and gradient (device [stride], may be NULL) at the position. */
+int kl_energy_gradient(nre_kl *kl, double *energy, void *grad,
+                       nre_stream_t stream);
+/* Energy (host) at xi (device [stride]); the position does not change. */
+int kl_energy_at(nre_kl *kl, const void *xi, double *energy,
+                 nre_stream_t stream);
+/* Mbar at the position as a metric object for metric_apply / cg_solve
+ * (max_batch 1, no preconditioner, no mgvi_rhs).  Owned by the KL object:
+ * metric_destroy refuses it. */
+int kl_metric(nre_kl *kl, nre_metric **metric);
+/* Copy of the position (device [stride]). */
+int kl_position(nre_kl *kl, void *xi_bar, nre_stream_t stream);
+/* One Newton-CG step (inner CG to cg_rtol / cg_maxiter); host outputs (may be
+ * NULL): mean |alpha D|, the new energy, the inner CG iterations. */
+int kl_newton_step(nre_kl *kl, double cg_rtol, int cg_maxiter,
+                   double *mean_abs_step, double *energy, int *cg_iters,
+                   nre_stream_t stream);
+/* Newton-CG steps until mean |step| <= xtol or maxiter steps. */
+int kl_minimize(nre_kl *kl, double xtol, int maxiter, double cg_rtol,
+                int cg_maxiter, int *iters, double *energy,
+                nre_stream_t stream);
+
 /* ================================================================ tracing
  * Launch accounting for measurement tools.  nre_launch_count() counts every
  * kernel launch the library has issued in this process.  While tracing is
@@ -363,13 +446,25 @@ typedef struct {
   const void *eta;           /* NULL, or [n_samples][N] data-space draws:
                                 the right-hand sides become the MGVI
                                 b = xi' + J^T (sqrt(w) eta)                 */
-  void *x_out;               /* [n_samples][latent] solutions               */
+  void *x_out;               /* [n_samples][latent] solutions (unused, may
+                                be NULL, when refine > 0)                   */
+  /* Residual correction to a TRUE relative residual (FP32 servers only; see
+   * cg_solve_refined): refine > 0 allows that many passes after the first
+   * solve.  The slot object then also holds an FP64 plan and metric at the
+   * same expansion point; each pass takes the FP64 residual b - M64 x and,
+   * while a system is above rtol, solves for its correction with the FP32
+   * CG to a relative 1e-2.  x64_out: HOST doubles [n_samples][latent], the
+   * FP64 solutions; the result's relres are the true residuals and iters
+   * the CG iterations of all passes. */
+  int refine;
+  void *x64_out;
 } nre_serve_req;
 
 typedef struct {
   int status;                /* NRE_OK, NRE_ENOTCONV or the error of the solve */
   int iters[64];             /* CG iterations per sample                    */
-  double relres[64];         /* recursive ||r|| / ||b|| per sample          */
+  double relres[64];         /* recursive ||r|| / ||b|| per sample (refine:
+                                the true FP64 residual)                     */
   double t_submit, t_start, t_done; /* CLOCK_MONOTONIC seconds: submit,
                                 admission, result copied to x_out           */
   uint64_t device_bytes;     /* footprint charged against the budget        */

@@ -43,7 +43,7 @@ class CFAmpParams(C.Structure):
 
 
 class ICRChartParams(C.Structure):
-    _fields_ = [("n0", C.c_int), ("r_min", C.c_double), ("r_max", C.c_double)]
+    _fields_ = [("n0", C.c_int), ("r_min", C.c_double), ("r_max", C.c_double), ("ndim", C.c_int)]
 
 
 class ICRKernelParams(C.Structure):
@@ -60,7 +60,8 @@ class ServeReq(C.Structure):
                 ("lik_kind", C.c_int), ("response", C.c_int), ("sigma_or_scale", C.c_double),
                 ("precond", C.c_int),
                 ("n_samples", C.c_int), ("rtol", C.c_double), ("maxiter", C.c_int),
-                ("xi_p", C.c_void_p), ("b", C.c_void_p), ("eta", C.c_void_p), ("x_out", C.c_void_p)]
+                ("xi_p", C.c_void_p), ("b", C.c_void_p), ("eta", C.c_void_p), ("x_out", C.c_void_p),
+                ("refine", C.c_int), ("x64_out", C.c_void_p)]
 
 
 class ServeResult(C.Structure):
@@ -106,6 +107,18 @@ SIGNATURES = {
     "cg_solve": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
                  C.POINTER(C.c_double), _P],
     "metric_set_precond": [_P, C.c_int, _P],
+    "geovi_update": [_P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int),
+                     C.POINTER(C.c_double), _P],
+    "kl_create": [C.POINTER(_P), _P, _P, C.POINTER(C.c_double), C.c_int64, _P, C.c_int, _P],
+    "kl_destroy": [_P],
+    "kl_set_position": [_P, _P, C.POINTER(C.c_double), _P],
+    "kl_energy_gradient": [_P, C.POINTER(C.c_double), _P, _P],
+    "kl_energy_at": [_P, _P, C.POINTER(C.c_double), _P],
+    "kl_metric": [_P, C.POINTER(_P)],
+    "kl_position": [_P, _P, _P],
+    "kl_newton_step": [_P, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                       C.POINTER(C.c_int), _P],
+    "kl_minimize": [_P, C.c_double, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), _P],
     "cg_solve_refined": [_P, _P, _P, _P, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
                          C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), _P],
     "nre_device_bytes": [_I64P],

@@ -161,12 +161,14 @@ class CorrelatedField:
 
 
 class ICR:
-    """Iterative-charted-refinement plan (icr_create) on the log-radial chart."""
+    """Iterative-charted-refinement plan (icr_create): ndim 2 on the log-radial
+    chart, ndim 3 on the spherical log-radial chart."""
 
-    def __init__(self, n0=8, n_levels=7, r_min=0.1, r_max=1.0, rho=0.1, var=1.0, dtype=torch.float32):
+    def __init__(self, n0=8, n_levels=7, r_min=0.1, r_max=1.0, rho=0.1, var=1.0, dtype=torch.float32, ndim=2):
         lib = L.load()
         self.dtype = dtype
-        ch = L.ICRChartParams(n0, r_min, r_max)
+        self.ndim = ndim
+        ch = L.ICRChartParams(n0, r_min, r_max, ndim)
         kp = L.ICRKernelParams(rho, var)
         h = C.c_void_p()
         check(lib.icr_create(C.byref(h), C.byref(ch), C.byref(kp), n_levels, _DT[dtype]))
@@ -277,7 +279,7 @@ class Metric:
         self.max_batch = max_batch
 
     def __del__(self):
-        if getattr(self, "handle", None) and L._lib is not None:
+        if getattr(self, "handle", None) and L._lib is not None and not getattr(self, "_owner", None):
             L._lib.metric_destroy(self.handle)
             self.handle = None
 
@@ -317,6 +319,18 @@ class Metric:
             check(st)
         return x, list(it), list(rr), st
 
+    def geovi_update(self, b, delta, xtol=1e-4, maxiter=5, cg_rtol=1e-5, cg_maxiter=500):
+        """geoVI nonlinear update of the residuals delta ([B, stride], updated in
+        place) for right-hand sides b.  Returns (iterations[B], last mean |step|[B])."""
+        B = b.shape[0]
+        _need(b, self.model.dtype, (B, self.model.stride), "b")
+        _need(delta, self.model.dtype, (B, self.model.stride), "delta")
+        it = (C.c_int * B)()
+        st = (C.c_double * B)()
+        check(L.load().geovi_update(self.handle, _ptr(b), _ptr(delta), B, float(xtol), int(maxiter), float(cg_rtol),
+                                    int(cg_maxiter), it, st, _stream()))
+        return list(it), list(st)
+
     def cg_refined(self, hi, b, rtol=1e-5, max_outer=6, inner_rtol=1e-3, inner_maxiter=1000, x=None,
                    raise_on_notconv=False):
         """cg_solve_refined: solve to a true relative residual rtol of the FP64
@@ -335,6 +349,74 @@ class Metric:
         if st != L.NRE_OK and (st != L.NRE_ENOTCONV or raise_on_notconv):
             check(st)
         return x, list(it), list(rr), outer.value, st
+
+
+class KL:
+    """kl_create: the MGVI KL energy of a correlated field for fixed residual
+    samples (deltas: [S, stride] tensor), its gradient, the sample-averaged
+    metric and Newton-CG steps.  data: host array of the N observations."""
+
+    def __init__(self, model, lik, data, deltas):
+        lib = L.load()
+        self.model, self.lik = model, lik
+        self._data = np.ascontiguousarray(np.asarray(data, dtype=np.float64).ravel())
+        S = deltas.shape[0]
+        _need(deltas, model.dtype, (S, model.stride), "deltas")
+        h = C.c_void_p()
+        check(lib.kl_create(C.byref(h), model.handle, lik.handle, self._data.ctypes.data_as(C.POINTER(C.c_double)),
+                            self._data.size, _ptr(deltas), S, _stream()))
+        self.handle = h
+        self.n_samples = S
+
+    def __del__(self):
+        if getattr(self, "handle", None) and L._lib is not None:
+            L._lib.kl_destroy(self.handle)
+            self.handle = None
+
+    def set_position(self, xi_bar):
+        _need(xi_bar, self.model.dtype, (self.model.stride,), "xi_bar")
+        e = C.c_double()
+        check(L.load().kl_set_position(self.handle, _ptr(xi_bar), C.byref(e), _stream()))
+        return e.value
+
+    def energy_gradient(self):
+        e = C.c_double()
+        g = torch.zeros(self.model.stride, dtype=self.model.dtype, device="cuda")
+        check(L.load().kl_energy_gradient(self.handle, C.byref(e), _ptr(g), _stream()))
+        return e.value, g
+
+    def energy_at(self, xi):
+        _need(xi, self.model.dtype, (self.model.stride,), "xi")
+        e = C.c_double()
+        check(L.load().kl_energy_at(self.handle, _ptr(xi), C.byref(e), _stream()))
+        return e.value
+
+    def metric(self):
+        """The sample-averaged metric at the position (a Metric owned by this KL)."""
+        h = C.c_void_p()
+        check(L.load().kl_metric(self.handle, C.byref(h)))
+        m = Metric.__new__(Metric)
+        m.model, m.lik, m.handle, m.max_batch, m._owner = self.model, self.lik, h, 1, self
+        return m
+
+    def position(self):
+        x = torch.zeros(self.model.stride, dtype=self.model.dtype, device="cuda")
+        check(L.load().kl_position(self.handle, _ptr(x), _stream()))
+        return x
+
+    def newton_step(self, cg_rtol=1e-3, cg_maxiter=200):
+        """One Newton-CG step: (mean |step|, energy, inner CG iterations)."""
+        st, e, it = C.c_double(), C.c_double(), C.c_int()
+        check(L.load().kl_newton_step(self.handle, float(cg_rtol), int(cg_maxiter), C.byref(st), C.byref(e),
+                                      C.byref(it), _stream()))
+        return st.value, e.value, it.value
+
+    def minimize(self, xtol=1e-4, maxiter=35, cg_rtol=1e-3, cg_maxiter=200):
+        """Newton-CG until mean |step| <= xtol: (iterations, energy)."""
+        it, e = C.c_int(), C.c_double()
+        check(L.load().kl_minimize(self.handle, float(xtol), int(maxiter), float(cg_rtol), int(cg_maxiter),
+                                   C.byref(it), C.byref(e), _stream()))
+        return it.value, e.value
 
 
 def _host_ptr(a, dtype, n, name):
@@ -370,7 +452,7 @@ class Server:
         self._keep = {}
 
     def _request(self, shape, xi_p, b, x_out, lik, sigma, scale, amplitude, prior, matern, precond,
-                 rtol, maxiter, eta, n_samples, check_arrays=True, response="exp"):
+                 rtol, maxiter, eta, n_samples, check_arrays=True, response="exp", refine=0, x64_out=None):
         r = L.ServeReq()
         r.ndim = len(shape)
         for d, n in enumerate(shape):
@@ -383,32 +465,38 @@ class Server:
         r.n_samples = int(n_samples)
         r.rtol = float(rtol)
         r.maxiter = int(maxiter)
+        r.refine = int(refine)
         if check_arrays:
             N = int(np.prod(shape))
-            lat = N + (4 + 2 * (r.amp.n_bins - 1) if r.amp.kind == L.NRE_AMP_POWER_MODEL else 0)
+            nh = {L.NRE_AMP_POWER_MODEL: 4 + 2 * (r.amp.n_bins - 1), L.NRE_AMP_MATERN_MODEL: 3}.get(r.amp.kind, 0)
+            lat = N + nh
             r.xi_p = _host_ptr(xi_p, self.dtype, lat, "xi_p")
             r.b = _host_ptr(b, self.dtype, n_samples * lat, "b")
-            r.x_out = _host_ptr(x_out, self.dtype, n_samples * lat, "x_out")
+            r.x_out = _host_ptr(x_out, self.dtype, n_samples * lat, "x_out") if x_out is not None else None
             r.eta = _host_ptr(eta, self.dtype, n_samples * N, "eta") if eta is not None else None
+            if refine:
+                r.x64_out = _host_ptr(x64_out, torch.float64, n_samples * lat, "x64_out")
         return r
 
     def submit(self, shape, xi_p, b, x_out, lik="gauss", sigma=0.1, scale=10.0, amplitude="power",
                prior=None, matern=None, precond="harmonic", rtol=1e-5, maxiter=1000, eta=None,
-               response="exp"):
-        """Queue one request (b: [n_samples, latent], x_out likewise); returns its id."""
+               response="exp", refine=0, x64_out=None):
+        """Queue one request (b: [n_samples, latent], x_out likewise); returns its id.
+        refine > 0: residual correction to a true rtol with up to that many
+        passes, the FP64 solutions in x64_out (x_out unused, may be None)."""
         n = int(np.prod(b.shape[:-1])) if len(b.shape) > 1 else 1
         r = self._request(shape, xi_p, b, x_out, lik, sigma, scale, amplitude, prior, matern, precond,
-                          rtol, maxiter, eta, n, response=response)
+                          rtol, maxiter, eta, n, response=response, refine=refine, x64_out=x64_out)
         rid = C.c_uint64()
         check(L.load().serve_submit(self.handle, C.byref(r), C.byref(rid)))
-        self._keep[rid.value] = (xi_p, b, x_out, eta)
+        self._keep[rid.value] = (xi_p, b, x_out, eta, x64_out)
         return rid.value
 
     def footprint(self, shape, n_samples=8, lik="gauss", amplitude="power", prior=None, matern=None,
-                  precond="harmonic", mgvi=False):
+                  precond="harmonic", mgvi=False, refine=0):
         """Device bytes a request of this kind is charged."""
         r = self._request(shape, None, None, None, lik, 0.1, 10.0, amplitude, prior, matern, precond, 1e-5,
-                          1, None, n_samples, check_arrays=False)
+                          1, None, n_samples, check_arrays=False, refine=refine)
         if mgvi:
             r.eta = 1
         out = C.c_uint64()

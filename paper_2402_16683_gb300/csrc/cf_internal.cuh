@@ -72,9 +72,11 @@ struct AmpView {
     if (stab != nullptr && mode != AMPV_FIXED) return bn < 0 ? a0t : stab[bn];
     return amp(b, flat, bn);
   }
+  // PIX without a per-pixel array (the KL's per-point views) reads the
+  // per-bin table of sample b through the per-pixel bins.
   __device__ __forceinline__ T amp(int b, int64_t flat, int bn) const {
     if (mode == AMPV_TAB) return bn < 0 ? a0t : tab[bn];
-    if (mode != AMPV_MODEL) return __ldg(&afull[flat]);
+    if (mode == AMPV_FIXED || (mode == AMPV_PIX && afull != nullptr)) return __ldg(&afull[flat]);
     return bn < 0 ? T(a0) : T(__ldg(&abin[b * astride + bn]));
   }
   __device__ __forceinline__ bool binned() const { return mode != AMPV_FIXED; }

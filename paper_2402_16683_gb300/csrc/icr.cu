@@ -23,29 +23,7 @@
 
 #include "metric_internal.cuh"
 
-struct nre_icr_plan {
-  int dtype = NRE_F32;
-  int n0 = 8, n_levels = 7;
-  double r_min = 0.1, r_max = 1.0, rho = 0.1, var = 1.0;
-  std::vector<int> sizes;        // n_l, l = 0..n_levels
-  std::vector<int64_t> offsets;  // latent offset of level l
-  int64_t latent = 0, stride = 0, n_out = 0;
-  nre::DevBuf L0;                // [n0^2][n0^2] lower (row-major), plan dtype
-  nre::DevBuf mats;              // per level: [n_l][52]: R (4x9 row-major), L (4x4 row-major)
-  std::vector<int64_t> mat_off;  // element offset of level l in mats
-  nre::DevBuf ws_a, ws_b, ws_c;  // per-batch level buffers
-  // second stream of a batch split into two halves (see icr_forward_t)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  nre_icr_plan() = default;
-  nre_icr_plan(const nre_icr_plan&) = delete;
-  nre_icr_plan& operator=(const nre_icr_plan&) = delete;
-  ~nre_icr_plan() {
-    if (side) cudaStreamDestroy(side);
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-  }
-};
+#include "icr_internal.cuh"
 
 namespace {
 
@@ -800,6 +778,7 @@ int icr_forward_range(nre_icr_plan* p, const T* xi, T* s, int b0, int B, const T
 // s = ICR(xi) (optionally times `scale`), batch B.
 template <typename T>
 int icr_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cudaStream_t st) {
+  if (p->ndim == 3) return nre::icr3_forward_t<T>(p, xi, s, B, scale, st);
   NRE_TRY(ensure_ws<T>(p, B));
   return icr_split(p, B, st, [&](int b0, int Bh, cudaStream_t sh) {
     return icr_forward_range<T>(p, xi, s, b0, Bh, scale, sh);
@@ -865,6 +844,7 @@ int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base
 // g = base + ICR^T ct, batch B (ct: [B][cts]).
 template <typename T>
 int icr_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, int B, cudaStream_t st) {
+  if (p->ndim == 3) return nre::icr3_vjp_t<T>(p, ct, cts, g, base, B, st);
   NRE_TRY(ensure_ws<T>(p, B));
   return icr_split(p, B, st, [&](int b0, int Bh, cudaStream_t sh) {
     return icr_vjp_range<T>(p, ct, cts, g, base, b0, Bh, sh);
@@ -953,6 +933,31 @@ int icr_create(nre_icr_plan** plan, const icr_chart_params* chart, const icr_ker
   clear_error();
   if (!plan || !chart || !kernel) return set_error(NRE_EINVAL, "NULL argument");
   *plan = nullptr;
+  if (chart->ndim != 0 && chart->ndim != 2 && chart->ndim != 3) return set_error(NRE_EINVAL, "ndim must be 2 or 3");
+  if (chart->ndim == 3) {
+    if (chart->n0 < 3 || chart->n0 > 8) return set_error(NRE_EINVAL, "3-D charts need n0 in [3, 8]");
+    if (n_levels < 1 || n_levels > 8) return set_error(NRE_EINVAL, "n_levels must be in [1, 8]");
+    if ((int64_t)chart->n0 << n_levels > 512) return set_error(NRE_EINVAL, "3-D charts need n0 * 2^n_levels <= 512");
+    if (!(chart->r_min > 0 && chart->r_max > chart->r_min)) return set_error(NRE_EINVAL, "need 0 < r_min < r_max");
+    if (!(kernel->rho > 0 && kernel->var > 0)) return set_error(NRE_EINVAL, "need rho > 0 and var > 0");
+    if (dtype != NRE_F32 && dtype != NRE_F64) return set_error(NRE_EINVAL, "dtype must be NRE_F32 or NRE_F64");
+    nre_icr_plan* p = new nre_icr_plan();
+    p->ndim = 3;
+    p->dtype = dtype;
+    p->n0 = chart->n0;
+    p->n_levels = n_levels;
+    p->r_min = chart->r_min;
+    p->r_max = chart->r_max;
+    p->rho = kernel->rho;
+    p->var = kernel->var;
+    const int s3 = nre::icr3_setup(p);
+    if (s3 != NRE_OK) {
+      delete p;
+      return s3;
+    }
+    *plan = p;
+    return NRE_OK;
+  }
   if (chart->n0 < 4 || chart->n0 > 64 || (chart->n0 & 1))
     return set_error(NRE_EINVAL, "n0 must be even and in [4, 64] (levels are read as 2-vectors)");
   if (n_levels < 1 || n_levels > 10) return set_error(NRE_EINVAL, "n_levels must be in [1, 10]");

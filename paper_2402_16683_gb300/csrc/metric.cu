@@ -263,6 +263,7 @@ int metric_relinearize(nre_metric* m, const void* xi_p, cudaStream_t st) {
 int metric_apply_impl(nre_metric* m, const void* v, void* out, int batch, cudaStream_t st, double* dot,
                       bool hyper_in_cg) {
   if (m->model_kind == NRE_MODEL_ICR) return icr_metric_apply(m, v, out, batch, st);
+  if (m->model_kind == NRE_MODEL_KL) return kl_metric_apply(m->kl, v, out, batch, st);
   if (m->dtype == NRE_F64)
     return cf_metric_apply<double>(m, (const double*)v, (double*)out, batch, st, dot, hyper_in_cg);
   return cf_metric_apply<float>(m, (const float*)v, (float*)out, batch, st, dot, hyper_in_cg);
@@ -359,6 +360,9 @@ int metric_create(nre_metric** out, int model_kind, void* model_plan, const nre_
 }
 
 int metric_destroy(nre_metric* m) {
+  clear_error();
+  if (m && m->model_kind == NRE_MODEL_KL)
+    return set_error(NRE_EINVAL, "this metric belongs to its KL object (kl_destroy releases it)");
   delete m;
   return NRE_OK;
 }
@@ -380,6 +384,7 @@ int mgvi_rhs(nre_metric* m, const void* xi_prime, const void* eta, void* b, int 
   if (batch == 0) return NRE_OK;
   if (!xi_prime || !eta || !b) return set_error(NRE_EINVAL, "NULL array argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (m->model_kind == NRE_MODEL_KL) return set_error(NRE_EINVAL, "mgvi_rhs needs the metric of one expansion point");
   if (m->model_kind == NRE_MODEL_ICR) return icr_mgvi_rhs(m, xi_prime, eta, b, batch, st);
   if (m->dtype == NRE_F64)
     return cf_mgvi_rhs<double>(m, (const double*)xi_prime, (const double*)eta, (double*)b, batch, st);

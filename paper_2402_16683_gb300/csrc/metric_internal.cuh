@@ -6,6 +6,11 @@
 #include "cf_internal.cuh"
 
 struct nre_icr_plan;
+struct nre_kl;
+
+// Model kind of the sample-averaged KL metric (kl.cu); internal: such metric
+// objects come from kl_metric and are owned by their KL object.
+constexpr int NRE_MODEL_KL = 2;
 
 struct nre_lik {
   int kind = NRE_LIK_GAUSS, response = NRE_RESP_EXP;
@@ -18,6 +23,7 @@ struct nre_metric {
   int model_kind = NRE_MODEL_CF;
   nre_cf_plan* cf = nullptr;
   nre_icr_plan* icr = nullptr;
+  nre_kl* kl = nullptr;  // NRE_MODEL_KL
   int dtype = NRE_F32;
   int max_batch = 1;
   int64_t n_data = 0, latent = 0, stride = 0;
@@ -54,6 +60,9 @@ struct nre_metric {
   // residual correction (refine.cu): FP64 metric: residual, product, partials;
   // low precision metric: right-hand side and correction of the inner solve
   nre::DevBuf rf_r, rf_q, rf_part;
+  // geoVI update (geovi.cu): p per system, shifted points, VJP output,
+  // coordinate residual, Newton step, model values, t(p) and dt(p), partials
+  nre::DevBuf gv_pp, gv_pts, gv_u, gv_F, gv_step, gv_cf, gv_tp, gv_part;
   // second stream of a metric product split into two half batches (metric.cu)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -87,6 +96,17 @@ int icr_metric_apply(nre_metric* m, const void* v, void* out, int batch, cudaStr
 int icr_mgvi_rhs(nre_metric* m, const void* xi_prime, const void* eta, void* b, int batch,
                  cudaStream_t st);
 int icr_layout(const nre_icr_plan* p, int64_t* n_out, int64_t* latent, int64_t* stride, int* dtype);
+// Residual correction in pieces (refine.cu), enqueue only: with d_lo (the
+// low precision correction of the last inner solve, lo->rf_q in cg_solve_refined)
+// x += d_lo first and the residual is r = b - M_hi x, else r = b; the sums
+// r.r (and with with_bb b.b) per system land in *sums ([B] then [B], device).
+// refine_down casts r of the systems flagged in active_host (host int[B]) to
+// lo's dtype into lo->rf_r (zeros for the others).
+int refine_residual(nre_metric* lo, nre_metric* hi, const double* b, double* x, const void* d_lo, int B,
+                    bool with_bb, double** sums, cudaStream_t st);
+int refine_down(nre_metric* lo, nre_metric* hi, int B, const int* active_host, void** rlo, cudaStream_t st);
+// The KL's sample-averaged metric (kl.cu): out[b] = Mbar v[b].
+int kl_metric_apply(nre_kl* k, const void* v, void* out, int batch, cudaStream_t st);
 // Preconditioned CG (pcg.cu), used by cg_solve when m->precond != NRE_PRECOND_NONE.
 int pcg_solve_impl(nre_metric* m, const void* b, void* x, int batch, double rtol, int maxiter,
                    int* iters_out, double* relres_out, cudaStream_t st);

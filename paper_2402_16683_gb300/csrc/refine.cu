@@ -79,42 +79,36 @@ __global__ void k_rf_up(double* x, const T* d, int64_t n, int64_t S) {
     x[off + i] += double(d[off + i]);
 }
 
+// Workspaces of a pass: FP64 residual, product and sums in the FP64 metric,
+// the low precision right-hand side and correction in the low one.
+int rf_ensure(nre_metric* lo, nre_metric* hi, int B) {
+  const int64_t S = hi->stride;
+  const int nblk = rf_blocks(hi->latent);
+  const size_t el = lo->dtype == NRE_F64 ? 8 : 4;
+  NRE_TRY(ensure(hi->rf_r, (size_t)B * S * sizeof(double)));
+  NRE_TRY(ensure(hi->rf_q, (size_t)B * S * sizeof(double)));
+  NRE_TRY(ensure(hi->rf_part, ((size_t)2 * B * nblk + 2 * B) * sizeof(double) + (size_t)B * sizeof(int)));
+  NRE_TRY(ensure(lo->rf_r, (size_t)B * S * el));
+  NRE_TRY(ensure(lo->rf_q, (size_t)B * S * el));
+  return NRE_OK;
+}
+
 template <typename T>
 int refined_t(nre_metric* lo, nre_metric* hi, const double* b, double* x, int B, double rtol, int max_outer,
               double inner_rtol, int inner_maxiter, int* iters_out, double* relres_out, int* outer_out,
               cudaStream_t st) {
-  const int64_t n = hi->latent, S = hi->stride;
-  const int nblk = rf_blocks(n);
-  // workspaces: FP64 residual and product in the FP64 metric, the low
-  // precision right-hand side and correction in the low precision metric
-  NRE_TRY(ensure(hi->rf_r, (size_t)B * S * sizeof(double)));
-  NRE_TRY(ensure(hi->rf_q, (size_t)B * S * sizeof(double)));
-  NRE_TRY(ensure(hi->rf_part, ((size_t)2 * B * nblk + 2 * B) * sizeof(double) + (size_t)B * sizeof(int)));
-  NRE_TRY(ensure(lo->rf_r, (size_t)B * S * sizeof(T)));
-  NRE_TRY(ensure(lo->rf_q, (size_t)B * S * sizeof(T)));
-  double* r = hi->rf_r.as<double>();
-  double* q = hi->rf_q.as<double>();
-  double* rr_part = hi->rf_part.as<double>();
-  double* bb_part = rr_part + (size_t)B * nblk;
-  double* sums = bb_part + (size_t)B * nblk;  // [B] rr, [B] bb
-  int* active = reinterpret_cast<int*>(sums + 2 * B);
+  const int64_t S = hi->stride;
+  NRE_TRY(rf_ensure(lo, hi, B));
   T* rlo = lo->rf_r.as<T>();
   T* dlo = lo->rf_q.as<T>();
   NRE_TRY_CUDA(cudaMemsetAsync(x, 0, (size_t)B * S * sizeof(double), st));
   NRE_TRY_CUDA(cudaMemsetAsync(rlo, 0, (size_t)B * S * sizeof(T), st));  // padding stays zero
   std::vector<double> hs(2 * B);
   std::vector<int> act(B, 1), its(B, 0);
-  const dim3 grid(nblk, B);
   int outer = 0;
   for (;; ++outer) {
-    if (outer > 0) NRE_TRY(metric_apply_impl(hi, x, q, B, st));
-    prof_begin("refine_residual", (double)B * n * (outer > 0 ? 24 : 16), st);
-    k_rf_residual<<<grid, RF_THREADS, 0, st>>>(b, outer > 0 ? q : nullptr, r, n, S, rr_part,
-                                               outer == 0 ? bb_part : nullptr);
-    k_rf_sum<<<(B + 127) / 128, 128, 0, st>>>(rr_part, nblk, B, sums);
-    if (outer == 0) k_rf_sum<<<(B + 127) / 128, 128, 0, st>>>(bb_part, nblk, B, sums + B);
-    prof_end(st);
-    NRE_CHECK_LAUNCH();
+    double* sums = nullptr;
+    NRE_TRY(refine_residual(lo, hi, b, x, outer > 0 ? dlo : nullptr, B, outer == 0, &sums, st));
     NRE_TRY_CUDA(cudaMemcpyAsync(hs.data(), sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, st));
     NRE_TRY_CUDA(cudaStreamSynchronize(st));
     bool any = false;
@@ -125,19 +119,11 @@ int refined_t(nre_metric* lo, nre_metric* hi, const double* b, double* x, int B,
       any = any || act[i];
     }
     if (!any || outer == max_outer) break;
-    NRE_TRY_CUDA(cudaMemcpyAsync(active, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    prof_begin("refine_down", (double)B * n * (8 + sizeof(T)), st);
-    k_rf_down<T><<<grid, RF_THREADS, 0, st>>>(r, rlo, n, S, active);
-    prof_end(st);
-    NRE_CHECK_LAUNCH();
+    NRE_TRY(refine_down(lo, hi, B, act.data(), nullptr, st));
     std::vector<int> inner(B, 0);
     const int s = cg_solve(lo, rlo, dlo, B, inner_rtol, inner_maxiter, inner.data(), nullptr, (nre_stream_t)st);
     if (s != NRE_OK && s != NRE_ENOTCONV) return s;
     for (int i = 0; i < B; ++i) its[i] += act[i] ? inner[i] : 0;
-    prof_begin("refine_update", (double)B * n * (16 + sizeof(T)), st);
-    k_rf_up<T><<<grid, RF_THREADS, 0, st>>>(x, dlo, n, S);
-    prof_end(st);
-    NRE_CHECK_LAUNCH();
   }
   clear_error();
   if (iters_out)
@@ -151,6 +137,52 @@ int refined_t(nre_metric* lo, nre_metric* hi, const double* b, double* x, int B,
 }
 
 }  // namespace
+
+namespace nre {
+int refine_residual(nre_metric* lo, nre_metric* hi, const double* b, double* x, const void* d_lo, int B,
+                    bool with_bb, double** sums_out, cudaStream_t st) {
+  const int64_t n = hi->latent, S = hi->stride;
+  const int nblk = rf_blocks(n);
+  NRE_TRY(rf_ensure(lo, hi, B));
+  double* r = hi->rf_r.as<double>();
+  double* q = hi->rf_q.as<double>();
+  double* rr_part = hi->rf_part.as<double>();
+  double* bb_part = rr_part + (size_t)B * nblk;
+  double* sums = bb_part + (size_t)B * nblk;  // [B] r.r, [B] b.b
+  const dim3 grid(nblk, B);
+  if (d_lo) {
+    prof_begin("refine_update", (double)B * n * (16 + (lo->dtype == NRE_F64 ? 8 : 4)), st);
+    if (lo->dtype == NRE_F64) k_rf_up<double><<<grid, RF_THREADS, 0, st>>>(x, (const double*)d_lo, n, S);
+    else k_rf_up<float><<<grid, RF_THREADS, 0, st>>>(x, (const float*)d_lo, n, S);
+    prof_end(st);
+    NRE_CHECK_LAUNCH();
+    NRE_TRY(metric_apply_impl(hi, x, q, B, st));
+  }
+  prof_begin("refine_residual", (double)B * n * (d_lo ? 24 : 16), st);
+  k_rf_residual<<<grid, RF_THREADS, 0, st>>>(b, d_lo ? q : nullptr, r, n, S, rr_part, with_bb ? bb_part : nullptr);
+  k_rf_sum<<<(B + 127) / 128, 128, 0, st>>>(rr_part, nblk, B, sums);
+  if (with_bb) k_rf_sum<<<(B + 127) / 128, 128, 0, st>>>(bb_part, nblk, B, sums + B);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  if (sums_out) *sums_out = sums;
+  return NRE_OK;
+}
+
+int refine_down(nre_metric* lo, nre_metric* hi, int B, const int* active_host, void** rlo_out, cudaStream_t st) {
+  const int64_t n = hi->latent, S = hi->stride;
+  const int nblk = rf_blocks(n);
+  int* active = reinterpret_cast<int*>(hi->rf_part.as<double>() + (size_t)2 * B * nblk + 2 * B);
+  NRE_TRY_CUDA(cudaMemcpyAsync(active, active_host, B * sizeof(int), cudaMemcpyHostToDevice, st));
+  const dim3 grid(nblk, B);
+  prof_begin("refine_down", (double)B * n * (8 + (lo->dtype == NRE_F64 ? 8 : 4)), st);
+  if (lo->dtype == NRE_F64) k_rf_down<double><<<grid, RF_THREADS, 0, st>>>(hi->rf_r.as<double>(), lo->rf_r.as<double>(), n, S, active);
+  else k_rf_down<float><<<grid, RF_THREADS, 0, st>>>(hi->rf_r.as<double>(), lo->rf_r.as<float>(), n, S, active);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
+  if (rlo_out) *rlo_out = lo->rf_r.p;
+  return NRE_OK;
+}
+}  // namespace nre
 
 extern "C" int cg_solve_refined(nre_metric* m_lo, nre_metric* m_hi, const void* b, void* x, int batch, double rtol,
                                 int max_outer, double inner_rtol, int inner_maxiter, int* iters_out,

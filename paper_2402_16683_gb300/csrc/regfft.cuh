@@ -212,10 +212,10 @@ __device__ __forceinline__ void reg_mirror(const C (&v)[LPT][8], C (&zm)[LPT][8]
 // maximal ranges of consecutive lanes with the same key) and add each run's
 // total to whist[key] from its last lane.  key < 0: no contribution.
 // whist is a histogram that only this warp writes (a warp-private region of
-// shared memory), so no atomics are needed and the result does not depend on
-// how warps or CTAs are scheduled: runs of the same key that are not adjacent
-// are added one after another in lane order (ranked with __match_any_sync),
-// and successive calls add in program order.  The caller folds the warps'
+// shared memory), so the result does not depend on how warps or CTAs are
+// scheduled: runs of the same key that are not adjacent are added one after
+// another in lane order (ranked with __match_any_sync), and successive calls
+// add in program order.  The caller folds the warps'
 // histograms in a fixed order (fold_bins).  The run sums are formed in V (the
 // plan's value type: FP32 products of FP32 data are summed over at most 32
 // lanes) and added to whist in H (FP32 for FP32 plans: an FP64 add and
@@ -238,22 +238,22 @@ __device__ __forceinline__ void warp_run_add(int key, V val, H* whist) {
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
   const bool act = tail && key >= 0;
-  __syncwarp();  // earlier calls' writes by other lanes are visible
+  // The adds are shared-memory atomics so that they need no read round trip;
+  // only this warp writes whist, in program order, so their order is fixed.
   // Keys monotone along the lanes (the sweeps' usual case: consecutive |k|)
   // give every run its own key, and the tails add at once.
   const bool mono = __all_sync(full, lane == 0 || prev <= key) || __all_sync(full, lane == 0 || prev >= key);
   if (mono) {
-    if (act) whist[key] += H(val);
+    if (act) atomicAdd(&whist[key], H(val));
   } else {
     // tails of other runs with the same key (inactive lanes get unique keys)
     const unsigned same = __match_any_sync(full, act ? key : -1 - lane);
     const int rank = __popc(same & ((1u << lane) - 1u));
     for (int r = 0; __any_sync(full, act && rank >= r); ++r) {
-      if (act && rank == r) whist[key] += H(val);
+      if (act && rank == r) atomicAdd(&whist[key], H(val));
       __syncwarp();
     }
   }
-  __syncwarp();
 }
 
 // Adds the contributions c[s] of slots with bins bn[s] (all into the same

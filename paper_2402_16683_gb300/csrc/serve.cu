@@ -21,7 +21,10 @@
 //   launcher   keeps every running request busy: when a request's previous
 //              chunk has finished (event query, no blocking), it reads the
 //              scalars copied to host memory by that chunk and either launches
-//              the next chunk or hands the request on;
+//              the next chunk or hands the request on; for requests with
+//              residual correction it enqueues the FP64 residual pass after a
+//              solve and, while a system is above rtol, restarts CG on the
+//              cast-down residual (refine.cu);
 //   completion copies x to the caller's buffer, records the result and
 //              returns the slot object to the idle pool.
 // The device runs the chunks of all running requests concurrently on their
@@ -115,6 +118,20 @@ uint64_t footprint(const nre_serve_req* r, const Geom& g, int dtype) {
   // slot buffers: xi_p, b, x (+ eta and the formed right-hand sides)
   b += a256(S * E) + 2 * a256(B * S * E);
   if (r->eta) b += a256(B * N * E) + a256(B * S * E);
+  if (r->refine > 0) {
+    // FP64 plan and metric (products only), xi_p / b / x in FP64, the
+    // correction workspaces of both metrics and the inner solves' graph
+    b += a256(16 * g.Lmax);
+    if (nb == 0) b += a256(N * 8);
+    else b += a256(2 * (size_t)(g.qmax + 1)) + 2 * a256(nb * 8);
+    b += 2 * a256(N / 2 * sizeof(int) + 16);
+    b += a256(S * 8) + a256(N * 8) + 2 * a256(B * N * 8);
+    if (nb > 0)
+      b += a256((size_t)amp_state_size((int)nb) * 8) + a256(B * nb * 8) + a256(B * 128 * nb * 8) + a256(N * 8) +
+           a256(N * 2);
+    b += a256(S * 8) + 2 * a256(B * S * 8);
+    b += 2 * a256(B * S * 8) + a256((2 * B * 64 + 2 * B) * 8 + B * 4) + 2 * a256(B * S * E);
+  }
   return (uint64_t)b + (1u << 20);
 }
 
@@ -124,10 +141,10 @@ struct Key {
   nre_cf_amp_params amp;
   int lik_kind, response;
   double sig;
-  int B, precond, mgvi;
+  int B, precond, mgvi, refine;
   bool operator==(const Key& o) const {
     if (ndim != o.ndim || lik_kind != o.lik_kind || response != o.response || sig != o.sig || B != o.B ||
-        precond != o.precond || mgvi != o.mgvi)
+        precond != o.precond || mgvi != o.mgvi || refine != o.refine)
       return false;
     for (int d = 0; d < ndim; ++d)
       if (shape[d] != o.shape[d]) return false;
@@ -150,6 +167,16 @@ struct SlotObj {
   nre_lik* lik = nullptr;
   nre_metric* m = nullptr;
   DevBuf dxi, db, dx, deta, drhs;
+  // residual correction: FP64 plan and metric, xi_p / b / x in FP64, the
+  // passes' sums on the host, the inner solves' chunk graph
+  nre_cf_plan* plan64 = nullptr;
+  nre_metric* m64 = nullptr;
+  DevBuf dxi64, db64, dx64;
+  double* h_rf = nullptr;  // page-locked [2 B]: r.r, b.b
+  cudaGraphExec_t gexec_in = nullptr;
+  double gin_rtol = -1.0;
+  int gin_chunk = 0;
+  unsigned long long gin_kernels = 0;
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
   double* h_sc = nullptr;  // page-locked [B][CG_SC_N]
@@ -160,6 +187,10 @@ struct SlotObj {
   uint64_t last_used = 0;
   ~SlotObj() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (gexec_in) cudaGraphExecDestroy(gexec_in);
+    if (m64) metric_destroy(m64);
+    if (plan64) cf_destroy(plan64);
+    if (h_rf) cudaFreeHost(h_rf);
     if (m) metric_destroy(m);
     if (lik) lik_destroy(lik);
     if (plan) cf_destroy(plan);
@@ -182,8 +213,17 @@ struct Job {
   bool so_broken = false;
   int iters_done = 0;
   bool inflight = false;
+  // residual correction: passes taken, a pass's residual in flight, the
+  // tolerance of the running solve (rtol, then the inner one)
+  int pass = 0;
+  bool rf_inflight = false;
+  double cur_rtol = 0.0;
+  int its_total[64] = {0};
   nre_serve_result res{};
 };
+
+// Relative tolerance of the CG solves for the corrections after the first.
+constexpr double kInnerRtol = 1e-2;
 
 }  // namespace
 
@@ -246,7 +286,32 @@ int make_slot(const Job* j, int dtype, SlotObj** out) {
     return bad(s);
   if (r.eta && ((s = so->deta.alloc(B * N * E)) != NRE_OK || (s = so->drhs.alloc(B * S * E)) != NRE_OK))
     return bad(s);
+  if (r.refine > 0) {
+    s = cf_create(&so->plan64, r.ndim, r.shape, spacing, &r.amp, NRE_F64);
+    if (s != NRE_OK) return bad(s);
+    if ((s = so->dxi64.alloc(S * 8)) != NRE_OK || (s = so->db64.alloc(B * S * 8)) != NRE_OK ||
+        (s = so->dx64.alloc(B * S * 8)) != NRE_OK)
+      return bad(s);
+    if (cudaHostAlloc((void**)&so->h_rf, 2 * B * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return bad(set_error(NRE_ECUDA, "host buffer creation failed"));
+    }
+  }
   *out = so;
+  return NRE_OK;
+}
+
+// FP32 -> FP64 copy of n entries.
+__global__ void k_widen(const float* src, double* dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = double(src[i]);
+}
+
+int widen(const void* src, void* dst, int64_t n, cudaStream_t st) {
+  prof_begin("serve_widen", (double)n * 12, st);
+  k_widen<<<(int)std::min<int64_t>((n + 255) / 256, 1216), 256, 0, st>>>((const float*)src, (double*)dst, n);
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
   return NRE_OK;
 }
 
@@ -259,12 +324,14 @@ int enqueue_chunk(SlotObj* so, int iters, double rtol) {
   return NRE_OK;
 }
 
-// Capture one chunk as a graph (the pointers of a slot object never change).
-// A capture that fails leaves the slot on direct launches.
-void capture_chunk(SlotObj* so, int chunk, double rtol) {
-  if (so->gexec) {
-    cudaGraphExecDestroy(so->gexec);
-    so->gexec = nullptr;
+// Capture one chunk as a graph (the pointers of a slot object never change)
+// into the first solve's graph or (inner) the correction solves' one.  A
+// capture that fails leaves those solves on direct launches.
+void capture_chunk(SlotObj* so, int chunk, double rtol, bool inner = false) {
+  cudaGraphExec_t& gx = inner ? so->gexec_in : so->gexec;
+  if (gx) {
+    cudaGraphExecDestroy(gx);
+    gx = nullptr;
   }
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(so->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -293,10 +360,10 @@ void capture_chunk(SlotObj* so, int chunk, double rtol) {
     ex = nullptr;
   }
   cudaGraphDestroy(g);
-  so->gexec = ex;
-  so->g_rtol = rtol;
-  so->g_chunk = chunk;
-  so->g_kernels = kernels;
+  gx = ex;
+  (inner ? so->gin_rtol : so->g_rtol) = rtol;
+  (inner ? so->gin_chunk : so->g_chunk) = chunk;
+  (inner ? so->gin_kernels : so->g_kernels) = kernels;
 }
 
 }  // namespace
@@ -329,6 +396,18 @@ int nre_server::prepare(Job* j) {
     NRE_TRY(mgvi_rhs(so->m, so->db.p, so->deta.p, so->drhs.p, B, so->st));
     rhs = so->drhs.p;
   }
+  if (r.refine > 0) {
+    // the FP64 system at the same point: widened xi_p and right-hand sides
+    NRE_TRY(widen(so->dxi.p, so->dxi64.p, (int64_t)S, so->st));
+    if (!so->m64) NRE_TRY(metric_create(&so->m64, NRE_MODEL_CF, so->plan64, so->lik, so->dxi64.p, B, so->st));
+    else NRE_TRY(metric_relinearize(so->m64, so->dxi64.p, so->st));
+    NRE_TRY(widen(rhs, so->db64.p, (int64_t)B * S, so->st));
+    NRE_TRY_CUDA(cudaMemsetAsync(so->dx64.p, 0, (size_t)B * S * 8, so->st));
+  }
+  j->pass = 0;
+  j->rf_inflight = false;
+  j->cur_rtol = r.rtol;
+  for (int i = 0; i < B; ++i) j->its_total[i] = 0;
   NRE_TRY(cg_begin(so->m, rhs, so->dx.p, B, r.rtol, so->st));
   const int chunk = cfg.chunk_iters;
   if (cfg.use_graphs && (so->g_chunk != chunk || so->g_rtol != r.rtol || !so->gexec))
@@ -451,25 +530,88 @@ void nre_server::run_work() {
           done.push_back(j);
           continue;
         }
-        bool any = false;
-        for (int i = 0; i < B; ++i) any |= so->h_sc[(size_t)i * CG_SC_N + CG_SC_ACTIVE] != 0.0;
-        if (!any || j->iters_done >= r.maxiter) {
+        int s = NRE_OK;
+        if (j->rf_inflight) {
+          // a residual pass finished: the true residuals decide
+          j->rf_inflight = false;
+          std::vector<int> act(B, 0);
+          bool anyr = false;
+          for (int i = 0; i < B; ++i) {
+            const double bb = so->h_rf[B + i];
+            const double rel = bb > 0 ? std::sqrt(so->h_rf[i] / bb) : 0.0;
+            j->res.relres[i] = rel;
+            act[i] = rel > r.rtol ? 1 : 0;
+            anyr = anyr || act[i];
+          }
+          if (!anyr || j->pass >= r.refine) {
+            done.push_back(j);
+            continue;
+          }
+          // the next correction: CG on the cast-down residual of the systems above rtol
+          void* rlo = nullptr;
+          s = refine_down(so->m, so->m64, B, act.data(), &rlo, so->st);
+          if (s == NRE_OK) s = cg_begin(so->m, rlo, so->dx.p, B, kInnerRtol, so->st);
+          if (s == NRE_OK && cfg.use_graphs &&
+              (!so->gexec_in || so->gin_chunk != cfg.chunk_iters || so->gin_rtol != kInnerRtol))
+            capture_chunk(so, cfg.chunk_iters, kInnerRtol, true);
+          ++j->pass;
+          j->iters_done = 0;
+          j->cur_rtol = kInnerRtol;
+        } else {
+          bool any = false;
+          for (int i = 0; i < B; ++i) any |= so->h_sc[(size_t)i * CG_SC_N + CG_SC_ACTIVE] != 0.0;
+          if (!any || j->iters_done >= r.maxiter) {
+            if (r.refine <= 0) {
+              done.push_back(j);
+              continue;
+            }
+            // the solve of this pass is done: x64 += its result, r = b - M64 x64
+            for (int i = 0; i < B; ++i) j->its_total[i] += (int)so->h_sc[(size_t)i * CG_SC_N + CG_SC_ITERS];
+            double* sums = nullptr;
+            s = refine_residual(so->m, so->m64, so->db64.as<double>(), so->dx64.as<double>(), so->dx.p, B,
+                                j->pass == 0, &sums, so->st);
+            if (s == NRE_OK &&
+                (cudaMemcpyAsync(so->h_rf, sums, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, so->st) !=
+                     cudaSuccess ||
+                 cudaEventRecord(so->ev, so->st) != cudaSuccess)) {
+              cudaGetLastError();
+              s = set_error(NRE_ECUDA, "residual pass: copy / event record failed");
+            }
+            if (s != NRE_OK) {
+              set_msg(j, s, nre_last_error());
+              j->so_broken = true;
+              done.push_back(j);
+              continue;
+            }
+            j->rf_inflight = true;
+            j->inflight = true;
+            continue;
+          }
+        }
+        if (s != NRE_OK) {
+          set_msg(j, s, nre_last_error());
+          j->so_broken = true;
           done.push_back(j);
           continue;
         }
       }
       const int k = std::min(cfg.chunk_iters, r.maxiter - j->iters_done);
+      const double rt = j->cur_rtol;
+      cudaGraphExec_t gx = j->pass == 0 ? so->gexec : so->gexec_in;
+      const int gchunk = j->pass == 0 ? so->g_chunk : so->gin_chunk;
+      const double grt = j->pass == 0 ? so->g_rtol : so->gin_rtol;
+      const unsigned long long gk = j->pass == 0 ? so->g_kernels : so->gin_kernels;
       int s = NRE_OK;
       bool graph = false;
-      if (so->gexec && k == so->g_chunk && so->g_rtol == r.rtol) {
-        const cudaError_t e = cudaGraphLaunch(so->gexec, so->st);
+      if (gx && k == gchunk && grt == rt) {
+        const cudaError_t e = cudaGraphLaunch(gx, so->st);
         if (e != cudaSuccess) {
           cudaGetLastError();
           s = set_error(NRE_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
         }
         graph = true;
       } else {
-        s = enqueue_chunk(so, k, r.rtol);
+        s = enqueue_chunk(so, k, rt);
       }
       if (s == NRE_OK && cudaEventRecord(so->ev, so->st) != cudaSuccess)
         s = set_error(NRE_ECUDA, "cudaEventRecord failed");
@@ -479,7 +621,7 @@ void nre_server::run_work() {
         done.push_back(j);
         continue;
       }
-      if (graph) prof_add_launches(so->g_kernels);
+      if (graph) prof_add_launches(gk);
       j->iters_done += k;
       j->inflight = true;
       progressed = true;
@@ -521,7 +663,24 @@ void nre_server::run_fin() {
     SlotObj* so = j->so;
     const nre_serve_req& r = j->req;
     const int B = r.n_samples;
-    if (so && !j->so_broken) {
+    if (so && !j->so_broken && r.refine > 0) {
+      // FP64 solutions; relres already holds the true residuals
+      const size_t S = (size_t)j->g.S, L = (size_t)j->g.latent;
+      cudaError_t e = cudaMemcpy2DAsync(r.x64_out, L * 8, so->dx64.p, S * 8, L * 8, B, cudaMemcpyDeviceToHost, so->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(so->st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_msg(j, NRE_ECUDA, cudaGetErrorString(e));
+        j->so_broken = true;
+      } else {
+        bool conv = true;
+        for (int i = 0; i < B; ++i) {
+          j->res.iters[i] = j->its_total[i];
+          if (j->res.relres[i] > r.rtol) conv = false;
+        }
+        if (!conv) set_msg(j, NRE_ENOTCONV, "some system missed rtol (true residual) after the correction passes");
+      }
+    } else if (so && !j->so_broken) {
       const size_t E = cfg.dtype == NRE_F64 ? 8 : 4;
       const size_t S = (size_t)j->g.S, L = (size_t)j->g.latent;
       cudaError_t e = cudaMemcpy2DAsync(r.x_out, L * E, so->dx.p, S * E, L * E, B, cudaMemcpyDeviceToHost, so->st);
@@ -627,7 +786,11 @@ int serve_submit(nre_server* s, const nre_serve_req* req, uint64_t* id) {
     return set_error(NRE_EINVAL, "the Poisson likelihood uses the exponential response");
   if (req->precond != NRE_PRECOND_NONE && req->precond != NRE_PRECOND_HARMONIC)
     return set_error(NRE_EINVAL, "unknown preconditioner %d", req->precond);
-  if (!req->xi_p || !req->b || !req->x_out) return set_error(NRE_EINVAL, "NULL array in the request");
+  if (req->refine < 0 || req->refine > 16) return set_error(NRE_EINVAL, "refine must be in [0, 16]");
+  if (req->refine > 0 && s->cfg.dtype != NRE_F32)
+    return set_error(NRE_EINVAL, "residual correction needs an FP32 server");
+  if (!req->xi_p || !req->b || (req->refine > 0 ? !req->x64_out : !req->x_out))
+    return set_error(NRE_EINVAL, "NULL array in the request");
   const uint64_t est = footprint(req, g, s->cfg.dtype);
   if (est > s->cfg.hbm_budget_bytes)
     return set_error(NRE_EBUSY, "request needs %llu device bytes, the budget is %llu", (unsigned long long)est,
@@ -647,6 +810,7 @@ int serve_submit(nre_server* s, const nre_serve_req* req, uint64_t* id) {
   k.B = req->n_samples;
   k.precond = req->precond;
   k.mgvi = req->eta ? 1 : 0;
+  k.refine = req->refine > 0 ? 1 : 0;
   j->res.t_submit = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {

@@ -100,3 +100,20 @@ def icr_fp64_tol(n0, n_levels, rho=0.1):
         kap.append(k)
     tol = max(1e-12, 9 * np.finfo(np.float64).eps * sum(kap))
     return tol, kap
+
+
+def icr3_fp64_tol(n0, n_levels, rho):
+    """As icr_fp64_tol for the 3-D chart: the neighbourhood matrices are 27 x 27,
+    so tol = max(1e-12, 27 eps64 sum_l max_(i,j) kappa(K_cc[l, i, j]))."""
+    from oracle.icr3 import ICRChart3D
+    c = ICRChart3D(n0=n0, n_levels=n_levels, rho=rho)
+    kap = []
+    for lev in range(n_levels):
+        k = 0.0
+        n = c.sizes[lev]
+        for i in range(n):
+            for j in range(n):
+                pc, _ = c.coarse_fine_points(lev, i, j)
+                k = max(k, float(np.linalg.cond(c.kmat(pc, pc))))
+        kap.append(k)
+    return max(1e-12, 27 * np.finfo(np.float64).eps * sum(kap)), kap

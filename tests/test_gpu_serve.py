@@ -252,3 +252,52 @@ def test_serve_evicts_idle_objects_under_budget():
     st = srv.stats()
     assert st["evicted"] >= 2 and st["peak_reserved"] <= int(max(f64, f128) * 1.2)
     srv.close()
+
+
+def test_serve_refined_true_residual_alone_vs_mix_and_footprint():
+    """Requests with residual correction: FP32 solves, FP64 residuals.  Every
+    solution's true residual ||b - M64 x|| / ||b|| (checked here with an FP64
+    metric) is <= rtol, equals the reported one, and is bitwise the same alone
+    and in the mix; the footprint bounds what the slot object holds."""
+    nre = _nre()
+    reqs = []
+    for i, shape in enumerate([(64, 64), (32, 32, 32), (4096,)]):
+        for j, lik in enumerate(("gauss", "poisson")):
+            xi_p, b, _, _ = _inputs(shape, 4, 3000 + 10 * i + j)
+            reqs.append((shape, lik, xi_p, b))
+    outs = {}
+    for slots in (1, 8):
+        srv = nre.Server(max_slots=slots, use_graphs=True)
+        xs = [np.zeros(b.shape, dtype=np.float64) for (_, _, _, b) in reqs]
+        ids = [srv.submit(sh, xp, b, None, lik=lik, response="identity" if lik == "gauss" else "exp", rtol=1e-5,
+                          maxiter=3000, refine=4, x64_out=x) for (sh, lik, xp, b), x in zip(reqs, xs)]
+        res = [srv.poll(i, timeout_ms=600000) for i in ids]
+        srv.close()
+        outs[slots] = (xs, res)
+    for k, (shape, lik, xi_p, b) in enumerate(reqs):
+        xa, ra = outs[1][0][k], outs[1][1][k]
+        xm, rm = outs[8][0][k], outs[8][1][k]
+        assert ra["status"] == 0 and rm["status"] == 0, (shape, lik, ra["error"], rm["error"])
+        assert np.array_equal(xa, xm) and ra["relres"][:4] == rm["relres"][:4]
+        plan = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float64)
+        L = (nre.Likelihood("gauss", sigma=0.1, response="identity") if lik == "gauss"
+             else nre.Likelihood("poisson", scale=10.0))
+        M = nre.Metric(plan, L, plan.pad(torch.tensor(xi_p.astype(np.float64), device="cuda")[None])[0], max_batch=4)
+        xx = plan.pad(torch.tensor(xa, device="cuda"))
+        bb = plan.pad(torch.tensor(b.astype(np.float64), device="cuda"))
+        true = (plan.unpad(bb - M.apply(xx)).norm(dim=1) / plan.unpad(bb).norm(dim=1)).cpu().numpy()
+        print(shape, lik, "true relres", true, "reported", ra["relres"][:4], "iterations", ra["iters"][:4])
+        assert true.max() <= 1e-5
+        np.testing.assert_allclose(true, ra["relres"][:4], rtol=1e-6, atol=1e-12)
+    # footprint: the slot object of a refined request holds no more than charged
+    srv = nre.Server(max_slots=1)
+    shape = (128, 128)
+    fp = srv.footprint(shape, n_samples=4, lik="poisson", refine=4)
+    before = nre.device_bytes()
+    xi_p, b, _, _ = _inputs(shape, 4, 3100)
+    x = np.zeros(b.shape, dtype=np.float64)
+    r = srv.poll(srv.submit(shape, xi_p, b, None, lik="poisson", rtol=1e-5, maxiter=3000, refine=4, x64_out=x), -1)
+    assert r["status"] == 0, r["error"]
+    held = nre.device_bytes() - before
+    assert 0 < held <= fp, (held, fp)
+    srv.close()
