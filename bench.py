@@ -54,25 +54,44 @@ def parse():
                     help="skip the metric-product roofline leg on 2-D 1024^2 and 3-D 256^3")
     ap.add_argument("--metric-batch", type=int, default=8)
     ap.add_argument("--icr-batch", type=int, default=32)
-    ap.add_argument("--cg3d-maxiter", type=int, default=300,
+    ap.add_argument("--cg3d-maxiter", type=int, default=2000,
                     help="iteration cap of the 3-D masked batched CG solve in the metric leg")
-    ap.add_argument("--serve-requests", type=int, default=100,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream (0: skip the serving leg)")
+    ap.add_argument("--serve-budget-gb", type=float, default=2.0,
+                    help="HBM budget of the second FP32 server run (0: skip it)")
+    ap.add_argument("--serve-budget-requests", type=int, default=500,
+                    help="requests of the stream's start that the budgeted run serves")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-plain-cap-s", type=float, default=90.0,
                     help="stop the sequential FP64 arm after this many seconds")
+    ap.add_argument("--serve-timeout-s", type=float, default=900.0,
+                    help="limit of the serving leg's child process")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--icr-only", action="store_true", help="run only the ICR leg")
+    ap.add_argument("--next-only", action="store_true", help="run only the KL / geoVI / 3-D ICR leg")
+    ap.add_argument("--no-next-rows", action="store_true", help="skip the KL / geoVI / 3-D ICR leg")
     return ap.parse_args()
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
 # one capture, caches flushed before each launch) of the kernels that can be
 # the dominant one, keyed by (kernel tag, batch), averaged over the launch
-# variants the tag covers; None where no capture of the current kernels exists.
-DRAM_TRAFFIC = {
-    ("row_sweep_f32_2d", 32): (53.12e6, "profiles/traffic_f32_2d_512x512_b32.md"),
-}
+# variants the tag covers, with the digest of the kernel sources they were
+# captured from (kernel_src_digest); an entry whose digest differs from the
+# current sources is stale and reported as null.
+DRAM_TRAFFIC = {}
+
+
+def kernel_src_digest():
+    """sha256 (first 16 hex digits) of the library's CUDA / C++ sources."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2402_16683_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
 
 
 def config(batch):
@@ -160,37 +179,105 @@ def oracle_step(om, xi_p, w, seed, iters):
     return iters
 
 
-def cpu_baseline(target_s=15.0):
+def _oracle_worker(args):
+    """One host process of the CPU baseline: systems seed0, seed0 + stride, ...
+    until `seconds` have passed; returns (products, seconds)."""
+    seed0, stride, seconds, iters = args
     om, xi_p, w = oracle_setup()
     t0 = time.perf_counter()
-    n = 0
-    k = 0
-    while time.perf_counter() - t0 < target_s:
-        n += oracle_step(om, xi_p, w, 1000 + k, 20)
+    n, k = 0, 0
+    while time.perf_counter() - t0 < seconds:
+        n += oracle_step(om, xi_p, w, seed0 + stride * k, iters)
         k += 1
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{k} systems x (MGVI rhs + 20 CG iterations) of the 512x512 Poisson metric, "
-                      f"FP64 numpy oracle, single thread, {dt:.1f} s"}
+    return n, time.perf_counter() - t0, k
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_on_cores(ncores, seconds, iters=20, seed0=1000):
+    """The oracle on `ncores` host processes (one thread each, started with
+    spawn), each solving its own systems for `seconds`: products/s of all."""
+    if ncores <= 1:
+        n, dt, k = _oracle_worker((seed0, 1, seconds, iters))
+        return n / dt, k
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            res = pool.map(_oracle_worker, [(seed0 + c, ncores, seconds, iters) for c in range(ncores)])
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sum(r[0] for r in res) / max(r[1] for r in res), sum(r[2] for r in res)
+
+
+def cpu_baseline(target_s=12.0):
+    """The FP64 oracle on every host core (one process per core), and on one."""
+    nc = cpu_cores()
+    v_all, k_all = oracle_on_cores(nc, target_s)
+    v_one, k_one = oracle_on_cores(1, target_s)
+    return {"value": v_all, "unit": UNIT, "cores": nc, "kind": "oracle",
+            "sample": f"{k_all} systems x (MGVI rhs + 20 CG iterations) of the 512x512 Poisson metric, "
+                      f"FP64 numpy oracle, one process per core on {nc} cores ({cpu_model()}), "
+                      f"{target_s:.0f} s",
+            "single_core": {"value": v_one, "cores": 1,
+                            "sample": f"{k_one} systems, one process, {target_s:.0f} s"}}
+
+
+def _oracle_systems(args):
+    """`count` systems of the reference arm from seed0 (one host process)."""
+    seed0, count, iters = args
+    om, xi_p, w = oracle_setup()
+    for k in range(count):
+        oracle_step(om, xi_p, w, seed0 + k, iters)
+    return count * iters
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores: each step solves one system
+    per core (MGVI rhs + 20 CG iterations), one process per core."""
     if rank != 0:
         return
-    om, xi_p, w = oracle_setup()
+    import multiprocessing as mp
     iters = 20
-    for i in range(args.warmup):
-        oracle_step(om, xi_p, w, 2000 + i, iters)
-    times = []
-    for i in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(om, xi_p, w, 3000 + i, iters)
-        times.append(time.perf_counter() - t0)
+    nc = cpu_cores()
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    with mp.get_context("spawn").Pool(nc) as pool:
+        pool.map(_oracle_systems, [(2000 + c, 1, iters) for c in range(nc)] * max(1, args.warmup))
+        times = []
+        for i in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_systems, [(3000 + 100 * i + c, 1, iters) for c in range(nc)])
+            times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = args.steps * iters / tot
-    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"each step: one system's MGVI rhs + {iters} CG iterations of the 512x512 Poisson "
-                    f"metric, FP64 numpy oracle, single thread"}
+    value = args.steps * nc * iters / tot
+    cb = {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle",
+          "sample": f"each step: {nc} systems (one per core, {cpu_model()}), each the MGVI rhs + {iters} "
+                    f"CG iterations of the 512x512 Poisson metric, FP64 numpy oracle"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
                       "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -228,7 +315,11 @@ def run_ours(args, rank, world):
 
     if args.serve_only:
         if rank == 0:
-            print(json.dumps({"serve": run_serve(args)}), flush=True)
+            try:
+                serve = run_serve(args)
+            except Exception as e:
+                serve = {"error": f"{type(e).__name__}: {e}"[:500]}
+            print(json.dumps({"serve": serve}), flush=True)
         return
     if args.icr_only:
         lib0 = _lib.load()
@@ -236,6 +327,14 @@ def run_ours(args, rank, world):
         fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev0)
         if rank == 0:
             print(json.dumps({"icr": run_icr(args, lib0, fl, torch.cuda.current_stream(), peaks()[0])}), flush=True)
+        return
+    if args.next_only:
+        lib0 = _lib.load()
+        dev0 = torch.device("cuda", torch.cuda.current_device())
+        fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev0)
+        if rank == 0:
+            print(json.dumps({"next_rows": run_next_rows(args, lib0, fl, torch.cuda.current_stream(), peaks()[0])}),
+                  flush=True)
         return
     lib = _lib.load()
     lib.nre_launch_count.restype = C.c_ulonglong
@@ -308,6 +407,8 @@ def run_ours(args, rank, world):
     peak, peak_kind = peaks()
     achieved = kbytes / (kms / 1e3) / 1e9
     traffic = DRAM_TRAFFIC.get((name, B))
+    if traffic and traffic[2] != kernel_src_digest():
+        traffic = None  # captured from other kernel sources: stale
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": traffic[0] if traffic else None,
@@ -323,9 +424,15 @@ def run_ours(args, rank, world):
     grids = None
     if not args.no_metric_grids:
         grids = run_metric_grids(args, lib)
+    nxt = None
+    if not args.no_next_rows and rank == 0:
+        try:
+            nxt = run_next_rows(args, lib, flush, stream, peaks()[0])
+        except Exception as e:  # keep the line: the leg's failure is part of the result
+            nxt = {"error": f"{type(e).__name__}: {e}"[:500]}
     serve = None
     if args.serve_requests > 0 and world == 1:
-        serve = run_serve(args)
+        serve = run_serve_child(args)
     if rank != 0:
         return
     cb = None
@@ -339,6 +446,8 @@ def run_ours(args, rank, world):
            "cg_iterations": its[:1]}
     if grids is not None:
         out["metric_grids"] = grids
+    if nxt is not None:
+        out["next_rows"] = nxt
     if serve is not None:
         out["serve"] = serve
     print(json.dumps(out), flush=True)
@@ -414,8 +523,9 @@ def run_metric_grids(args, lib):
         if kind == "poisson":
             lik = nre.Likelihood("poisson", scale=10.0)
         else:
+            # the Gaussian likelihood observes the field itself (identity response)
             lik = nre.Likelihood("gauss", sigma=0.05, mask=synth.mask_fraction(synth.SEED_MASK, plan.n_field),
-                                 n_data=plan.n_field)
+                                 n_data=plan.n_field, response="identity")
         xi_p = torch.tensor(synth.normal(synth.SEED_POS, plan.latent_size), dtype=torch.float32, device=dev)
         M = nre.Metric(plan, lik, plan.pad(xi_p[None])[0], max_batch=B)
         g = np.random.default_rng(synth.SEED_TANGENT)
@@ -461,20 +571,32 @@ def run_metric_grids(args, lib):
                             "frac": (x[2] / (x[1] / 1e3) / 1e9 / peak) if x[1] else None}
                         for k, x in kern.items()}}
         if len(shape) == 3:
-            # the 3-D masked workload's batched sample solve: plain CG on the
-            # MGVI right-hand sides (the harmonic preconditioner does not model
-            # a 10 % mask), reported as it stands at a bounded iteration count
+            # the 3-D masked workload's batched sample solve: plain FP32 CG on
+            # the MGVI right-hand sides to a recursive 1e-5, then the FP64 true
+            # residual ||b - M x|| / ||b|| of each solution from an FP64 metric
+            # at the same expansion point
             eta = torch.tensor(np.random.default_rng(synth.SEED_RHS).standard_normal((B, plan.n_field)),
                                dtype=torch.float32, device=dev)
             M.mgvi_rhs(v, eta, out=o)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, its, rel, st_ = M.cg(o, rtol=1e-5, maxiter=args.cg3d_maxiter)
+            x3, its, rel, st_ = M.cg(o, rtol=1e-5, maxiter=args.cg3d_maxiter)
             torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            p64 = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float64)
+            M64 = nre.Metric(p64, lik, p64.pad(xi_p.double()[None])[0], max_batch=1)
+            true = []
+            for i in range(B):
+                xi64 = x3[i:i + 1].double()
+                bi64 = o[i:i + 1].double()
+                r64 = bi64 - M64.apply(xi64)
+                true.append(float(p64.unpad(r64).norm() / p64.unpad(bi64).norm()))
+            del M64, p64
             out[f"{len(shape)}d_{name}"]["cg_to_1e-5"] = {
                 "maxiter": args.cg3d_maxiter, "iterations": [int(i) for i in its],
-                "relres": [float(r) for r in rel], "converged": st_ == 0,
-                "seconds": time.perf_counter() - t0, "precond": "none"}
+                "relres": [float(r) for r in rel], "true_relres_fp64": true, "converged": st_ == 0,
+                "seconds": secs, "precond": "none",
+                "likelihood": "gauss sigma 0.05 on the field (identity response), 10 % mask"}
         del M, v, o
         torch.cuda.empty_cache()
     out["icr_8_to_1024"] = run_icr(args, lib, flush, stream, peak)
@@ -540,10 +662,173 @@ def run_icr(args, lib, flush, stream, peak):
     return res
 
 
+# ----------------------------------------------------------------- KL / geoVI / 3-D ICR leg
+def _timed_traced(lib, fn, n, flush, stream):
+    """Mean untraced time (ms) of fn over n calls, L2 flushed before each, and
+    the per-kernel (launches, ms, algorithmic bytes) of n traced calls."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2402_16683_gb300 import _lib
+
+    def timed():
+        ev = []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b_) for a, b_ in ev) / n
+
+    ms = timed()
+    lib.nre_prof_enable(1)
+    timed()
+    lib.nre_prof_enable(0)
+    buf = C.create_string_buffer(1 << 16)
+    _lib.check(lib.nre_prof_report(buf, len(buf)))
+    return ms, json.loads(buf.value.decode())
+
+
+def _leg_stats(ms, kern, n, peak, units, unit_name):
+    """units per second, and the HBM fraction of the whole call (its kernels'
+    algorithmic bytes over its untraced time) and of its kernels traced one by
+    one (over their summed device time)."""
+    kms = sum(x[1] for x in kern.values())
+    kbytes = sum(x[2] for x in kern.values())
+    top = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
+    return {unit_name: units / (ms / 1e3), "ms": ms, "bytes": kbytes / n,
+            "achieved_GBps": kbytes / n / (ms / 1e3) / 1e9, "frac": kbytes / n / (ms / 1e3) / 1e9 / peak,
+            "frac_traced_kernels": (kbytes / (kms / 1e3) / 1e9 / peak) if kms else None,
+            "kernel_launches_per_call": sum(x[0] for x in kern.values()) / n, "top_kernel": top,
+            "kernels": {k: {"us_per_call": 1e3 * x[1] / n, "share": x[1] / kms if kms else None,
+                            "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None} for k, x in kern.items()}}
+
+
+def run_next_rows(args, lib, flush, stream, peak):
+    """The rows after sampling, FP32 on the 2-D 512^2 Poisson workload (rate
+    10 exp(cf), power-spectrum model) and the 3-D chart:
+
+    * KL (MGVI): four residual samples (two antithetic pairs of linear draws,
+      CG to 1e-3 on the MGVI right-hand sides at xi_bar); energy and gradient,
+      the sample-averaged metric product, one Newton-CG step (CG to 1e-3);
+    * geoVI: the nonlinear update of 8 linear draws (5 Newton iterations at
+      most, inner CG to 1e-3);
+    * ICR on the spherical log-radial chart refined 4^3 -> 256^3 (6 levels),
+      Matern-3/2 (length scale 0.1), batch 4: forward and VJP.
+    Counts drawn from the model at a N(0, 1) truth (seed SEED_TRUTH)."""
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = max(5, args.steps)
+    out = {}
+    shape = (512, 512)
+    plan = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float32)
+    lik = nre.Likelihood("poisson", scale=10.0)
+    truth = torch.tensor(synth.normal(synth.SEED_TRUTH, plan.latent_size), dtype=torch.float32, device=dev)
+    cf = plan.forward(plan.pad(truth[None]))[0].double().cpu().numpy()
+    data = synth.rng(synth.SEED_TRUTH + 100).poisson(10.0 * np.exp(cf)).astype(np.float64)
+    xbar = plan.pad(torch.tensor(0.1 * synth.normal(synth.SEED_POS, plan.latent_size), dtype=torch.float32,
+                                 device=dev)[None])[0]
+
+    # ---- MGVI: linear draws at xi_bar, the KL of their antithetic samples
+    M = nre.Metric(plan, lik, xbar, max_batch=8)
+    g = np.random.default_rng(synth.SEED_RHS)
+    xi_prime = plan.pad(torch.tensor(g.standard_normal((8, plan.latent_size)), dtype=torch.float32, device=dev))
+    eta = torch.tensor(g.standard_normal((8, plan.n_field)), dtype=torch.float32, device=dev)
+    rhs = M.mgvi_rhs(xi_prime, eta)
+    draws, _, _, _ = M.cg(rhs, rtol=1e-3, maxiter=500)
+    deltas = torch.cat([draws[:2], -draws[:2]])
+    kl = nre.KL(plan, lik, data, deltas.contiguous())
+    kl.set_position(xbar)
+    res = {"samples": 4, "grid": list(shape)}
+    ms, kern = _timed_traced(lib, lambda: kl.energy_gradient(), n, flush, stream)
+    res["energy_gradient"] = _leg_stats(ms, kern, n, peak, 1, "per_s")
+    KM = kl.metric()
+    v = plan.pad(torch.tensor(g.standard_normal((1, plan.latent_size)), dtype=torch.float32, device=dev))
+    o = torch.empty_like(v)
+    ms, kern = _timed_traced(lib, lambda: KM.apply(v, out=o), n, flush, stream)
+    res["metric_product"] = _leg_stats(ms, kern, n, peak, 1, "products_per_s")
+    e0 = kl.energy_gradient()[0]
+    steps = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, e, its = kl.newton_step(cg_rtol=1e-3, cg_maxiter=200)
+        torch.cuda.synchronize()
+        steps.append({"ms": 1e3 * (time.perf_counter() - t0), "cg_iterations": its, "mean_abs_step": st,
+                      "energy": e})
+    res["newton_steps"] = steps
+    res["energy_start"] = e0
+    out["kl_2d_512x512_poisson_S4"] = res
+    del KM, kl
+
+    # ---- geoVI: nonlinear update of the 8 linear draws at xi_bar
+    d0 = draws.clone()
+    d = torch.empty_like(d0)
+    info = {}
+
+    def gv():
+        d.copy_(d0)
+        its, stp = M.geovi_update(rhs, d, xtol=0.0, maxiter=5, cg_rtol=1e-3, cg_maxiter=500)
+        info["its"], info["steps"] = its, stp
+
+    gv()
+    ms, kern = _timed_traced(lib, gv, max(3, n // 2), flush, stream)
+    r = _leg_stats(ms, kern, max(3, n // 2), peak, 8, "samples_per_s")
+    r.update({"samples": 8, "newton_iterations": [int(i) for i in info["its"]],
+              "last_mean_abs_step": [float(s) for s in info["steps"]]})
+    out["geovi_2d_512x512_poisson_B8"] = r
+    del M, draws, d0, d, rhs
+    torch.cuda.empty_cache()
+
+    # ---- 3-D ICR
+    B = 4
+    icr = nre.ICR(n0=4, n_levels=6, rho=0.1, var=1.0, dtype=torch.float32, ndim=3)
+    xi = icr.pad(torch.tensor(synth.rng(synth.SEED_POS).standard_normal((B, icr.latent_size)), dtype=torch.float32,
+                              device=dev))
+    ct = torch.tensor(synth.rng(synth.SEED_TANGENT).standard_normal((B, icr.n_out)), dtype=torch.float32, device=dev)
+    res = {"batch": B, "levels": 6, "grid": [256, 256, 256]}
+    for name, fn in (("forward", lambda: icr.forward(xi)), ("vjp", lambda: icr.vjp(xi, ct))):
+        fn()
+        ms, kern = _timed_traced(lib, fn, n, flush, stream)
+        res[name] = _leg_stats(ms, kern, n, peak, B, "fields_per_s")
+    out["icr3_4_to_256"] = res
+    del icr, xi, ct
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- serving leg
+def run_serve_child(args):
+    """The serving leg in a child process (this script with --serve-only), so
+    that its failure, whatever it is, leaves the rest of the line intact."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve-only",
+           "--serve-requests", str(args.serve_requests), "--serve-budget-gb", str(args.serve_budget_gb),
+           "--serve-budget-requests", str(args.serve_budget_requests), "--serve-slots", str(args.serve_slots),
+           "--serve-plain-cap-s", str(args.serve_plain_cap_s)]
+    try:
+        p = subprocess.run(cmd, capture_output=True, text=True, timeout=args.serve_timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"serving leg exceeded {args.serve_timeout_s:.0f} s"}
+    for line in reversed(p.stdout.splitlines()):
+        if line.startswith('{"serve"'):
+            return json.loads(line)["serve"]
+    return {"error": f"serving leg exited with {p.returncode}: {p.stderr[-400:]}"}
+
+
 SERVE_SAMPLES = 8
 SERVE_RTOL = 1e-5
 SERVE_MAXITER = 2000
+# residual-correction passes of the FP32 server's requests: its solutions are
+# FP64 and meet SERVE_RTOL on the true residual
+SERVE_REFINE = 4
 # Gaussian requests observe the field itself (sigma 0.1, every pixel); Poisson
 # requests count at rate 10 exp(cf)
 SERVE_RESPONSE = {"gauss": "identity", "poisson": "exp"}
@@ -560,7 +845,9 @@ def run_serve(args):
     request to 1e-5 relative residual) through
 
     * the FP32 server: continuous batching, one stream per admitted request,
-      CG chunks replayed as CUDA graphs, admission by HBM footprint;
+      CG chunks replayed as CUDA graphs, admission by HBM footprint, FP32
+      solves with FP64 residual correction to the true 1e-5 (FP64 solutions);
+      run once with the whole device and once under an HBM budget;
     * the plain sequential FP64 path: requests first in first out, one
       system at a time (batch 1), through Metric / cg, nothing overlapped.
 
@@ -596,65 +883,94 @@ def run_serve(args):
         with lock:
             if free[shape]:
                 return free[shape].pop()
-        return torch.empty_like(inputs[shape][0][1]).pin_memory()
+        return torch.empty(inputs[shape][0][1].shape, dtype=torch.float64).pin_memory()
 
-    # ---- FP32 server
-    srv = nre.Server(max_slots=args.serve_slots, dtype=torch.float32, chunk_iters=8, use_graphs=True)
-    for shape in synth.SERVE_SHAPES:
-        for lik in ("gauss", "poisson"):
-            xi, b = inputs[shape][0]
+    def serve_fp32(budget_bytes, reqs):
+        """The stream through one FP32 server; returns its statistics and one
+        solution per (grid, likelihood) class for the true-residual check."""
+        srv = nre.Server(hbm_budget_bytes=budget_bytes, max_slots=args.serve_slots, dtype=torch.float32,
+                         chunk_iters=8, use_graphs=True)
+        try:
+            return _serve_fp32(srv, reqs)
+        finally:
+            srv.close()
+
+    def _serve_fp32(srv, reqs):
+        for shape in synth.SERVE_SHAPES:
+            for lik in ("gauss", "poisson"):
+                xi, b = inputs[shape][0]
+                out = take_out(shape)
+                srv.poll(srv.submit(shape, xi, b, None, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
+                                    response=SERVE_RESPONSE[lik], refine=SERVE_REFINE, x64_out=out), -1)
+                free[shape].append(out)
+        results = [None] * len(reqs)
+        ids = [None] * len(reqs)
+        kept = {}
+        ready = threading.Semaphore(0)
+
+        def poller():
+            for i in range(len(reqs)):
+                ready.acquire()
+                r = srv.poll(ids[i][0], 600000)
+                if r is None:  # not done after 10 minutes: count it as failed
+                    r = {"status": -1, "error": "no result within 600 s", "t_done": time.monotonic(),
+                         "iters": [0] * SERVE_SAMPLES, "relres": [float("inf")] * SERVE_SAMPLES}
+                results[i] = r
+                key = (reqs[i][1], reqs[i][2])
+                if key not in kept and r["status"] == 0:
+                    kept[key] = (i % pool, ids[i][1].clone())
+                with lock:
+                    free[reqs[i][1]].append(ids[i][1])
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.monotonic()
+        for i, (ta, shape, lik) in enumerate(reqs):
+            dt = t0 + ta - time.monotonic()
+            if dt > 0:
+                time.sleep(dt)
+            xi, b = inputs[shape][i % pool]
             out = take_out(shape)
-            r = srv.poll(srv.submit(shape, xi, b, out, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
-                                    response=SERVE_RESPONSE[lik]), -1)
-            free[shape].append(out)
-    results = [None] * len(reqs)
-    ids = [None] * len(reqs)
-    ready = threading.Semaphore(0)
+            ids[i] = (srv.submit(shape, xi, b, None, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
+                                 response=SERVE_RESPONSE[lik], refine=SERVE_REFINE, x64_out=out), out)
+            ready.release()
+        th.join()
+        st = srv.stats()
+        lat32 = [1e3 * (r["t_done"] - (t0 + reqs[i][0])) for i, r in enumerate(results)]
+        errors = []
+        for r in results:
+            if r["status"] != 0 and r["error"] not in errors and len(errors) < 5:
+                errors.append(r["error"])
+        ok32 = sum(1 for r in results if r["status"] == 0)
+        end32 = max(r["t_done"] for r in results)
+        its32 = [max(r["iters"][:SERVE_SAMPLES]) for r in results]
+        by_class = {}
+        for i, r in enumerate(results):
+            key = "x".join(str(d) for d in reqs[i][1]) + "_" + reqs[i][2]
+            c = by_class.setdefault(key, {"n": 0, "converged": 0, "iters": [], "lat": []})
+            c["n"] += 1
+            c["converged"] += int(r["status"] == 0)
+            c["iters"].append(max(r["iters"][:SERVE_SAMPLES]))
+            c["lat"].append(lat32[i])
+        by_class = {k: {"n": v["n"], "converged": v["converged"], "mean_iters": float(np.mean(v["iters"])),
+                        "p50_ms": _pctl(v["lat"], 50), "p99_ms": _pctl(v["lat"], 99)}
+                    for k, v in sorted(by_class.items())}
+        res = {"p50_ms": _pctl(lat32, 50), "p99_ms": _pctl(lat32, 99), "mean_ms": float(np.mean(lat32)),
+               "solves_per_s": SERVE_SAMPLES * len(reqs) / (end32 - t0), "converged": ok32,
+               "mean_iters": float(np.mean(its32)),
+               "max_true_relres": max(max(r["relres"][:SERVE_SAMPLES]) for r in results),
+               "refine_passes_max": SERVE_REFINE,
+               "slots": args.serve_slots, "graph_replays": st["graph_replays"], "chunks": st["chunks"],
+               "slot_objects_created": st["created"], "reused": st["reused"], "evicted": st["evicted"],
+               "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9,
+               "failed": len(results) - ok32, "errors": errors, "by_class": by_class}
+        return res, kept
 
-    def poller():
-        for i in range(len(reqs)):
-            ready.acquire()
-            r = srv.poll(ids[i][0], -1)
-            results[i] = r
-            with lock:
-                free[reqs[i][1]].append(ids[i][1])
-
-    th = threading.Thread(target=poller)
-    th.start()
-    t0 = time.monotonic()
-    for i, (ta, shape, lik) in enumerate(reqs):
-        dt = t0 + ta - time.monotonic()
-        if dt > 0:
-            time.sleep(dt)
-        xi, b = inputs[shape][i % pool]
-        out = take_out(shape)
-        ids[i] = (srv.submit(shape, xi, b, out, lik=lik, rtol=SERVE_RTOL, maxiter=SERVE_MAXITER,
-                             response=SERVE_RESPONSE[lik]), out)
-        ready.release()
-    th.join()
-    st = srv.stats()
-    srv.close()
-    lat32 = [1e3 * (r["t_done"] - (t0 + reqs[i][0])) for i, r in enumerate(results)]
-    ok32 = sum(1 for r in results if r["status"] == 0)
-    end32 = max(r["t_done"] for r in results)
-    its32 = [max(r["iters"][:SERVE_SAMPLES]) for r in results]
-    by_class = {}
-    for i, r in enumerate(results):
-        key = "x".join(str(d) for d in reqs[i][1]) + "_" + reqs[i][2]
-        c = by_class.setdefault(key, {"n": 0, "converged": 0, "iters": [], "lat": []})
-        c["n"] += 1
-        c["converged"] += int(r["status"] == 0)
-        c["iters"].append(max(r["iters"][:SERVE_SAMPLES]))
-        c["lat"].append(lat32[i])
-    by_class = {k: {"n": v["n"], "converged": v["converged"], "mean_iters": float(np.mean(v["iters"])),
-                    "p50_ms": _pctl(v["lat"], 50)} for k, v in sorted(by_class.items())}
-    fp32 = {"p50_ms": _pctl(lat32, 50), "p99_ms": _pctl(lat32, 99), "mean_ms": float(np.mean(lat32)),
-            "solves_per_s": SERVE_SAMPLES * len(reqs) / (end32 - t0), "converged": ok32,
-            "mean_iters": float(np.mean(its32)), "max_relres": max(max(r["relres"][:SERVE_SAMPLES]) for r in results),
-            "slots": args.serve_slots, "graph_replays": st["graph_replays"], "chunks": st["chunks"],
-            "slot_objects_created": st["created"], "reused": st["reused"],
-            "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9,
-            "by_class": by_class}
+    fp32, kept32 = serve_fp32(0, reqs)
+    fp32_budget = None
+    if args.serve_budget_gb > 0:
+        fp32_budget, _ = serve_fp32(int(args.serve_budget_gb * 1e9), reqs[:args.serve_budget_requests])
+        fp32_budget["requests"] = min(len(reqs), args.serve_budget_requests)
 
     # ---- plain sequential FP64 path
     plans = {shape: nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR),
@@ -684,18 +1000,38 @@ def run_serve(args):
             rels.append(rel[0])
             sts.append(st_)
         torch.cuda.synchronize()
-        return max(its), max(rels), all(v == 0 for v in sts)
+        return max(its), max(rels), all(v == 0 for v in sts), out
+
+    def true_relres(shape, lik, k, x):
+        """FP64 ||b - M x|| / ||b|| of the 8 solutions x (host) of input set k."""
+        plan = plans[shape]
+        xi, b = inp64[shape][k]
+        xp = torch.zeros(plan.stride, dtype=torch.float64, device=dev)
+        xp[:plan.latent_size].copy_(xi)
+        M = nre.Metric(plan, liks[lik], xp, max_batch=SERVE_SAMPLES)
+        xd = plan.pad(x.to(dev).double())
+        bd = plan.pad(b.to(dev))
+        r = plan.unpad(bd - M.apply(xd))
+        return float((r.norm(dim=1) / plan.unpad(bd).norm(dim=1)).max())
+
+    true32 = {"x".join(str(d) for d in sh) + "_" + lik: true_relres(sh, lik, k, x)
+              for (sh, lik), (k, x) in sorted(kept32.items())}
+    fp32["true_relres_fp64_by_class"] = true32
+    fp32["max_true_relres_sampled"] = max(true32.values()) if true32 else None
 
     for shape in synth.SERVE_SHAPES:
         plain(shape, "gauss", 0)
     lat64, its64, ok64, rel64 = [], [], 0, 0.0
+    kept64 = {}
     t0 = time.monotonic()
     truncated = False
     for i, (ta, shape, lik) in enumerate(reqs):
         dt = t0 + ta - time.monotonic()
         if dt > 0:
             time.sleep(dt)
-        it, rel, ok = plain(shape, lik, i % pool)
+        it, rel, ok, x64 = plain(shape, lik, i % pool)
+        if (shape, lik) not in kept64:
+            kept64[(shape, lik)] = (i % pool, x64.clone())
         lat64.append(1e3 * (time.monotonic() - (t0 + ta)))
         its64.append(it)
         rel64 = max(rel64, rel)
@@ -705,14 +1041,17 @@ def run_serve(args):
             break
     end64 = time.monotonic()
     n64 = len(lat64)
-    fp64 = {"p50_ms": _pctl(lat64, 50), "p99_ms": _pctl(lat64, 99), "mean_ms": float(np.mean(lat64)),
+    true64 = {"x".join(str(d) for d in sh) + "_" + lik: true_relres(sh, lik, k, x)
+              for (sh, lik), (k, x) in sorted(kept64.items())}
+    fp64 = {"true_relres_fp64_by_class": true64, "max_true_relres_sampled": max(true64.values()) if true64 else None,
+            "p50_ms": _pctl(lat64, 50), "p99_ms": _pctl(lat64, 99), "mean_ms": float(np.mean(lat64)),
             "solves_per_s": SERVE_SAMPLES * n64 / (end64 - t0), "converged": ok64, "requests_served": n64,
             "mean_iters": float(np.mean(its64)), "max_relres": rel64,
             "truncated_at_s": args.serve_plain_cap_s if truncated else None}
     return {"requests": len(reqs), "rate_hz": 50.0, "samples_per_request": SERVE_SAMPLES, "rtol": SERVE_RTOL,
             "grids": [list(s) for s in synth.SERVE_SHAPES], "precond": "harmonic",
             "likelihoods": {"gauss": "sigma 0.1, identity response", "poisson": "rate 10 exp(cf)"},
-            "fp32_batched": fp32, "fp64_sequential": fp64,
+            "fp32_batched": fp32, "fp32_batched_budget": fp32_budget, "fp64_sequential": fp64,
             "p50_speedup": fp64["p50_ms"] / fp32["p50_ms"], "p99_speedup": fp64["p99_ms"] / fp32["p99_ms"],
             "throughput_ratio": fp32["solves_per_s"] / fp64["solves_per_s"]}
 

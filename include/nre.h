@@ -379,9 +379,11 @@ int nre_prof_report(char *buf, size_t len);
  * and the power-spectrum hyper-parameters h couple through the amplitude
  * Jacobian G = dA/dh; the preconditioner solves the block system by the Schur
  * complement S = I + c G^T diag(U) G, U_b = sum_{k in b} xi_p[k]^2 / D_k
- * (n_hyper x n_hyper, factored on the host in FP64, applied in FP32).  It
- * changes the CG iterates but not the solution; the stopping test stays on the
- * unpreconditioned residual ||r|| / ||b||.  Setup synchronises `stream`.
+ * (n_hyper x n_hyper; formed and inverted on the device in FP64, through the
+ * Woodbury identity with an n_bins x n_bins matrix when n_hyper > n_bins;
+ * applied in FP32).  It changes the CG iterates but not the solution; the
+ * stopping test stays on the unpreconditioned residual ||r|| / ||b||.  Setup
+ * only enqueues work on `stream` (no host synchronisation).
  * This is an addition for solves to a tolerance: the paper runs plain CG. */
 enum { NRE_PRECOND_NONE = 0, NRE_PRECOND_HARMONIC = 1 };
 int metric_set_precond(nre_metric *m, int kind, nre_stream_t stream);
@@ -389,6 +391,14 @@ int metric_set_precond(nre_metric *m, int kind, nre_stream_t stream);
 /* Device bytes currently held by the library's own allocations (plans,
  * metrics, CG workspaces, servers), summed over all devices. */
 int nre_device_bytes(int64_t *bytes);
+
+/* Kernels that stage tiles with bulk tensor copies (TMA) wait for them on a
+ * shared-memory barrier with an iteration limit (about a second); a wait that
+ * runs out makes the kernel skip the rest of its work and counts here.  Writes
+ * the count of the current device to *count and, if reset != 0, clears it;
+ * synchronises the device.  A nonzero count means that some output of an
+ * earlier call is incomplete. */
+int nre_wait_timeouts(unsigned *count, int reset);
 
 /* ================================================================ serving
  * A request loop for sampling solves: each request is one expansion point of

@@ -99,9 +99,14 @@ struct DevBuf {
     dev_bytes().fetch_add((long long)n);
     return NRE_OK;
   }
+  // Copy of n host bytes, landed on the device when this returns.  A plain
+  // cudaMemcpy from pageable memory may return once the bytes are staged, with
+  // the DMA still queued on the legacy stream, which kernels on non-blocking
+  // streams do not wait for; hence a stream-ordered copy that is waited for.
   int upload(const void* h, size_t n) {
     NRE_TRY(alloc(n));
-    NRE_TRY_CUDA(cudaMemcpy(p, h, n, cudaMemcpyHostToDevice));
+    NRE_TRY_CUDA(cudaMemcpyAsync(p, h, n, cudaMemcpyHostToDevice, cudaStreamPerThread));
+    NRE_TRY_CUDA(cudaStreamSynchronize(cudaStreamPerThread));
     return NRE_OK;
   }
   template <typename T> T* as() const { return static_cast<T*>(p); }

@@ -24,6 +24,7 @@
 #include "metric_internal.cuh"
 
 #include "icr_internal.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -487,6 +488,144 @@ __global__ void __launch_bounds__(ICR4_X * ICR4_Y) k_icr_refine4_t(int nc, const
   st4(g_c + b * gcs + (int64_t)ip * nc + jp0, acc);
 }
 
+// Adjoint with four coarse pixels per thread, its fine rows staged by bulk
+// tensor copies.  A CTA covers coarse rows ip0 .. ip0 + 3 and coarse columns
+// jc0 .. jc0 + 127; the gathers of its threads read fine rows 2 ip0 - 4 ..
+// 2 ip0 + 11 (the children of coarse rows ip0 - 2 .. ip0 + 5) at fine columns
+// 2 jc0 - 2 .. 2 jc0 + 257.  One elected thread loads them as three boxes of
+// the 16 rows: the main box of BW = min(256, 2 nc) columns at x = 2 jc0 and
+// four columns on either side, wrapped around the angular axis (x rounded to
+// 16 bytes; the needed pair is the upper half of the left box and the lower
+// half of the right one).  Rows outside the chart read as zero and are never
+// used (the gather skips coarse rows outside 0 .. nc - 1).  Same arithmetic
+// and order as k_icr_refine4_t.
+constexpr int TRows = 16, TMainMax = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(ICR4_X * ICR4_Y) k_icr_refine4_t_tma(int nc, const T* __restrict__ mats,
+                                                                      const __grid_constant__ CUtensorMap tm_main,
+                                                                      const __grid_constant__ CUtensorMap tm_halo,
+                                                                      T* g_c, int64_t gcs, T* g_xi, int64_t gxs,
+                                                                      const T* base, int64_t bs, unsigned* status) {
+  __shared__ __align__(128) T gm[TRows * TMainMax];
+  __shared__ __align__(128) T hl[TRows * 4];
+  __shared__ __align__(128) T hr[TRows * 4];
+  __shared__ __align__(8) uint64_t bar;
+  const int nf = 2 * nc, BW = nf < TMainMax ? nf : TMainMax;
+  const int tid = threadIdx.y * ICR4_X + threadIdx.x, b = blockIdx.z;
+  const int ip0 = blockIdx.y * ICR4_Y, jc0 = blockIdx.x * (4 * ICR4_X);
+  const int y0 = 2 * ip0 - 4;
+  if (tid == 0) {
+    nre::mbar_init(&bar, 1);
+    nre::mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    nre::mbar_arrive_tx(&bar, (unsigned)((BW + 8) * TRows * sizeof(T)));
+    nre::tma_load_3d(gm, &tm_main, 2 * jc0, y0, b, &bar);
+    nre::tma_load_3d(hl, &tm_halo, jc0 == 0 ? nf - 4 : 2 * jc0 - 4, y0, b, &bar);
+    nre::tma_load_3d(hr, &tm_halo, jc0 + 4 * ICR4_X >= nc ? 0 : 2 * jc0 + 8 * ICR4_X, y0, b, &bar);
+  }
+  const int ip = ip0 + threadIdx.y, jp0 = jc0 + 4 * threadIdx.x;
+  const bool act = ip < nc && jp0 < nc;
+  const int64_t f0 = (int64_t)(2 * ip) * nf + 2 * jp0;
+  // base values while the copies land
+  T b0[8], b1[8];
+  if (act && base) {
+    const T* bb = base + b * bs + f0;
+    ld4(bb, b0);
+    ld4(bb + 4, b0 + 4);
+    ld4(bb + nf, b1);
+    ld4(bb + nf + 4, b1 + 4);
+  }
+  if (!nre::mbar_wait(&bar, 0)) {
+    // give up on this tile; wait (bounded) for the copies in flight before the
+    // shared memory is released
+    if (tid == 0) nre::note_timeout(status);
+    nre::mbar_wait(&bar, 0);
+    return;
+  }
+  if (!act) return;
+  const int lx = 8 * threadIdx.x;  // local fine column of 2 jp0
+  // own children: L^T g (+ base)
+  {
+    const T* r0 = gm + (2 * threadIdx.y + 4) * BW + lx;
+    T g0[8], g1[8];
+    ld4(r0, g0);
+    ld4(r0 + 4, g0 + 4);
+    ld4(r0 + BW, g1);
+    ld4(r0 + BW + 4, g1 + 4);
+    const T* ML = mats + (int64_t)ip * MAT + 36;
+    T l[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) l[k] = __ldg(&ML[k]);
+    T o0[8], o1[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T g[4] = {g0[2 * q], g0[2 * q + 1], g1[2 * q], g1[2 * q + 1]};
+      T o[4];
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = mm; k < 4; ++k) acc += l[k * 4 + mm] * g[k];
+        o[mm] = acc;
+      }
+      o0[2 * q] = o[0];
+      o0[2 * q + 1] = o[1];
+      o1[2 * q] = o[2];
+      o1[2 * q + 1] = o[3];
+    }
+    if (base) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        o0[k] += b0[k];
+        o1[k] += b1[k];
+      }
+    }
+    T* gx = g_xi + b * gxs + f0;
+    st4(gx, o0);
+    st4(gx + 4, o0 + 4);
+    st4(gx + nf, o1);
+    st4(gx + nf + 4, o1 + 4);
+  }
+  // gather R^T g over the coarse pixels whose neighbourhood holds (ip, jp0 + q)
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  // the right neighbour column wraps to 0 at the chart's end, which need not
+  // be the end of the main box (nc not a multiple of 128)
+  const bool left_halo = threadIdx.x == 0, right_halo = lx + 8 >= BW || jp0 + 4 >= nc;
+  const int i_lo = ip - 2 < 0 ? 0 : ip - 2, i_hi = ip + 2 > nc - 1 ? nc - 1 : ip + 2;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const int a = ip - window(nc, i);
+    if (a < 0 || a > 2) continue;
+    const T* MR = mats + (int64_t)i * MAT;
+    T G[2][12];  // fine rows 2i, 2i+1; entry 2 (jj + 1) + c for coarse column jp0 + jj, child column c
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int lr = 2 * i + r - y0;
+      const T* row = gm + lr * BW;
+      G[r][0] = left_halo ? hl[lr * 4 + 2] : row[lx - 2];
+      G[r][1] = left_halo ? hl[lr * 4 + 3] : row[lx - 1];
+      ld4(row + lx, &G[r][2]);
+      ld4(row + lx + 4, &G[r][6]);
+      G[r][10] = right_halo ? hr[lr * 4] : row[lx + 8];
+      G[r][11] = right_halo ? hr[lr * 4 + 1] : row[lx + 9];
+    }
+#pragma unroll
+    for (int bcol = 0; bcol < 3; ++bcol) {
+      const int n = 3 * a + bcol;
+      const T r0 = __ldg(&MR[0 * 9 + n]), r1 = __ldg(&MR[1 * 9 + n]), r2 = __ldg(&MR[2 * 9 + n]),
+              r3 = __ldg(&MR[3 * 9 + n]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t0 = 2 * (q - bcol + 2);
+        acc[q] += r0 * G[0][t0] + r1 * G[0][t0 + 1] + r2 * G[1][t0] + r3 * G[1][t0 + 1];
+      }
+    }
+  }
+  st4(g_c + b * gcs + (int64_t)ip * nc + jp0, acc);
+}
+
 // The coarse end of a chart, level 0 and the refinements whose coarse side is
 // at most kSmallN, in one CTA per sample with the levels in shared memory:
 // as separate launches they were a chain of short latency-bound kernels.
@@ -803,11 +942,27 @@ int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base
     const int nc = p->sizes[l];
     T* gc = bufs[which];
     prof_begin("icr_refine_t", (double)nc * nc * sizeof(T) * B * (base ? 13.0 : 9.0), st);
-    if (nc % 4 == 0 && p->n0 % 4 == 0)
-      k_icr_refine4_t<T><<<dim3((nc / 4 + ICR4_X - 1) / ICR4_X, (nc + ICR4_Y - 1) / ICR4_Y, B),
-                           dim3(ICR4_X, ICR4_Y), 0, st>>>(nc, mats + p->mat_off[l], gin, gis, gc, big,
-                                                          g + p->offsets[l + 1], p->stride,
-                                                          base ? base + p->offsets[l + 1] : nullptr, p->stride);
+    const dim3 g4((nc / 4 + ICR4_X - 1) / ICR4_X, (nc + ICR4_Y - 1) / ICR4_Y, B);
+    const bool tma_ok = p->use_tma && reinterpret_cast<uintptr_t>(gin) % 16 == 0 &&
+                        ((uint64_t)gis * sizeof(T)) % 16 == 0;
+    if (nc % 4 == 0 && p->n0 % 4 == 0 && tma_ok) {
+      // the fine gradient [B][nf][nf] (batch stride gis) as a 3-D tensor
+      const int nf = 2 * nc;
+      const uint64_t dims[3] = {(uint64_t)nf, (uint64_t)nf, (uint64_t)B};
+      const uint64_t strides[2] = {(uint64_t)nf * sizeof(T), (uint64_t)gis * sizeof(T)};
+      const uint32_t box_m[3] = {(uint32_t)(nf < TMainMax ? nf : TMainMax), (uint32_t)TRows, 1u};
+      const uint32_t box_h[3] = {4u, (uint32_t)TRows, 1u};
+      const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+      CUtensorMap tm, th;
+      NRE_TRY(nre::tmap_tiled(&tm, dt, 3, gin, dims, strides, box_m));
+      NRE_TRY(nre::tmap_tiled(&th, dt, 3, gin, dims, strides, box_h));
+      k_icr_refine4_t_tma<T><<<g4, dim3(ICR4_X, ICR4_Y), 0, st>>>(
+          nc, mats + p->mat_off[l], tm, th, gc, big, g + p->offsets[l + 1], p->stride,
+          base ? base + p->offsets[l + 1] : nullptr, p->stride, p->status);
+    } else if (nc % 4 == 0 && p->n0 % 4 == 0)
+      k_icr_refine4_t<T><<<g4, dim3(ICR4_X, ICR4_Y), 0, st>>>(nc, mats + p->mat_off[l], gin, gis, gc, big,
+                                                             g + p->offsets[l + 1], p->stride,
+                                                             base ? base + p->offsets[l + 1] : nullptr, p->stride);
     else
       k_icr_refine_t<T><<<pix_grid((int64_t)nc * nc, B), ICR_THREADS, 0, st>>>(
           nc, mats + p->mat_off[l], gin, gis, gc, big, g + p->offsets[l + 1], p->stride,
@@ -973,6 +1128,8 @@ int icr_create(nre_icr_plan** plan, const icr_chart_params* chart, const icr_ker
   p->r_max = chart->r_max;
   p->rho = kernel->rho;
   p->var = kernel->var;
+  p->status = nre::timeout_word();
+  p->use_tma = p->status != nullptr;
   int64_t off = 0;
   for (int l = 0; l <= n_levels; ++l) {
     const int n = p->n0 << l;

@@ -18,6 +18,10 @@ struct nre_icr_plan {
                                  // 3-D, per level: [n_l][n_l][280]: R (8x27), L (8x8), row-major
   std::vector<int64_t> mat_off;  // element offset of level l in mats
   nre::DevBuf ws_a, ws_b, ws_c;  // per-batch level buffers (3-D: ws_c holds the adjoint's R^T g)
+  // 2-D adjoint: stage fine rows with bulk tensor copies; status counts the
+  // waits that ran out (nre_wait_timeouts)
+  bool use_tma = true;
+  unsigned* status = nullptr;
   // second stream of a batch split into two halves (see icr_forward_t)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -48,15 +48,15 @@ struct nre_metric {
   std::vector<double> cg_host;
   // preconditioner (metric_set_precond)
   int precond = 0;
-  double pc_c = 0.0;      // N * mean(w)
   int pc_nh = 0;          // hyper-parameters handled by the Schur block
   nre::DevBuf pc_G;       // float [n_hyper][n_bins]: dA_b / dh at xi_p
   nre::DevBuf pc_Sinv;    // float [n_hyper][n_hyper]: inverse Schur complement
   nre::DevBuf cg_z, pc_gz, pc_part;
   nre::DevBuf pc_tmp, pc_eye, pc_dG;  // preconditioner set-up scratch
+  nre::DevBuf pc_A, pc_W, pc_T1, pc_Sd;  // FP64 Schur block, its factor, Woodbury product, S^-1
   nre::DevBuf pc_invD, pc_e;          // per pixel: 1 / D and A xi_p / D
   nre::DevBuf pc_Gt;                  // float [n_bins][n_hyper]: G transposed
-  nre::DevBuf pc_cdev;                // double: pc_c on the device
+  nre::DevBuf pc_cdev;                // double: c = N mean(w), on the device
   // residual correction (refine.cu): FP64 metric: residual, product, partials;
   // low precision metric: right-hand side and correction of the inner solve
   nre::DevBuf rf_r, rf_q, rf_part;

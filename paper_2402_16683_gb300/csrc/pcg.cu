@@ -53,9 +53,8 @@ int pc_blocks(int64_t n, int B) {
 template <typename T>
 struct PCArgs {
   int64_t N;            // field entries (the rest of the latent vector is hyper)
-  double c;             // N * mean(w) (set-up kernels)
-  const double* cdev;   // the same on the device (iteration kernels: read at run time,
-                        // so that captured launches follow a re-linearised metric)
+  const double* cdev;   // N * mean(w) on the device (read at run time, so that
+                        // captured launches follow a re-linearised metric)
   AmpView<T> av;        // amplitude at the expansion point (set-up only)
   const T* xi_p;        // expansion point (set-up only)
   const T* invD;        // [N] 1 / D_k = 1 / (1 + c A_k^2)
@@ -445,7 +444,7 @@ __global__ void k_pc_pix(PCArgs<T> pc, T* invD, T* e) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pc.N; i += (int64_t)gridDim.x * blockDim.x) {
     const int bn = pc.av.binned() ? pc.av.bin(i) : -1;
     const double A = double(pc.av.amp(0, i, bn));
-    const double D = 1.0 + pc.c * A * A;
+    const double D = 1.0 + *pc.cdev * A * A;
     invD[i] = T(1.0 / D);
     if (e) e[i] = (bn >= 0 && pc.nb > 0) ? T(A * double(pc.xi_p[i]) / D) : T(0);
   }
@@ -456,9 +455,11 @@ __global__ void k_pc_pix(PCArgs<T> pc, T* invD, T* e) {
 // weight sum), from warp-private histograms folded in warp order; the trip
 // count is uniform over the block (warp reductions of the bins).
 template <typename T>
-__global__ void __launch_bounds__(PC_THREADS) k_pc_setup(const T* w, int64_t N, PCArgs<T> pc, double* part) {
+__global__ void __launch_bounds__(PC_THREADS) k_pc_setup(const T* w, int64_t N, PCArgs<T> pc, double* part,
+                                                        int with_bins) {
   extern __shared__ double hist[];
-  const int nbh = (pc.nb > 0 && pc.c > 0.0) ? pc.nb : 0;
+  const int nbh = (pc.nb > 0 && with_bins) ? pc.nb : 0;
+  const double cc = with_bins ? *pc.cdev : 0.0;
   double* whist = hist + (threadIdx.x >> 5) * nbh;
   for (int i = threadIdx.x; i < (PC_THREADS / 32) * nbh; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pc_setup(const T* w, int64_t N, 
       if (bn >= 0) {
         const double A = double(pc.av.amp(0, i, bn));
         const double xp = double(pc.xi_p[i]);
-        c = xp * xp / (1.0 + pc.c * A * A);
+        c = xp * xp / (1.0 + cc * A * A);
       }
       warp_run_add(bn, c, whist);
     }
@@ -500,12 +501,138 @@ __global__ void k_pc_setup_sum(const double* part, int nblk, int nj, double* out
   }
 }
 
+// ---------------------------------------------------------------- Schur block
+// The preconditioner's hyper block S = I + c G diag(U) G^T (G [nh][nb]) is
+// formed and inverted on the device in FP64, so that a set-up never waits for
+// the host (serving re-linearises a metric per request).
+
+template <typename T>
+__global__ void k_schur_eye(T* e, int nh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nh * nh) e[t] = (t / nh == t % nh) ? T(1) : T(0);
+}
+
+// wb == 0: A = S (nh x nh).  wb == 1: A = K = I + F^T F (nb x nb),
+// F[h][b] = G[h][b] sqrt(c U_b).  One entry per thread, sums in index order.
+__global__ void k_schur_assemble(const double* G, const double* U, const double* cdev, int nh, int nb, int wb,
+                                 double* A) {
+  const int n = wb ? nb : nh;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  const double c = *cdev;
+  double s = 0.0;
+  if (wb) {
+    for (int h = 0; h < nh; ++h) s += G[(int64_t)h * nb + i] * G[(int64_t)h * nb + j];
+    s *= c * sqrt(fmax(U[i], 0.0) * fmax(U[j], 0.0));
+  } else {
+    for (int b = 0; b < nb; ++b) s += G[(int64_t)i * nb + b] * U[b] * G[(int64_t)j * nb + b];
+    s *= c;
+  }
+  A[t] = s + (i == j ? 1.0 : 0.0);
+}
+
+// Inverse of the SPD n x n matrix A (row-major) in three launches:
+// k_chol factors A = L L^T in place (lower triangle; one CTA), k_trinv forms
+// X = L^-1 (one warp per column), k_gram A^-1 = X^T X.  A pivot that is not
+// positive makes k_chol write the identity and flag[0] = 1 (the later kernels
+// then copy it through).
+__global__ void __launch_bounds__(1024) k_chol(double* A, int n, int* flag) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = A[(int64_t)j * n + j];
+      if (!(d > 0.0)) bad = 1;
+      A[(int64_t)j * n + j] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    if (bad) break;
+    const double dj = A[(int64_t)j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * n + j] /= dj;
+    __syncthreads();
+    // trailing lower triangle: A[i][k] -= L[i][j] L[k][j], j < k <= i
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = j + 1 + t / m, k = j + 1 + t % m;
+      if (k <= i) A[(int64_t)i * n + k] -= A[(int64_t)i * n + j] * A[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) flag[0] = bad;
+  if (bad)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// X = L^-1: warp c solves L x = e_c by forward substitution (x_k = 0 for
+// k < c); each dot product is split over the lanes and reduced in lane order.
+__global__ void k_trinv(const double* L, int n, const int* flag, double* X) {
+  const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (c >= n || flag[0]) return;
+  for (int i = 0; i < c; ++i)
+    if (lane == 0) X[(int64_t)i * n + c] = 0.0;
+  for (int i = c; i < n; ++i) {
+    double s = 0.0;
+    for (int k = c + lane; k < i; k += 32) s += L[(int64_t)i * n + k] * X[(int64_t)k * n + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) X[(int64_t)i * n + c] = ((i == c ? 1.0 : 0.0) - s) / L[(int64_t)i * n + i];
+    __syncwarp();
+  }
+}
+
+// A^-1[a][b] = sum_{i >= max(a, b)} X[i][a] X[i][b] (A keeps the identity
+// written by k_chol on a failed factorisation).
+__global__ void k_gram(const double* X, int n, const int* flag, double* A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n || flag[0]) return;
+  const int a = t / n, b = t % n;
+  double s = 0.0;
+  for (int i = a > b ? a : b; i < n; ++i) s += X[(int64_t)i * n + a] * X[(int64_t)i * n + b];
+  A[t] = s;
+}
+
+// T1 = F K^-1 (nh x nb), F[h][a] = G[h][a] sqrt(c U_a).
+__global__ void k_wb_t1(const double* G, const double* U, const double* cdev, const double* Kinv, int nh, int nb,
+                        double* T1) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nh * nb) return;
+  const int h = t / nb, b = t % nb;
+  const double c = *cdev;
+  double s = 0.0;
+  for (int a = 0; a < nb; ++a) s += G[(int64_t)h * nb + a] * sqrt(c * fmax(U[a], 0.0)) * Kinv[(int64_t)a * nb + b];
+  T1[t] = s;
+}
+
+// S^-1 = I - T1 F^T (nh x nh).
+__global__ void k_wb_s(const double* G, const double* U, const double* cdev, const double* T1, int nh, int nb,
+                       double* Sinv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nh * nh) return;
+  const int i = t / nh, j = t % nh;
+  const double c = *cdev;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += T1[(int64_t)i * nb + b] * G[(int64_t)j * nb + b] * sqrt(c * fmax(U[b], 0.0));
+  Sinv[t] = (i == j ? 1.0 : 0.0) - s;
+}
+
+// FP32 copies for the iteration kernels: G [nh][nb], G^T [nb][nh], S^-1.
+__global__ void k_schur_f32(const double* G, const double* Sinv, int nh, int nb, float* Gf, float* Gtf, float* Sf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nh * nb) {
+    const int h = t / nb, b = t % nb;
+    Gf[t] = float(G[t]);
+    Gtf[(int64_t)b * nh + h] = float(G[t]);
+  }
+  if (t < nh * nh) Sf[t] = float(Sinv[t]);
+}
+
 template <typename T>
 PCArgs<T> pc_args(nre_metric* m) {
   nre_cf_plan* p = m->cf;
   PCArgs<T> a{};
   a.N = p->N;
-  a.c = m->pc_c;
   a.cdev = m->pc_cdev.as<double>();
   a.xi_p = m->xi_p.as<T>();
   const bool model = binned_model(p);
@@ -517,44 +644,6 @@ PCArgs<T> pc_args(nre_metric* m) {
   return a;
 }
 
-// In-place Cholesky and inverse of an SPD n x n matrix (host, FP64).
-bool spd_inverse(std::vector<double>& A, int n, std::vector<double>& inv) {
-  std::vector<double> L = A;
-  for (int j = 0; j < n; ++j) {
-    double s = L[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(s > 0.0)) return false;
-    const double d = std::sqrt(s);
-    L[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double t = L[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = t / d;
-    }
-  }
-  std::vector<double> Lt((size_t)n * n);  // L^T, so both substitutions read rows
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k <= i; ++k) Lt[(size_t)k * n + i] = L[(size_t)i * n + k];
-  inv.assign((size_t)n * n, 0.0);
-  std::vector<double> col(n);
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < c; ++i) col[i] = 0.0;  // L^-1 e_c vanishes above c
-    for (int i = c; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      const double* Li = &L[(size_t)i * n];
-      for (int k = c; k < i; ++k) s -= Li[k] * col[k];
-      col[i] = s / Li[i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double s = col[i];
-      const double* Lti = &Lt[(size_t)i * n];
-      for (int k = i + 1; k < n; ++k) s -= Lti[k] * col[k];
-      col[i] = s / Lti[i];
-    }
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = col[i];
-  }
-  return true;
-}
 
 template <typename T>
 int setup_t(nre_metric* m, cudaStream_t st) {
@@ -567,77 +656,71 @@ int setup_t(nre_metric* m, cudaStream_t st) {
   const int sblk = sm_count();
   NRE_TRY(ensure(dbuf, (size_t)(1 + sblk) * (1 + nb) * sizeof(double)));
   double* spart = dbuf.as<double>() + (1 + nb);
-  // pass 1: mean weight
+  NRE_TRY(ensure(m->pc_cdev, sizeof(double)));
+  NRE_TRY(ensure(m->pc_invD, (size_t)N * sizeof(T)));
+  if (model) NRE_TRY(ensure(m->pc_e, (size_t)N * sizeof(T)));
   PCArgs<T> a = pc_args<T>(m);
-  a.c = 0.0;
+  // pass 1: c = sum(w) = N mean(w), kept on the device
   prof_begin("pc_setup", (double)N * sizeof(T), st);
   NRE_TRY(pc_smem(k_pc_setup<T>, (size_t)(PC_THREADS / 32) * (nb > 0 ? nb : 1) * sizeof(double)));
   k_pc_setup<T><<<sblk, PC_THREADS, (size_t)(PC_THREADS / 32) * (nb > 0 ? nb : 1) * sizeof(double), st>>>(
-      m->w.as<T>(), N, a, spart);
-  k_pc_setup_sum<<<1, 256, 0, st>>>(spart, sblk, 1 + nb, dbuf.as<double>());
+      m->w.as<T>(), N, a, spart, 0);
+  k_pc_setup_sum<<<1, 256, 0, st>>>(spart, sblk, 1, m->pc_cdev.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();
-  double wsum = 0.0;
-  NRE_TRY_CUDA(cudaMemcpyAsync(&wsum, dbuf.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-  NRE_TRY_CUDA(cudaStreamSynchronize(st));
-  m->pc_c = wsum;  // N * mean(w) = sum(w)
   m->pc_nh = nh;
-  NRE_TRY(ensure(m->pc_cdev, sizeof(double)));
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_cdev.p, &m->pc_c, sizeof(double), cudaMemcpyHostToDevice, st));
   // per-pixel coefficients 1 / D and A xi_p / D
-  NRE_TRY(ensure(m->pc_invD, (size_t)N * sizeof(T)));
-  if (model) NRE_TRY(ensure(m->pc_e, (size_t)N * sizeof(T)));
-  a.c = m->pc_c;
   prof_begin("pc_setup", (double)N * 3 * sizeof(T), st);
   k_pc_pix<T><<<304, PC_THREADS, 0, st>>>(a, m->pc_invD.as<T>(), model ? m->pc_e.as<T>() : nullptr);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   if (!model) return NRE_OK;
-  // pass 2: U_b with the final c
-  a.c = m->pc_c;
+  // pass 2: U_b with the final c (dbuf[1 .. nb])
   prof_begin("pc_setup", (double)N * 2 * sizeof(T), st);
   k_pc_setup<T><<<sblk, PC_THREADS, (size_t)(PC_THREADS / 32) * nb * sizeof(double), st>>>(m->w.as<T>(), N, a,
-                                                                                          spart);
+                                                                                          spart, 1);
   k_pc_setup_sum<<<1, 256, 0, st>>>(spart, sblk, 1 + nb, dbuf.as<double>());
   prof_end(st);
   NRE_CHECK_LAUNCH();
   // amplitude Jacobian G[h][b] = dA_b / dh: JVPs along the unit vectors
-  std::vector<T> eye((size_t)nh * nh, T(0));
-  for (int h = 0; h < nh; ++h) eye[(size_t)h * nh + h] = T(1);
   DevBuf& deye = m->pc_eye;
   DevBuf& dG = m->pc_dG;
-  NRE_TRY(ensure(deye, eye.size() * sizeof(T)));
-  NRE_TRY_CUDA(cudaMemcpyAsync(deye.p, eye.data(), eye.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  NRE_TRY(ensure(deye, (size_t)nh * nh * sizeof(T)));
   NRE_TRY(ensure(dG, (size_t)nh * nb * sizeof(double)));
+  k_schur_eye<T><<<(nh * nh + 255) / 256, 256, 0, st>>>(deye.as<T>(), nh);
+  NRE_CHECK_LAUNCH();
   NRE_TRY(amp_jvp<T>(amp_prior_of(p), m->state.as<double>(), 0, deye.as<T>(), nh, dG.as<double>(), nh, st));
-  std::vector<double> G((size_t)nh * nb), U(nb);
-  NRE_TRY_CUDA(cudaMemcpyAsync(G.data(), dG.p, G.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  NRE_TRY_CUDA(cudaMemcpyAsync(U.data(), dbuf.as<double>() + 1, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  NRE_TRY_CUDA(cudaStreamSynchronize(st));
-  // S = I + c G diag(U) G^T (G stored [h][b])
-  std::vector<double> S((size_t)nh * nh), Sinv, GU((size_t)nh * nb);
-  const double c = m->pc_c;
-  for (size_t i = 0; i < GU.size(); ++i) GU[i] = G[i] * U[i % nb];
-  for (int i = 0; i < nh; ++i) {
-    const double* gi = &GU[(size_t)i * nb];
-    for (int j = 0; j <= i; ++j) {
-      const double* gj = &G[(size_t)j * nb];
-      double s = 0.0;
-      for (int k = 0; k < nb; ++k) s += gi[k] * gj[k];
-      S[(size_t)i * nh + j] = S[(size_t)j * nh + i] = c * s + (i == j ? 1.0 : 0.0);
-    }
+  // S^-1 of S = I + c G diag(U) G^T on the device, in FP64: directly when
+  // nh <= nb, else by the Woodbury identity through the nb x nb matrix
+  // K = I + F^T F, F = G diag(sqrt(c U)):  S^-1 = I - F K^-1 F^T
+  const bool wb = nh > nb;
+  const int n = wb ? nb : nh;
+  NRE_TRY(ensure(m->pc_A, (size_t)n * n * sizeof(double)));
+  NRE_TRY(ensure(m->pc_W, (size_t)n * n * sizeof(double) + 16));  // X = L^-1 and a flag
+  NRE_TRY(ensure(m->pc_Sd, (size_t)nh * nh * sizeof(double)));
+  if (wb) NRE_TRY(ensure(m->pc_T1, (size_t)nh * nb * sizeof(double)));
+  const double* c = m->pc_cdev.as<double>();
+  const double* U = dbuf.as<double>() + 1;
+  const double* G = dG.as<double>();
+  double* A = m->pc_A.as<double>();
+  prof_begin("pc_schur", (double)(nh * nb + 2 * n * n) * sizeof(double), st);
+  k_schur_assemble<<<(n * n + 255) / 256, 256, 0, st>>>(G, U, c, nh, nb, wb ? 1 : 0, A);
+  int* flag = reinterpret_cast<int*>(m->pc_W.as<double>() + (size_t)n * n);
+  k_chol<<<1, 1024, 0, st>>>(A, n, flag);
+  k_trinv<<<(n + 7) / 8, 256, 0, st>>>(A, n, flag, m->pc_W.as<double>());
+  k_gram<<<(n * n + 255) / 256, 256, 0, st>>>(m->pc_W.as<double>(), n, flag, A);
+  if (wb) {
+    k_wb_t1<<<(nh * nb + 255) / 256, 256, 0, st>>>(G, U, c, A, nh, nb, m->pc_T1.as<double>());
+    k_wb_s<<<(nh * nh + 255) / 256, 256, 0, st>>>(G, U, c, m->pc_T1.as<double>(), nh, nb, m->pc_Sd.as<double>());
   }
-  if (!spd_inverse(S, nh, Sinv)) return set_error(NRE_EINVAL, "preconditioner Schur block is not positive definite");
-  std::vector<float> Gf(G.begin(), G.end()), Sf(Sinv.begin(), Sinv.end()), Gtf((size_t)nb * nh);
-  for (int h = 0; h < nh; ++h)
-    for (int k = 0; k < nb; ++k) Gtf[(size_t)k * nh + h] = Gf[(size_t)h * nb + k];
-  NRE_TRY(ensure(m->pc_G, Gf.size() * sizeof(float)));
-  NRE_TRY(ensure(m->pc_Gt, Gtf.size() * sizeof(float)));
-  NRE_TRY(ensure(m->pc_Sinv, Sf.size() * sizeof(float)));
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_G.p, Gf.data(), Gf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_Gt.p, Gtf.data(), Gtf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  NRE_TRY_CUDA(cudaMemcpyAsync(m->pc_Sinv.p, Sf.data(), Sf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  NRE_TRY_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  NRE_TRY(ensure(m->pc_G, (size_t)nh * nb * sizeof(float)));
+  NRE_TRY(ensure(m->pc_Gt, (size_t)nb * nh * sizeof(float)));
+  NRE_TRY(ensure(m->pc_Sinv, (size_t)nh * nh * sizeof(float)));
+  k_schur_f32<<<(nh * (nh > nb ? nh : nb) + 255) / 256, 256, 0, st>>>(G, wb ? m->pc_Sd.as<double>() : A, nh, nb,
+                                                                      m->pc_G.as<float>(), m->pc_Gt.as<float>(),
+                                                                      m->pc_Sinv.as<float>());
+  prof_end(st);
+  NRE_CHECK_LAUNCH();
   return NRE_OK;
 }
 

@@ -111,8 +111,10 @@ uint64_t footprint(const nre_serve_req* r, const Geom& g, int dtype) {
   // CG workspace (r, p, q and z) and scalars
   b += (pc ? 4 : 3) * a256(B * S * E) + a256(B * CG_SC_N * 8) + a256(3 * B * 64 * 8 + B * 4);
   if (pc && nb > 0)
-    b += a256(B * 64 * nb * 8) + a256(B * nb * 8) + 2 * a256(nh * nb * 4) + a256(nh * nh * 4) + a256((1 + nb) * 8) +
-         a256(nh * nh * E) + a256(nh * nb * 8) + 2 * a256(N * E);
+    b += a256(B * 64 * nb * 8) + a256(B * nb * 8) + 2 * a256(nh * nb * 4) + a256(nh * nh * 4) +
+         a256((1 + (size_t)sm_count()) * (1 + nb) * 8) + a256(nh * nh * E) + a256(nh * nb * 8) + 2 * a256(N * E) +
+         // the FP64 Schur block: its matrix and factor (n = min(nh, nb)), S^-1, the Woodbury product
+         2 * a256(std::min(nh, nb) * std::min(nh, nb) * 8 + 16) + a256(nh * nh * 8) + a256(nh * nb * 8);
   else if (pc)
     b += a256(8 + 8) + a256(N * E);
   // slot buffers: xi_p, b, x (+ eta and the formed right-hand sides)
@@ -444,6 +446,9 @@ void nre_server::run_prep() {
         lk.unlock();
         for (SlotObj* d : drop) delete d;
         lk.lock();
+        // another admission thread may have taken the head of the queue (or
+        // the last free slot) while the lock was released: start over
+        continue;
       }
       if (reserved + j->est > cfg.hbm_budget_bytes) {
         // wait for a running request to release memory

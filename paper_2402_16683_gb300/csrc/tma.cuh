@@ -1,0 +1,86 @@
+// Bulk tensor copies (TMA) into shared memory, completing on an mbarrier.
+//
+// Tensor maps cover buffers of this device only and are never multicast.  A
+// tiled load must start at an innermost coordinate whose byte offset is a
+// multiple of 16; callers round x down and index from the remainder.  Every
+// wait on an mbarrier is bounded: after the limit the waiter records a timeout
+// in a status word that the host reads, and the kernel skips its remaining
+// work (after waiting, again bounded, for its copies in flight).
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace nre {
+
+// Tiled tensor map of a row-major array: dims[0] innermost (elements),
+// strides_b[d] the byte stride of dimension d + 1 (multiples of 16), box[d]
+// the copied extent (box[0] * element size a multiple of 16, each <= 256).
+// Out-of-range elements of a box read as zero.
+int tmap_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const uint64_t* dims,
+               const uint64_t* strides_b, const uint32_t* box);
+
+// Per-device count of waits that ran out (allocated on first use; call it once
+// outside stream capture, e.g. when a plan is created).
+unsigned* timeout_word();
+
+// Iterations of a bounded mbarrier wait (each try_wait suspends for a
+// hardware-chosen time slice): about a second on a GB300 before giving up.
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Make the initialised barriers visible to the async proxy (TMA).
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) accesses of it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Arrive on the barrier and announce `bytes` of transactions for this phase.
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase of the given parity; false after kWaitLimit tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Record a wait that ran out (status[0] counts them).
+__device__ __forceinline__ void note_timeout(unsigned* status) {
+  if (status) atomicAdd(status, 1u);
+}
+
+}  // namespace nre

@@ -29,7 +29,20 @@ def _dev(plan, x):
     return plan.pad(torch.tensor(np.atleast_2d(x), dtype=plan.dtype, device=DEV))
 
 
-@pytest.mark.parametrize("n0,levels,dtype", [(8, 3, "f64"), (4, 4, "f64"), (8, 7, "f32"), (6, 2, "f32")])
+def _timeouts():
+    import ctypes as C
+
+    from paper_2402_16683_gb300 import _lib
+    n = C.c_uint(0)
+    _lib.check(_lib.load().nre_wait_timeouts(C.byref(n), 1))
+    return n.value
+
+
+# (4, 6) and (8, 7): levels of coarse side 64 .. 512 run the adjoint whose fine
+# rows arrive by bulk tensor copies (FP64 and FP32); (12, 5): coarse sides 48,
+# 96, 192, where the angular wrap falls inside a tile
+@pytest.mark.parametrize("n0,levels,dtype", [(8, 3, "f64"), (4, 4, "f64"), (4, 6, "f64"), (8, 7, "f32"),
+                                             (12, 5, "f32"), (6, 2, "f32")])
 def test_icr_forward_vjp(n0, levels, dtype):
     if dtype == "f64":
         tol, kap = icr_fp64_tol(n0, levels)
@@ -50,6 +63,7 @@ def test_icr_forward_vjp(n0, levels, dtype):
         assert rel_max(s[b], ref) <= tol
         assert rel_max(jv[b], ref) <= tol
         assert rel_max(gr[b], oc.vjp(ct[b])) <= tol
+    assert _timeouts() == 0
 
 
 def test_icr_autograd_fd_and_oracle_gradient():

@@ -254,6 +254,40 @@ def test_serve_evicts_idle_objects_under_budget():
     srv.close()
 
 
+def test_serve_concurrent_admission_with_eviction():
+    """Many requests of six keys at once under a budget of about two slot
+    objects, with several admission threads evicting idle objects: every
+    request runs once, on its own slot object, with the result bitwise equal to
+    the same request served alone, and the slot-object accounting balances."""
+    nre = _nre()
+    keys = [((64, 64), "gauss"), ((64, 64), "poisson"), ((32, 32, 32), "gauss"), ((32, 32, 32), "poisson"),
+            ((4096,), "gauss"), ((4096,), "poisson")]
+    probe = nre.Server(max_slots=1)
+    fmax = max(probe.footprint(s, n_samples=4) for s, _ in keys)
+    probe.close()
+    reqs = []
+    for i in range(24):
+        s, lik = keys[i % len(keys)]
+        xi_p, b, _, x = _inputs(s, 4, 4000 + i)
+        reqs.append((s, lik, xi_p, b, None, x))
+    ref = [(s, l, xp, b, e, np.zeros_like(x)) for (s, l, xp, b, e, x) in reqs]
+    alone = nre.Server(max_slots=1)
+    res_ref = _run(alone, ref, "identity")
+    alone.close()
+    budget = int(2.2 * fmax)
+    srv = nre.Server(hbm_budget_bytes=budget, max_slots=4, prep_threads=8)
+    res = _run(srv, reqs, "identity")
+    st = srv.stats()
+    srv.close()
+    for (s, lik, _, _, _, x), (_, _, _, _, _, xr), r, rr in zip(reqs, ref, res, res_ref):
+        assert r["status"] == 0 and rr["status"] == 0, (s, lik, r["error"], rr["error"])
+        assert np.array_equal(x, xr), (s, lik, _rel(x, xr))
+    assert st["completed"] == len(reqs) and st["active"] == 0 and st["queued"] == 0
+    assert st["evicted"] > 0 and st["peak_reserved"] <= budget
+    assert st["created"] - st["evicted"] == st["idle_objects"]
+    assert st["created"] + st["reused"] == len(reqs)
+
+
 def test_serve_refined_true_residual_alone_vs_mix_and_footprint():
     """Requests with residual correction: FP32 solves, FP64 residuals.  Every
     solution's true residual ||b - M64 x|| / ||b|| (checked here with an FP64
