@@ -136,6 +136,27 @@ bool pair_matrices(const nre_icr_plan* p, int level, int i, int j, double* out) 
 
 // ---------------------------------------------------------------- kernels
 // s0[b] = L0 xi0[b]: one warp per output row.
+// Four consecutive values as 16-byte vectors (two for double).
+template <typename T>
+__device__ __forceinline__ void ld4v(const T* p, T* o) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), c = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4v(T* p, const T* o) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+  }
+}
+
 template <typename T>
 __global__ void k_icr3_level0(const T* L0, const T* xi, int64_t xs, T* s0, int64_t ss, int n) {
   const int b = blockIdx.y, lane = threadIdx.x & 31;
@@ -211,6 +232,92 @@ __global__ void __launch_bounds__(128) k_icr3_refine(int nc, const T* __restrict
       const int64_t o = ((int64_t)(2 * i + a) * nf + (2 * j + bb)) * nf + 2 * k + cc;
       f[o] = scale ? acc * scale[o] : acc;
     }
+  }
+}
+
+// Forward with four consecutive coarse voxels (k0 .. k0 + 3) per thread, for
+// coarse sides of 64 and up (nc % 4 == 0): each matrix entry read from shared
+// memory serves four voxels, the 3 x 3 neighbourhood rows move as 16-byte
+// vectors plus one halo value on either side (periodic in k), and the
+// children of each (a, b) child row go out as two 16-byte stores.  A CTA of
+// 128 threads covers 128 / (nc / 4) pairs (i, j), each with its matrices in
+// shared memory.  Same arithmetic and order per output as k_icr3_refine.
+constexpr int ICR3_T = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(ICR3_T, 3) k_icr3_refine4(int nc, const T* __restrict__ mats, const T* sc,
+                                                            int64_t scs, const T* xif, int64_t xs, T* sf, int64_t sfs,
+                                                            const T* __restrict__ scale) {
+  extern __shared__ __align__(16) unsigned char sm3_raw[];
+  T* Ms = reinterpret_cast<T*>(sm3_raw);
+  const int tp = nc / 4, pp = ICR3_T / tp;  // threads per pair, pairs per CTA
+  const int b = blockIdx.y;
+  const int64_t pair0 = (int64_t)blockIdx.x * pp;
+  for (int e = threadIdx.x; e < pp * MAT3; e += blockDim.x) Ms[e] = mats[pair0 * MAT3 + e];
+  __syncthreads();
+  const int pl = threadIdx.x / tp, t = threadIdx.x - pl * tp;
+  const int64_t pair = pair0 + pl;
+  const int i = (int)(pair / nc), j = (int)(pair - (int64_t)i * nc);
+  const T* M = Ms + pl * MAT3;
+  const int wi = win(nc, i), wj = win(nc, j), nf = 2 * nc;
+  const int k0 = 4 * t;
+  const int km = k0 == 0 ? nc - 1 : k0 - 1, kp = k0 + 4 == nc ? 0 : k0 + 4;
+  const T* c = sc + b * scs;
+  // neighbourhood rows (A, B): entries k0 - 1 .. k0 + 4
+  T nbv[9][6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+      const T* rowp = c + ((int64_t)(wi + a) * nc + (wj + bb)) * nc;
+      T* r = nbv[3 * a + bb];
+      r[0] = rowp[km];
+      ld4v(rowp + k0, r + 1);
+      r[5] = rowp[kp];
+    }
+  // excitations of the children rows (a, b): entries 2 k0 .. 2 k0 + 7
+  T xe[4][8];
+  const T* x = xif + b * xs;
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    const int64_t o = ((int64_t)(2 * i + (ab >> 1)) * nf + (2 * j + (ab & 1))) * nf + 2 * k0;
+    ld4v(x + o, xe[ab]);
+    ld4v(x + o + 4, xe[ab] + 4);
+  }
+  T* f = sf + b * sfs;
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    T out[8];  // entry 2 kk + cc
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int m = 2 * ab + cc;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int n = 0; n < 27; ++n) {
+        const T w = M[m * 27 + n];
+        const T* r = nbv[n / 3];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc[kk] += w * r[kk + n % 3];
+      }
+#pragma unroll
+      for (int q = 0; q <= m; ++q) {
+        const T w = M[216 + m * 8 + q];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc[kk] += w * xe[q >> 1][2 * kk + (q & 1)];
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) out[2 * kk + cc] = acc[kk];
+    }
+    const int64_t o = ((int64_t)(2 * i + (ab >> 1)) * nf + (2 * j + (ab & 1))) * nf + 2 * k0;
+    if (scale) {
+      T sv[8];
+      ld4v(scale + o, sv);
+      ld4v(scale + o + 4, sv + 4);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) out[e] *= sv[e];
+    }
+    st4v(f + o, out);
+    st4v(f + o + 4, out + 4);
   }
 }
 
@@ -360,9 +467,26 @@ int icr3_forward_t(nre_icr_plan* p, const T* xi, T* s, int B, const T* scale, cu
     T* out = last ? s : bufs[(l + 1) & 1];
     const int64_t os = last ? p->n_out : big;
     prof_begin("icr3_refine", (double)B * nf3 * sizeof(T) * (2.0 + 1.0 / 8) + (double)nc * nc * MAT3 * sizeof(T), st);
-    k_icr3_refine<T><<<dim3(nc * nc, B), 128, 0, st>>>(nc, mats + p->mat_off[l], bufs[l & 1], big,
-                                                        xi + p->offsets[l + 1], p->stride, out, os,
-                                                        last ? scale : nullptr);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      // whole pairs per CTA (nc / 4 a power of two up to the CTA size) and
+      // 16-byte aligned rows of every array the kernel reads as vectors
+      auto al = [](const void* q) { return reinterpret_cast<uintptr_t>(q) % 16 == 0; };
+      const T* xl = xi + p->offsets[l + 1];
+      if (nc >= 64 && nc % 4 == 0 && nc / 4 <= ICR3_T && ICR3_T % (nc / 4) == 0 && al(xl) && al(out) &&
+          al(bufs[l & 1]) && p->stride % 4 == 0 && os % 4 == 0 && big % 4 == 0 && (!last || !scale || al(scale))) {
+        const int pp = ICR3_T / (nc / 4);
+        k_icr3_refine4<T><<<dim3((unsigned)((int64_t)nc * nc / pp), B), ICR3_T, pp * MAT3 * sizeof(T), st>>>(
+            nc, mats + p->mat_off[l], bufs[l & 1], big, xi + p->offsets[l + 1], p->stride, out, os,
+            last ? scale : nullptr);
+        done = true;
+      }
+    }
+    if (!done) {
+      k_icr3_refine<T><<<dim3(nc * nc, B), 128, 0, st>>>(nc, mats + p->mat_off[l], bufs[l & 1], big,
+                                                          xi + p->offsets[l + 1], p->stride, out, os,
+                                                          last ? scale : nullptr);
+    }
     prof_end(st);
     NRE_CHECK_LAUNCH();
   }

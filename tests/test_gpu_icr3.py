@@ -26,8 +26,10 @@ def _dev(plan, x):
     return plan.pad(torch.tensor(np.atleast_2d(x), dtype=plan.dtype, device=DEV))
 
 
+# (4, 5) / (8, 3): the FP32 refinement of coarse side 64 runs the kernel that
+# takes four coarse voxels per thread
 @pytest.mark.parametrize("n0,levels,dtype,rho", [(4, 2, "f64", 0.3), (3, 3, "f64", 0.4), (4, 3, "f32", 0.3),
-                                                 (5, 2, "f32", 0.5)])
+                                                 (5, 2, "f32", 0.5), (4, 5, "f32", 0.3), (8, 3, "f32", 0.3)])
 def test_icr3_forward_jvp_vjp(n0, levels, dtype, rho):
     if dtype == "f64":
         tol, kap = icr3_fp64_tol(n0, levels, rho)
