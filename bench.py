@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--serve-budget-requests", type=int, default=500,
                     help="requests of the stream's start that the budgeted run serves")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-sustained-requests", type=int, default=300,
+                    help="requests of the slower stream served by the FP32 server alone (0: skip)")
+    ap.add_argument("--serve-sustained-rate", type=float, default=10.0)
     ap.add_argument("--serve-plain-cap-s", type=float, default=90.0,
                     help="stop the sequential FP64 arm after this many seconds")
     ap.add_argument("--serve-timeout-s", type=float, default=900.0,
@@ -571,32 +574,42 @@ def run_metric_grids(args, lib):
                             "frac": (x[2] / (x[1] / 1e3) / 1e9 / peak) if x[1] else None}
                         for k, x in kern.items()}}
         if len(shape) == 3:
-            # the 3-D masked workload's batched sample solve: plain FP32 CG on
-            # the MGVI right-hand sides to a recursive 1e-5, then the FP64 true
-            # residual ||b - M x|| / ||b|| of each solution from an FP64 metric
-            # at the same expansion point
+            # the 3-D masked workload's batched sample solve: FP32 CG with the
+            # harmonic preconditioner on the MGVI right-hand sides to a
+            # recursive 1e-5 (timed), the FP64 true residual ||b - M x|| / ||b||
+            # of each solution from an FP64 metric at the same expansion point,
+            # then the same systems with FP64 residual correction around the
+            # FP32 PCG to a true 1e-5
             eta = torch.tensor(np.random.default_rng(synth.SEED_RHS).standard_normal((B, plan.n_field)),
                                dtype=torch.float32, device=dev)
             M.mgvi_rhs(v, eta, out=o)
+            M.set_precond("harmonic")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             x3, its, rel, st_ = M.cg(o, rtol=1e-5, maxiter=args.cg3d_maxiter)
             torch.cuda.synchronize()
             secs = time.perf_counter() - t0
             p64 = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float64)
-            M64 = nre.Metric(p64, lik, p64.pad(xi_p.double()[None])[0], max_batch=1)
-            true = []
-            for i in range(B):
-                xi64 = x3[i:i + 1].double()
-                bi64 = o[i:i + 1].double()
-                r64 = bi64 - M64.apply(xi64)
-                true.append(float(p64.unpad(r64).norm() / p64.unpad(bi64).norm()))
-            del M64, p64
+            M64 = nre.Metric(p64, lik, p64.pad(xi_p.double()[None])[0], max_batch=B)
+            o64 = o.double()
+            r64 = o64 - M64.apply(x3.double())
+            true = [float(p64.unpad(r64)[i].norm() / p64.unpad(o64)[i].norm()) for i in range(B)]
+            del r64
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, its_r, true_r, passes, st_r = M.cg_refined(M64, o64, rtol=1e-5, max_outer=8, inner_rtol=1e-3,
+                                                          inner_maxiter=args.cg3d_maxiter)
+            torch.cuda.synchronize()
+            secs_r = time.perf_counter() - t0
+            del M64, p64, o64
             out[f"{len(shape)}d_{name}"]["cg_to_1e-5"] = {
-                "maxiter": args.cg3d_maxiter, "iterations": [int(i) for i in its],
-                "relres": [float(r) for r in rel], "true_relres_fp64": true, "converged": st_ == 0,
-                "seconds": secs, "precond": "none",
-                "likelihood": "gauss sigma 0.05 on the field (identity response), 10 % mask"}
+                "maxiter": args.cg3d_maxiter, "precond": "harmonic",
+                "likelihood": "gauss sigma 0.05 on the field (identity response), 10 % mask",
+                "fp32_pcg": {"iterations": [int(i) for i in its], "relres": [float(r) for r in rel],
+                             "true_relres_fp64": true, "converged_recursive": st_ == 0, "seconds": secs},
+                "refined": {"passes": passes, "inner_iterations": [int(i) for i in its_r],
+                            "true_relres_fp64": [float(r) for r in true_r], "converged": st_r == 0,
+                            "seconds": secs_r}}
         del M, v, o
         torch.cuda.empty_cache()
     out["icr_8_to_1024"] = run_icr(args, lib, flush, stream, peak)
@@ -748,8 +761,11 @@ def run_next_rows(args, lib, flush, stream, peak):
     kl = nre.KL(plan, lik, data, deltas.contiguous())
     kl.set_position(xbar)
     res = {"samples": 4, "grid": list(shape)}
-    ms, kern = _timed_traced(lib, lambda: kl.energy_gradient(), n, flush, stream)
-    res["energy_gradient"] = _leg_stats(ms, kern, n, peak, 1, "per_s")
+    # energy and gradient at a position: S forward models, the likelihood
+    # terms and S adjoints (set_position evaluates both; energy_gradient
+    # returns them)
+    ms, kern = _timed_traced(lib, lambda: kl.set_position(xbar), n, flush, stream)
+    res["energy_and_gradient"] = _leg_stats(ms, kern, n, peak, 1, "per_s")
     KM = kl.metric()
     v = plan.pad(torch.tensor(g.standard_normal((1, plan.latent_size)), dtype=torch.float32, device=dev))
     o = torch.empty_like(v)
@@ -812,7 +828,9 @@ def run_serve_child(args):
     cmd = [sys.executable, os.path.abspath(__file__), "--serve-only",
            "--serve-requests", str(args.serve_requests), "--serve-budget-gb", str(args.serve_budget_gb),
            "--serve-budget-requests", str(args.serve_budget_requests), "--serve-slots", str(args.serve_slots),
-           "--serve-plain-cap-s", str(args.serve_plain_cap_s)]
+           "--serve-plain-cap-s", str(args.serve_plain_cap_s),
+           "--serve-sustained-requests", str(args.serve_sustained_requests),
+           "--serve-sustained-rate", str(args.serve_sustained_rate)]
     try:
         p = subprocess.run(cmd, capture_output=True, text=True, timeout=args.serve_timeout_s)
     except subprocess.TimeoutExpired:
@@ -963,7 +981,9 @@ def run_serve(args):
                "slots": args.serve_slots, "graph_replays": st["graph_replays"], "chunks": st["chunks"],
                "slot_objects_created": st["created"], "reused": st["reused"], "evicted": st["evicted"],
                "peak_reserved_gb": st["peak_reserved"] / 1e9, "budget_gb": st["budget"] / 1e9,
-               "failed": len(results) - ok32, "errors": errors, "by_class": by_class}
+               "failed": len(results) - ok32, "errors": errors, "by_class": by_class,
+               # the time the server needed for the stream against the span of its arrivals
+               "busy_s": end32 - t0, "arrival_span_s": reqs[-1][0]}
         return res, kept
 
     fp32, kept32 = serve_fp32(0, reqs)
@@ -971,6 +991,14 @@ def run_serve(args):
     if args.serve_budget_gb > 0:
         fp32_budget, _ = serve_fp32(int(args.serve_budget_gb * 1e9), reqs[:args.serve_budget_requests])
         fp32_budget["requests"] = min(len(reqs), args.serve_budget_requests)
+    # a slower stream of the same mix that one server keeps up with: latency
+    # without the queueing of the 50/s stream
+    fp32_sustained = None
+    if args.serve_sustained_requests > 0:
+        reqs_s = synth.request_stream(synth.SEED_STREAM + 1, n=args.serve_sustained_requests,
+                                      rate=args.serve_sustained_rate)
+        fp32_sustained, _ = serve_fp32(0, reqs_s)
+        fp32_sustained.update({"requests": len(reqs_s), "rate_hz": args.serve_sustained_rate})
 
     # ---- plain sequential FP64 path
     plans = {shape: nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR),
@@ -1051,7 +1079,8 @@ def run_serve(args):
     return {"requests": len(reqs), "rate_hz": 50.0, "samples_per_request": SERVE_SAMPLES, "rtol": SERVE_RTOL,
             "grids": [list(s) for s in synth.SERVE_SHAPES], "precond": "harmonic",
             "likelihoods": {"gauss": "sigma 0.1, identity response", "poisson": "rate 10 exp(cf)"},
-            "fp32_batched": fp32, "fp32_batched_budget": fp32_budget, "fp64_sequential": fp64,
+            "fp32_batched": fp32, "fp32_batched_budget": fp32_budget, "fp32_batched_sustained": fp32_sustained,
+            "fp64_sequential": fp64,
             "p50_speedup": fp64["p50_ms"] / fp32["p50_ms"], "p99_speedup": fp64["p99_ms"] / fp32["p99_ms"],
             "throughput_ratio": fp32["solves_per_s"] / fp64["solves_per_s"]}
 

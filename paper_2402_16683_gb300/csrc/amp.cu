@@ -365,13 +365,13 @@ __global__ void k_jac_store(const double* Jt, int nh, int nb, float* G, float* G
 // its FP32 rate).  Staging dh in shared memory measured slower: the barrier
 // puts a second round trip on the path of this latency-bound kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs,
-                                                    double* dA, double* gzero) {
+__global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int64_t gs, int nb, int nh, const T* dh,
+                                                    int64_t dhs, double* dA, double* gzero) {
   const int b = blockIdx.y, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= nb) return;
   if (gzero != nullptr && lane == 0) gzero[(int64_t)b * nb + i] = 0.0;
-  const float* g = G + (int64_t)i * ((nh + 3) & ~3);
+  const float* g = G + b * gs + (int64_t)i * ((nh + 3) & ~3);
   const T* d = dh + b * dhs;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int h0 = 0; h0 < nh; h0 += 256) {
@@ -391,9 +391,9 @@ __global__ void __launch_bounds__(256) k_amp_jvp_lin(const float* G, int nb, int
 // sum(base_h * out_h) at dot[b][kDotHyper + cta].  FP32 arithmetic; FP64 only
 // for the one conversion of each staged sum and of the CTA's share.
 template <typename T>
-__global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum,
-                                                    const T* base, int64_t bhs, T* out, int64_t ohs,
-                                                    double* dot) {
+__global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int64_t gs, int nb, int nh,
+                                                    const double* gsum, const T* base, int64_t bhs, T* out,
+                                                    int64_t ohs, double* dot) {
   __shared__ float4 sg[256];
   __shared__ float red[8];
   const int b = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, in
   if (bb != nullptr && lane < 4 && hq < nh) bval = float(bb[hq]);
   // first 64 vectors of the warp's rows, in flight across the staging barrier
   float4 gv[4][2];
-  const float4* g4 = reinterpret_cast<const float4*>(Gt);
+  const float4* g4 = reinterpret_cast<const float4*>(Gt + b * gs);
   auto load = [&](int j0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -417,8 +417,8 @@ __global__ void __launch_bounds__(256) k_amp_vjp_lin(const float* Gt, int nb, in
   };
   load(0);
   float* sgf = reinterpret_cast<float*>(sg);
-  const double* gs = gsum + (int64_t)b * nb;
-  for (int i = threadIdx.x; i < 4 * nb4; i += blockDim.x) sgf[i] = i < nb ? float(gs[i]) : 0.f;
+  const double* gb = gsum + (int64_t)b * nb;
+  for (int i = threadIdx.x; i < 4 * nb4; i += blockDim.x) sgf[i] = i < nb ? float(gb[i]) : 0.f;
   __syncthreads();
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j0 = 0; j0 < nb4; j0 += 64) {
@@ -537,9 +537,9 @@ int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double
 
 template <typename T>
 int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st,
-                double* gzero) {
-  prof_begin("amp_jvp", (double)nb * nh * 4 + (double)B * (nh * sizeof(T) + nb * 8), st);
-  k_amp_jvp_lin<T><<<dim3((nb + 7) / 8, B), 256, 0, st>>>(G, nb, nh, dh, dhs, dA, gzero);
+                double* gzero, int64_t gs) {
+  prof_begin("amp_jvp", (double)nb * nh * 4 * (gs ? B : 1) + (double)B * (nh * sizeof(T) + nb * 8), st);
+  k_amp_jvp_lin<T><<<dim3((nb + 7) / 8, B), 256, 0, st>>>(G, gs, nb, nh, dh, dhs, dA, gzero);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -547,9 +547,10 @@ int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double
 
 template <typename T>
 int amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum, const T* base_h, int64_t bhs, T* out_h,
-                int64_t ohs, int B, cudaStream_t st, double* dot) {
-  prof_begin("amp_vjp", (double)nb * nh * 4 + (double)B * (8.0 * nb + (base_h ? 2 : 1) * nh * sizeof(T)), st);
-  k_amp_vjp_lin<T><<<dim3((nh + 31) / 32, B), 256, 0, st>>>(Gt, nb, nh, gsum, base_h, bhs, out_h, ohs, dot);
+                int64_t ohs, int B, cudaStream_t st, double* dot, int64_t gs) {
+  prof_begin("amp_vjp", (double)nb * nh * 4 * (gs ? B : 1) + (double)B * (8.0 * nb + (base_h ? 2 : 1) * nh * sizeof(T)),
+             st);
+  k_amp_vjp_lin<T><<<dim3((nh + 31) / 32, B), 256, 0, st>>>(Gt, gs, nb, nh, gsum, base_h, bhs, out_h, ohs, dot);
   prof_end(st);
   NRE_CHECK_LAUNCH();
   return NRE_OK;
@@ -564,9 +565,9 @@ int amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum, const T* ba
   template int amp_jacobian<T>(const AmpPrior&, const double*, int, T*, double*, float*, float*,       \
                                cudaStream_t);                                                          \
   template int amp_jvp_lin<T>(const float*, int, int, const T*, int64_t, double*, int, cudaStream_t,    \
-                              double*);                                                               \
+                              double*, int64_t);                                                      \
   template int amp_vjp_lin<T>(const float*, int, int, const double*, const T*, int64_t, T*, int64_t, int, \
-                              cudaStream_t, double*);
+                              cudaStream_t, double*, int64_t);
 NRE_INST(float)
 NRE_INST(double)
 #undef NRE_INST

@@ -374,12 +374,15 @@ int amp_vjp(const AmpPrior& pr, const double* state, int64_t ss, const double* p
 template <typename T>
 int amp_jacobian(const AmpPrior& pr, const double* state, int nh, T* eye, double* Jt, float* G, float* Gt,
                  cudaStream_t st);
+// gs: float stride of the matrix between batch entries (0: one matrix for the
+// batch; the KL metric's samples each have their own expansion point).
 template <typename T>
 int amp_jvp_lin(const float* G, int nb, int nh, const T* dh, int64_t dhs, double* dA, int B, cudaStream_t st,
-                double* gzero = nullptr);  // gzero: [B][nb] set to 0 (the next sweep's in-place bin sums)
+                double* gzero = nullptr,  // gzero: [B][nb] set to 0 (the next sweep's in-place bin sums)
+                int64_t gs = 0);
 template <typename T>
 int amp_vjp_lin(const float* Gt, int nb, int nh, const double* gsum, const T* base_h, int64_t bhs, T* out_h,
-                int64_t ohs, int B, cudaStream_t st, double* dot = nullptr);
+                int64_t ohs, int B, cudaStream_t st, double* dot = nullptr, int64_t gs = 0);
 
 // Sweep chains (sweeps.cu).  Runs one Hartley transform (mid == nullptr) or the
 // metric's transform pair with t = w * y between them (mid != nullptr) over a

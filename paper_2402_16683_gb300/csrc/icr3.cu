@@ -322,11 +322,12 @@ __global__ void __launch_bounds__(ICR3_T, 3) k_icr3_refine4(int nc, const T* __r
 }
 
 // Adjoint phase 1: for the children gradient gf of coarse voxel (i, j, k):
-// gxi = L^T gf into the excitations' gradient (plus base), U[v][n] = (R^T gf)_n.
+// gxi = L^T gf into the excitations' gradient (plus base), U[n][v] = (R^T gf)_n
+// (27 planes of stride ps, so that both phases read and write along k).
 template <typename T>
 __global__ void __launch_bounds__(128) k_icr3_refine_t1(int nc, const T* __restrict__ mats, const T* gf, int64_t gfs,
                                                        T* gxi, int64_t gxs, const T* base, int64_t bs, T* U,
-                                                       int64_t us) {
+                                                       int64_t us, int64_t ps) {
   __shared__ T M[MAT3];
   const int i = blockIdx.x / nc, j = blockIdx.x - i * nc, b = blockIdx.y;
   for (int e = threadIdx.x; e < MAT3; e += blockDim.x) M[e] = mats[(int64_t)blockIdx.x * MAT3 + e];
@@ -349,21 +350,94 @@ __global__ void __launch_bounds__(128) k_icr3_refine_t1(int nc, const T* __restr
       const int64_t o = ((int64_t)(2 * i + a) * nf + (2 * j + bb)) * nf + 2 * k + cc;
       gxi[b * gxs + o] = (base ? base[b * bs + o] : T(0)) + acc;
     }
-    T* u = U + b * us + (((int64_t)i * nc + j) * nc + k) * 27;
+    // U in planes: entry n of voxel v at n * ps + v (coalesced along k)
+    T* u = U + b * us + ((int64_t)i * nc + j) * nc + k;
 #pragma unroll
     for (int n = 0; n < 27; ++n) {
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < 8; ++m) acc += M[m * 27 + n] * ge[m];
-      u[n] = acc;
+      u[n * ps] = acc;
     }
   }
 }
 
-// Adjoint phase 2: gc(i, j, k) = sum of U[v'][idx] over the coarse voxels v'
+// Phase 1 with four consecutive coarse voxels per thread (FP32, coarse sides
+// 64..512 with nc / 4 dividing the CTA): the layout and the CTA shape of
+// k_icr3_refine4; same arithmetic and order per output as k_icr3_refine_t1.
+template <typename T>
+__global__ void __launch_bounds__(ICR3_T, 4) k_icr3_refine_t1_4(int nc, const T* __restrict__ mats, const T* gf,
+                                                                int64_t gfs, T* gxi, int64_t gxs, const T* base,
+                                                                int64_t bs, T* U, int64_t us, int64_t ps) {
+  extern __shared__ __align__(16) unsigned char sm3_raw[];
+  T* Ms = reinterpret_cast<T*>(sm3_raw);
+  const int tp = nc / 4, pp = ICR3_T / tp;
+  const int b = blockIdx.y;
+  const int64_t pair0 = (int64_t)blockIdx.x * pp;
+  for (int e = threadIdx.x; e < pp * MAT3; e += blockDim.x) Ms[e] = mats[pair0 * MAT3 + e];
+  __syncthreads();
+  const int pl = threadIdx.x / tp, t = threadIdx.x - pl * tp;
+  const int64_t pair = pair0 + pl;
+  const int i = (int)(pair / nc), j = (int)(pair - (int64_t)i * nc);
+  const T* M = Ms + pl * MAT3;
+  const int nf = 2 * nc, k0 = 4 * t;
+  const T* g = gf + b * gfs;
+  // children gradient of the four voxels: ge[ab][2 kk + cc]
+  T ge[4][8];
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    const int64_t o = ((int64_t)(2 * i + (ab >> 1)) * nf + (2 * j + (ab & 1))) * nf + 2 * k0;
+    ld4v(g + o, ge[ab]);
+    ld4v(g + o + 4, ge[ab] + 4);
+  }
+  // gxi = L^T g (+ base), child q = 2 ab + cc
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    const int64_t o = ((int64_t)(2 * i + (ab >> 1)) * nf + (2 * j + (ab & 1))) * nf + 2 * k0;
+    T outv[8];
+    if (base) {
+      ld4v(base + b * bs + o, outv);
+      ld4v(base + b * bs + o + 4, outv + 4);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) outv[e] = T(0);
+    }
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int q = 2 * ab + cc;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int m = q; m < 8; ++m) {
+        const T w = M[216 + m * 8 + q];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) acc[kk] += w * ge[m >> 1][2 * kk + (m & 1)];
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) outv[2 * kk + cc] = outv[2 * kk + cc] + acc[kk];
+    }
+    T* go = gxi + b * gxs + o;
+    st4v(go, outv);
+    st4v(go + 4, outv + 4);
+  }
+  // U[n][v] = (R^T g)_n for v = (i, j, k0 .. k0 + 3)
+  T* u = U + b * us + ((int64_t)i * nc + j) * nc + k0;
+#pragma unroll
+  for (int n = 0; n < 27; ++n) {
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const T w = M[m * 27 + n];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc[kk] += w * ge[m >> 1][2 * kk + (m & 1)];
+    }
+    st4v(u + n * ps, acc);
+  }
+}
+
+// Adjoint phase 2: gc(i, j, k) = sum of U[idx][v'] over the coarse voxels v'
 // whose neighbourhood holds (i, j, k) at position idx (fixed loop order).
 template <typename T>
-__global__ void k_icr3_refine_t2(int nc, const T* U, int64_t us, T* gc, int64_t gcs) {
+__global__ void k_icr3_refine_t2(int nc, const T* U, int64_t us, int64_t ps, T* gc, int64_t gcs) {
   const int b = blockIdx.y;
   const int64_t n3 = (int64_t)nc * nc * nc;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n3; v += (int64_t)gridDim.x * blockDim.x) {
@@ -380,7 +454,7 @@ __global__ void k_icr3_refine_t2(int nc, const T* U, int64_t us, T* gc, int64_t 
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
           const int kp = (k - d + nc) % nc;  // k = kp + d: position d + 1 in the neighbourhood of kp
-          acc += U[b * us + (((int64_t)ip * nc + jp) * nc + kp) * 27 + 9 * a + 3 * bb + (d + 1)];
+          acc += U[b * us + (int64_t)(9 * a + 3 * bb + (d + 1)) * ps + ((int64_t)ip * nc + jp) * nc + kp];
         }
       }
     }
@@ -509,12 +583,27 @@ int icr3_vjp_t(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base, i
     T* gc = bufs[l & 1];
     prof_begin("icr3_refine_t", (double)B * n3 * sizeof(T) * (8.0 * 3 + 27 * 2 + 1) + (double)nc * nc * MAT3 * sizeof(T),
                st);
-    k_icr3_refine_t1<T><<<dim3(nc * nc, B), 128, 0, st>>>(nc, mats + p->mat_off[l], gf, gfs, g + p->offsets[l + 1],
-                                                           p->stride, base ? base + p->offsets[l + 1] : nullptr,
-                                                           p->stride, U, big * 27);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      auto al = [](const void* q) { return reinterpret_cast<uintptr_t>(q) % 16 == 0; };
+      const T* bl = base ? base + p->offsets[l + 1] : nullptr;
+      T* gl = g + p->offsets[l + 1];
+      if (nc >= 64 && nc % 4 == 0 && nc / 4 <= ICR3_T && ICR3_T % (nc / 4) == 0 && al(gf) && al(gl) &&
+          (!bl || al(bl)) && al(U) && gfs % 4 == 0 && p->stride % 4 == 0 && big % 4 == 0) {
+        const int pp = ICR3_T / (nc / 4);
+        k_icr3_refine_t1_4<T><<<dim3((unsigned)((int64_t)nc * nc / pp), B), ICR3_T, pp * MAT3 * sizeof(T), st>>>(
+            nc, mats + p->mat_off[l], gf, gfs, gl, p->stride, bl, p->stride, U, big * 27, big);
+        done = true;
+      }
+    }
+    if (!done)
+      k_icr3_refine_t1<T><<<dim3(nc * nc, B), 128, 0, st>>>(nc, mats + p->mat_off[l], gf, gfs,
+                                                             g + p->offsets[l + 1], p->stride,
+                                                             base ? base + p->offsets[l + 1] : nullptr, p->stride, U,
+                                                             big * 27, big);
     int blocks = (int)((n3 + 255) / 256);
     if (blocks > 1024) blocks = 1024;
-    k_icr3_refine_t2<T><<<dim3(blocks, B), 256, 0, st>>>(nc, U, big * 27, gc, big);
+    k_icr3_refine_t2<T><<<dim3(blocks, B), 256, 0, st>>>(nc, U, big * 27, big, gc, big);
     prof_end(st);
     NRE_CHECK_LAUNCH();
     gf = gc;

@@ -35,6 +35,12 @@ struct nre_kl {
   nre::DevBuf pts, g, outs;         // [S][stride]
   nre::DevBuf cf, w, r, tmp0, tmp1; // [S][N]
   nre::DevBuf states, dA, part, bpix;
+  // FP32 power / Matern model: per-sample amplitude Jacobians at the points
+  // (G [S][nb][nhp], Gt [S][nh][nbp]), their scratch, and the complete bin
+  // sums with their arrival counters
+  bool lin = false;
+  int64_t gstr = 0, gtstr = 0;
+  nre::DevBuf G, Gt, eye, Jt, gsum, gcnt;
   nre::DevBuf red;                  // partials and per-sample sums
   double energy = 0.0;
   bool have_pos = false;
@@ -45,6 +51,27 @@ struct nre_kl {
 namespace {
 
 constexpr int KL_THREADS = 256;
+
+// Four consecutive values as 16-byte vectors (two for double).
+template <typename T>
+__device__ __forceinline__ void ld4v(const T* p, T* o) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), c = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4v(T* p, const T* o) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+  }
+}
 
 int kl_blocks(int64_t n) {
   int64_t nb = (n + KL_THREADS * 4 - 1) / (KL_THREADS * 4);
@@ -66,27 +93,29 @@ template <typename T>
 __global__ void __launch_bounds__(KL_THREADS) k_kl_lik(const T* cf, const T* data, const T* mask, int64_t N,
                                                       int kind, int response, double sig_or_scale, T* r, T* w,
                                                       double* part) {
+  // pointwise terms in the plan's precision (FP64 transcendentals are slow on
+  // this part), their sum in FP64; ln(lambda) = ln(scale) + cf
   const int64_t off = (int64_t)blockIdx.y * N;
+  const T lsc = T(log(sig_or_scale)), sc = T(sig_or_scale), inv = T(1.0 / (sig_or_scale * sig_or_scale));
   double acc = 0.0;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
-    const double c = double(cf[off + x]), d = double(data[x]);
-    double nll, dn, fw;
+    const T c = cf[off + x], d = data[x];
+    T nll, dn, fw;
     if (kind == NRE_LIK_POISSON) {
-      const double lam = sig_or_scale * exp(c);
-      nll = lam - d * log(lam);
+      const T lam = sc * exp(c);
+      nll = lam - d * (lsc + c);
       dn = lam - d;
       fw = lam;
     } else {
-      const double m = mask ? double(mask[x]) : 1.0;
-      const double inv = 1.0 / (sig_or_scale * sig_or_scale);
-      const double s = response == NRE_RESP_EXP ? exp(c) : c;
-      const double ds = response == NRE_RESP_EXP ? s : 1.0;
-      const double res = d - s;
-      nll = 0.5 * m * res * res * inv;
+      const T m = mask ? mask[x] : T(1);
+      const T s = response == NRE_RESP_EXP ? exp(c) : c;
+      const T ds = response == NRE_RESP_EXP ? s : T(1);
+      const T res = d - s;
+      nll = T(0.5) * m * res * res * inv;
       dn = -m * res * ds * inv;
       fw = m * ds * ds * inv;
     }
-    acc += nll;
+    acc += double(nll);
     if (r) r[off + x] = T(dn);
     if (w) w[off + x] = T(fw);
   }
@@ -118,18 +147,30 @@ __global__ void k_kl_rows(const double* part, int nblk, int rows, double* out) {
   out[k] = s;
 }
 
-// out[i] = (1/S) sum_s (a[s][i] + (b ? b[s][i] : 0)) for i < n, in sample order;
+// out[i] = (1/S) sum_s (a[s][i] + (b ? b[s][i] : 0)) for i < n, in sample order
+// (the sum times the rounded 1/S);
 // zero padding up to the stride.
+// Four consecutive entries per thread and round (the stride is a multiple of
+// 64 entries, the arrays 16-byte aligned), so every load is a 16-byte vector.
 template <typename T>
 __global__ void k_kl_mean(const T* a, const T* b, T* out, int64_t n, int64_t stride, int S) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < stride; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i >= n) {
-      out[i] = T(0);
-      continue;
+  for (int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); i0 < stride;
+       i0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    // in the plan's precision, samples in order (FP64 conversions and
+    // divisions are slow on this part)
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    for (int k = 0; k < S; ++k) {
+      T av[4], bv[4] = {T(0), T(0), T(0), T(0)};
+      ld4v(a + (int64_t)k * stride + i0, av);
+      if (b) ld4v(b + (int64_t)k * stride + i0, bv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) s[e] += av[e] + bv[e];
     }
-    double s = 0.0;
-    for (int k = 0; k < S; ++k) s += double(a[(int64_t)k * stride + i]) + (b ? double(b[(int64_t)k * stride + i]) : 0.0);
-    out[i] = T(s / S);
+    const T invS = T(1) / T(S);
+    T o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = i0 + e < n ? s[e] * invS : T(0);
+    st4v(out + i0, o);
   }
 }
 
@@ -218,6 +259,14 @@ int kl_set_position_t(nre_kl* k, const T* xbar, cudaStream_t st) {
   NRE_CHECK_LAUNCH();
   // amplitude states of the points for the metric
   if (binned_model(p)) NRE_TRY(amp_forward<T>(amp_prior_of(p), pts + k->N, SZ, k->states.as<double>(), S, st));
+  if (k->lin) {
+    // FP32: each point's amplitude Jacobian, formed from FP64 JVPs
+    const int SS = amp_state_size(p->n_bins);
+    for (int s = 0; s < S; ++s)
+      NRE_TRY(amp_jacobian<T>(amp_prior_of(p), k->states.as<double>() + (int64_t)s * SS, p->n_hyper, k->eye.as<T>(),
+                              k->Jt.as<double>(), k->G.as<float>() + s * k->gstr, k->Gt.as<float>() + s * k->gtstr,
+                              st));
+  }
   k->have_pos = true;
   return NRE_OK;
 }
@@ -236,7 +285,12 @@ int kl_metric_apply_t(nre_kl* k, const T* v, T* out, cudaStream_t st) {
   const bool model = binned_model(p);
   const int SS = model ? amp_state_size(nb) : 0;
   const AmpPrior pr = model ? amp_prior_of(p) : AmpPrior{};
-  if (model) NRE_TRY(amp_jvp<T>(pr, k->states.as<double>(), SS, v + N, 0, k->dA.as<double>(), S, st));
+  const int nh = model ? p->n_hyper : 0;
+  if (k->lin)  // also zeroes the in-place bin sums of the epilogue
+    NRE_TRY(amp_jvp_lin<T>(k->G.as<float>(), nb, nh, v + N, 0, k->dA.as<double>(), S, st, k->gsum.as<double>(),
+                           k->gstr));
+  else if (model)
+    NRE_TRY(amp_jvp<T>(pr, k->states.as<double>(), SS, v + N, 0, k->dA.as<double>(), S, st));
   T* pts = k->pts.as<T>();
   Pro<T> pro{};
   pro.mode = PRO_AMP;
@@ -258,12 +312,19 @@ int kl_metric_apply_t(nre_kl* k, const T* v, T* out, cudaStream_t st) {
     epi.bins = 1;
     epi.xi_p = pts;
     epi.ps = SZ;
+    if (k->lin) {
+      epi.gsum = k->gsum.as<double>();
+      epi.gcnt = k->gcnt.as<unsigned>();
+    }
   }
   Mid<T> mid{k->w.as<T>(), N};
   int np = 0;
   NRE_TRY(run_hartley<T>(p, S, pro, epi, &mid, k->tmp0.as<T>(), k->tmp1.as<T>(),
                          model ? k->part.as<double>() : nullptr, &np, st));
-  if (model)
+  if (k->lin)
+    NRE_TRY(amp_vjp_lin<T>(k->Gt.as<float>(), nb, nh, k->gsum.as<double>(), v + N, 0, k->outs.as<T>() + N, SZ, S, st,
+                           nullptr, k->gtstr));
+  else if (model)
     NRE_TRY(amp_vjp<T>(pr, k->states.as<double>(), SS, k->part.as<double>(), np, v + N, 0, k->outs.as<T>() + N,
                        SZ, S, st));
   prof_begin("kl_mean", (double)S * SZ * sizeof(T), st);
@@ -394,6 +455,22 @@ int kl_create(nre_kl** out, nre_cf_plan* plan, const nre_lik* lik, const double*
     if ((s = k->states.alloc((size_t)S * amp_state_size(nb) * sizeof(double))) != NRE_OK) return fail(s);
     if ((s = k->dA.alloc((size_t)S * nb * sizeof(double))) != NRE_OK) return fail(s);
     if ((s = k->part.alloc((size_t)S * max_parts(plan) * nb * sizeof(double))) != NRE_OK) return fail(s);
+    const int nh = plan->n_hyper;
+    if (plan->dtype == NRE_F32 && nh <= 1024) {
+      k->lin = true;
+      k->gstr = (int64_t)nb * ((nh + 3) & ~3);
+      k->gtstr = (int64_t)nh * ((nb + 3) & ~3);
+      if ((s = k->G.alloc((size_t)S * k->gstr * sizeof(float))) != NRE_OK ||
+          (s = k->Gt.alloc((size_t)S * k->gtstr * sizeof(float))) != NRE_OK ||
+          (s = k->eye.alloc((size_t)nh * nh * sizeof(float))) != NRE_OK ||
+          (s = k->Jt.alloc((size_t)nh * nb * sizeof(double))) != NRE_OK ||
+          (s = k->gsum.alloc((size_t)S * nb * sizeof(double))) != NRE_OK ||
+          (s = k->gcnt.alloc((size_t)S * sizeof(unsigned))) != NRE_OK)
+        return fail(s);
+      // the sweeps leave the arrival counters zero
+      e = cudaMemsetAsync(k->gcnt.p, 0, (size_t)S * sizeof(unsigned), st);
+      if (e != cudaSuccess) return fail(set_error(NRE_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
+    }
     // per-pixel bins (-1 at k = 0) for the register sweeps' tables
     std::vector<int64_t> shp(plan->ndim);
     std::vector<double> sp(plan->ndim);
