@@ -111,6 +111,37 @@ int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_
   const bool buf = a.pro.mode == PRO_BUF && a.epi.mode == EPI_BUF;
   if (mid && !buf) return set_error(NRE_EINVAL, "internal: the metric's column sweep reads and writes plain buffers");
   prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, mid, B, N), st);
+  if constexpr (sizeof(T) == 4 && L >= 128 && L <= 1024) {
+    // FP32 plain buffers with whole tiles: bulk tensor copies
+    auto al = [](const void* q) { return reinterpret_cast<uintptr_t>(q) % 16 == 0; };
+    unsigned* status = timeout_word();
+    if (buf && a.W == ColShape<L, 4>::W && a.inner % 4 == 0 && a.pro.xs % 4 == 0 && a.epi.ys % 4 == 0 &&
+        al(a.pro.x) && al(a.epi.y) && status != nullptr) {
+      typedef ColTma<L> TM;
+      const int64_t outer = a.n_units / a.nblk;
+      const uint64_t dims[4] = {(uint64_t)a.inner, (uint64_t)L, (uint64_t)outer, (uint64_t)B};
+      const uint64_t sin[3] = {(uint64_t)a.inner * 4, (uint64_t)L * a.inner * 4, (uint64_t)a.pro.xs * 4};
+      const uint64_t sout[3] = {(uint64_t)a.inner * 4, (uint64_t)L * a.inner * 4, (uint64_t)a.epi.ys * 4};
+      const uint32_t box[4] = {(uint32_t)TM::W, (uint32_t)TM::RB, 1u, 1u};
+      CUtensorMap tin, tout;
+      int s = tmap_tiled(&tin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.pro.x, dims, sin, box, TM::SWB);
+      if (s == NRE_OK) s = tmap_tiled(&tout, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.epi.y, dims, sout, box, TM::SWB);
+      if (s == NRE_OK) {
+        const size_t tsm = TM::bytes();
+        if (mid) {
+          NRE_TRY(set_smem(k_col_tma<L, true>, tsm));
+          k_col_tma<L, true><<<grid, NT, tsm, st>>>(a, tin, tout, status);
+        } else {
+          NRE_TRY(set_smem(k_col_tma<L, false>, tsm));
+          k_col_tma<L, false><<<grid, NT, tsm, st>>>(a, tin, tout, status);
+        }
+        prof_end(st);
+        NRE_CHECK_LAUNCH();
+        return NRE_OK;
+      }
+      clear_error();  // fall back to the staged kernel
+    }
+  }
   if (mid) {
     NRE_TRY(set_smem(k_col_reg<T, L, true, SK_BUF, SK_BUF>, smem));
     k_col_reg<T, L, true, SK_BUF, SK_BUF><<<grid, NT, smem, st>>>(a);

@@ -30,6 +30,7 @@
 
 #include "cf_internal.cuh"
 #include "regfft.cuh"
+#include "tma.cuh"
 
 namespace nre {
 
@@ -658,6 +659,128 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
     __syncthreads();
     fold_bins(a.epi, a.partials, b, gridDim.x, blockIdx.x, hist, NW, a.nb, a.nb);
   }
+}
+
+// Column sweep of FP32 plain buffers (the metric's axis-0 sweep, MID, and the
+// 3-D middle-axis sweeps) with its tiles moved by bulk tensor copies.  One
+// elected thread loads the next unit's tile (W columns x L rows, boxes of at
+// most 256 rows) into the other half of the double buffer, completing on that
+// half's mbarrier, and stores each finished output tile from shared memory
+// with a bulk tensor store; the threads only transform.  Tiles are dense rows
+// of W floats (32 / 64 / 128 bytes) in the copies' swizzled layout, which
+// keeps a half-warp's 8-byte column-pair accesses at two wavefronts.  Waits
+// are bounded: a wait that runs out (decided for the whole CTA) is counted in
+// *status and the CTA stops after waiting, again bounded, for its copies.
+template <int L>
+struct ColTma {
+  typedef ColShape<L, 4> CS;
+  static constexpr int W = CS::W, XS = L * W, RB = L < 256 ? L : 256, NBOX = L / RB;
+  static constexpr unsigned SWM = W == 8 ? 0x10u : (W == 16 ? 0x30u : 0x70u);
+  static constexpr int SWB = W * 4;  // swizzle span in bytes
+  // a buffer holds a tile and, once the tile is in registers, the exchange
+  // lines; buffers start at multiples of 1024 bytes (the swizzle's alignment)
+  static constexpr int LNSZ = CS::NL * rline(L) * 2;  // floats
+  static constexpr int BUFB = ((XS > LNSZ ? XS : LNSZ) * 4 + 1023) / 1024 * 1024;
+  static size_t bytes() { return 1024 + (size_t)2 * BUFB + (size_t)L * 8; }
+  // float index of element (l, col) of a tile
+  __device__ __forceinline__ static int at(int l, int col) {
+    const unsigned A = (unsigned)(l * W + col) * 4u;
+    return (int)((A ^ ((A >> 3) & SWM)) >> 2);
+  }
+};
+
+template <int L, bool MID>
+__global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4>::NT, 4))
+    k_col_tma(ColArgs<float> a, const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+              unsigned* status) {
+  typedef float T;
+  typedef float2 C;
+  typedef ColTma<L> TM;
+  constexpr int T8 = L / 8, W = TM::W, XS = TM::XS, RB = TM::RB, NBOX = TM::NBOX, LS = rline(L);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const unsigned s0 = smem_u32(smem_raw);
+  unsigned char* bufs = smem_raw + (((s0 + 1023u) & ~1023u) - s0);
+  auto tile = [&](int buf) { return reinterpret_cast<T*>(bufs + buf * TM::BUFB); };
+  C* tw = reinterpret_cast<C*>(bufs + 2 * TM::BUFB);
+  const int b = blockIdx.y;
+  load_twiddles<L>(tw, a.tw, a.log2Lmax - a.log2L);
+  const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
+  const LineSync<T8> sync{1 + u};
+  const int nblk_sh = __ffsll(a.nblk) - 1;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t unit, int buf) {  // elected thread
+    const int z = (int)(unit >> nblk_sh), x = (int)((unit & (a.nblk - 1)) * W);
+    mbar_arrive_tx(&bar[buf], (unsigned)(XS * 4));
+#pragma unroll
+    for (int k = 0; k < NBOX; ++k) tma_load_4d(tile(buf) + k * RB * W, &tin, x, k * RB, z, b, &bar[buf]);
+  };
+  int64_t unit = blockIdx.x;
+  if (threadIdx.x == 0 && unit < a.n_units) issue(unit, 0);
+  int it = 0;
+  bool timed_out = false;
+  for (; unit < a.n_units; unit += gridDim.x, ++it) {
+    const int cur = it & 1;
+    if (threadIdx.x == 0 && unit + gridDim.x < a.n_units) {
+      bulk_wait_read0();  // the store of two units ago has read the other half
+      issue(unit + gridDim.x, cur ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[cur], (unsigned)(it >> 1) & 1u);
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    const int64_t o = unit >> nblk_sh;
+    const int64_t base = o * L * a.inner + (unit & (a.nblk - 1)) * W;
+    T* X = tile(cur);
+    C v[1][8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[0][s] = *reinterpret_cast<const C*>(X + TM::at(t + T8 * s, 2 * u));
+    __syncthreads();  // the whole tile is in registers: its buffer becomes the exchange lines
+    C* sm[1] = {reinterpret_cast<C*>(X) + u * LS};
+    C* const* smc = sm;
+    reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+    C zm[1][8];
+    if constexpr (MID) {
+      reg_mirror<C, L, 1>(v, zm, smc, t, sync);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        T ha[2], hb[2];
+        hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+        const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
+        v[0][s] = a.mid.apply2(b, flat, ha[0], hb[0]);
+      }
+      reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+    }
+    reg_mirror<C, L, 1>(v, zm, smc, t, sync);
+    __syncthreads();  // every line has read the input tile: it takes the output
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      T ha[2], hb[2];
+      hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
+      *reinterpret_cast<C*>(X + TM::at(t + T8 * s, 2 * u)) = cmake<C>(ha[0], hb[0]);
+    }
+    fence_proxy_async();  // the generic-proxy writes before the async-proxy store
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int z = (int)o, x = (int)((unit & (a.nblk - 1)) * W);
+#pragma unroll
+      for (int k = 0; k < NBOX; ++k) tma_store_4d(&tout, x, k * RB, z, b, X + k * RB * W);
+      bulk_commit();
+    }
+  }
+  if (timed_out && threadIdx.x == 0) {
+    note_timeout(status);
+    // the loads in flight: the current unit's and the one issued for the next
+    mbar_wait(&bar[it & 1], (unsigned)(it >> 1) & 1u);
+    if (unit + gridDim.x < a.n_units) mbar_wait(&bar[(it + 1) & 1], (unsigned)((it + 1) >> 1) & 1u);
+  }
+  if (threadIdx.x == 0) bulk_wait0();
 }
 
 }  // namespace nre

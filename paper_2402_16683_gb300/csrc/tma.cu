@@ -47,7 +47,7 @@ unsigned* timeout_word() {
 }
 
 int tmap_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const uint64_t* dims,
-               const uint64_t* strides_b, const uint32_t* box) {
+               const uint64_t* strides_b, const uint32_t* box, int swizzle_bytes) {
   const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return set_error(NRE_ECUDA, "cuTensorMapEncodeTiled is not available");
   if (rank < 1 || rank > 5) return set_error(NRE_EINVAL, "internal: tensor map rank %d", rank);
@@ -67,8 +67,15 @@ int tmap_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* bas
     if (strides_b[d] % 16 != 0) return set_error(NRE_EINVAL, "internal: tensor map stride not a 16-byte multiple");
     gs[d] = strides_b[d];
   }
+  CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+  if (swizzle_bytes == 32) sw = CU_TENSOR_MAP_SWIZZLE_32B;
+  else if (swizzle_bytes == 64) sw = CU_TENSOR_MAP_SWIZZLE_64B;
+  else if (swizzle_bytes == 128) sw = CU_TENSOR_MAP_SWIZZLE_128B;
+  else if (swizzle_bytes != 0) return set_error(NRE_EINVAL, "internal: swizzle of %d bytes", swizzle_bytes);
+  if (swizzle_bytes && box[0] * es != (uint32_t)swizzle_bytes)
+    return set_error(NRE_EINVAL, "internal: swizzled box rows must span the swizzle");
   const CUresult r = fn(m, dt, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, el,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(NRE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return NRE_OK;

@@ -20,7 +20,11 @@ namespace nre {
 // the copied extent (box[0] * element size a multiple of 16, each <= 256).
 // Out-of-range elements of a box read as zero.
 int tmap_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base, const uint64_t* dims,
-               const uint64_t* strides_b, const uint32_t* box);
+               const uint64_t* strides_b, const uint32_t* box, int swizzle_bytes = 0);
+// swizzle_bytes 32 / 64 / 128: the box's rows of that many bytes are stored in
+// shared memory with their 16-byte chunks permuted: byte address A holds what
+// the unswizzled layout has at A ^ ((A >> 3) & mask), mask 0x10 / 0x30 / 0x70
+// (the box must start at a multiple of 1024 bytes).
 
 // Per-device count of waits that ran out (allocated on first use; call it once
 // outside stream capture, e.g. when a plan is created).
@@ -77,6 +81,28 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int
       "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bulk tensor store of a box from shared memory (this thread's bulk group).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* m, int x, int y, int z, int w, const void* src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(m)),
+               "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Wait until this thread's committed bulk stores have read their shared
+// memory (.read) or completed.
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // Record a wait that ran out (status[0] counts them).
 __device__ __forceinline__ void note_timeout(unsigned* status) {
