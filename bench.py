@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--icr-only", action="store_true", help="run only the ICR leg")
     ap.add_argument("--next-only", action="store_true", help="run only the KL / geoVI / 3-D ICR leg")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the KL / geoVI / 3-D ICR leg")
+    ap.add_argument("--icr3-only", action="store_true", help="run only the 3-D ICR part of that leg")
     return ap.parse_args()
 
 
@@ -331,13 +332,13 @@ def run_ours(args, rank, world):
         if rank == 0:
             print(json.dumps({"icr": run_icr(args, lib0, fl, torch.cuda.current_stream(), peaks()[0])}), flush=True)
         return
-    if args.next_only:
+    if args.next_only or args.icr3_only:
         lib0 = _lib.load()
         dev0 = torch.device("cuda", torch.cuda.current_device())
         fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev0)
         if rank == 0:
-            print(json.dumps({"next_rows": run_next_rows(args, lib0, fl, torch.cuda.current_stream(), peaks()[0])}),
-                  flush=True)
+            print(json.dumps({"next_rows": run_next_rows(args, lib0, fl, torch.cuda.current_stream(), peaks()[0],
+                                                          icr3_only=args.icr3_only)}), flush=True)
         return
     lib = _lib.load()
     lib.nre_launch_count.restype = C.c_ulonglong
@@ -722,7 +723,7 @@ def _leg_stats(ms, kern, n, peak, units, unit_name):
                             "GBps": x[2] / (x[1] / 1e3) / 1e9 if x[1] else None} for k, x in kern.items()}}
 
 
-def run_next_rows(args, lib, flush, stream, peak):
+def run_next_rows(args, lib, flush, stream, peak, icr3_only=False):
     """The rows after sampling, FP32 on the 2-D 512^2 Poisson workload (rate
     10 exp(cf), power-spectrum model) and the 3-D chart:
 
@@ -741,6 +742,9 @@ def run_next_rows(args, lib, flush, stream, peak):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = max(5, args.steps)
     out = {}
+    if icr3_only:
+        out["icr3_4_to_256"] = run_icr3(args, lib, flush, stream, peak, n, dev)
+        return out
     shape = (512, 512)
     plan = nre.CorrelatedField(shape, amplitude="power", prior=dict(synth.AMP_PRIOR), dtype=torch.float32)
     lik = nre.Likelihood("poisson", scale=10.0)
@@ -804,7 +808,17 @@ def run_next_rows(args, lib, flush, stream, peak):
     del M, draws, d0, d, rhs
     torch.cuda.empty_cache()
 
-    # ---- 3-D ICR
+    out["icr3_4_to_256"] = run_icr3(args, lib, flush, stream, peak, n, dev)
+    return out
+
+
+def run_icr3(args, lib, flush, stream, peak, n, dev):
+    """ICR on the spherical log-radial chart refined 4^3 -> 256^3 (6 levels),
+    Matern-3/2 (length scale 0.1), FP32, batch 4: forward and VJP."""
+    import torch
+
+    import paper_2402_16683_gb300 as nre
+
     B = 4
     icr = nre.ICR(n0=4, n_levels=6, rho=0.1, var=1.0, dtype=torch.float32, ndim=3)
     xi = icr.pad(torch.tensor(synth.rng(synth.SEED_POS).standard_normal((B, icr.latent_size)), dtype=torch.float32,
@@ -815,10 +829,9 @@ def run_next_rows(args, lib, flush, stream, peak):
         fn()
         ms, kern = _timed_traced(lib, fn, n, flush, stream)
         res[name] = _leg_stats(ms, kern, n, peak, B, "fields_per_s")
-    out["icr3_4_to_256"] = res
     del icr, xi, ct
     torch.cuda.empty_cache()
-    return out
+    return res
 
 
 # ----------------------------------------------------------------- serving leg

@@ -55,7 +55,14 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
   const int64_t N = p->N;
   if (!m->side && p->ndim >= 2 && m->max_batch >= 2) {
     // the second stream of split products (created here, outside any capture)
-    NRE_TRY_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    // with the priority of the stream the metric is created on (serving gives
+    // small requests higher priority)
+    int prio = 0;
+    if (cudaStreamGetPriority(st, &prio) != cudaSuccess) {
+      cudaGetLastError();
+      prio = 0;
+    }
+    NRE_TRY_CUDA(cudaStreamCreateWithPriority(&m->side, cudaStreamNonBlocking, prio));
     NRE_TRY_CUDA(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
     NRE_TRY_CUDA(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
   }

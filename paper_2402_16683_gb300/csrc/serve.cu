@@ -276,7 +276,13 @@ int make_slot(const Job* j, int dtype, SlotObj** out) {
   if (s != NRE_OK) return bad(s);
   s = lik_create(&so->lik, r.lik_kind, r.response, nullptr, so->g.N, r.sigma_or_scale);
   if (s != NRE_OK) return bad(s);
-  if (cudaStreamCreateWithFlags(&so->st, cudaStreamNonBlocking) != cudaSuccess ||
+  // Smaller grids get higher stream priority: their CTAs are scheduled ahead
+  // of the queued CTAs of large requests, so a short solve is not stuck behind
+  // the long sweeps of the requests running beside it.
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int prio = so->g.N <= 8192 ? greatest : so->g.N <= 65536 ? (least + greatest) / 2 : least;
+  if (cudaStreamCreateWithPriority(&so->st, cudaStreamNonBlocking, prio) != cudaSuccess ||
       cudaEventCreateWithFlags(&so->ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc((void**)&so->h_sc, B * CG_SC_N * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
