@@ -81,18 +81,30 @@ def parse():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
 # one capture, caches flushed before each launch) of the kernels that can be
 # the dominant one, keyed by (kernel tag, batch), averaged over the launch
-# variants the tag covers, with the digest of the kernel sources they were
-# captured from (kernel_src_digest); an entry whose digest differs from the
-# current sources is stale and reported as null.
-DRAM_TRAFFIC = {}
+# variants the tag covers, with the digest of the sources that define those
+# kernels at capture time (kernel_src_digest); an entry whose digest differs
+# from the current sources is stale and reported as null.
+# row_sweep_f32_2d at batch 32: the traced (unsplit) launches take the whole
+# batch; the capture ran the half-batch launches of the split product (16
+# samples): 18.17 MB (prologue sweep) and 34.94 MB (epilogue sweep) read,
+# 0.02 MB written, scaled by two (traffic grows with the samples; the shared
+# bin and expansion-point tables, 1.5 MB, are then counted twice) and
+# averaged over the two variants (profiles/traffic_f32_2d_512x512_b32.md).
+DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.13e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                                    "half-batch launches x 2, mean of the two row sweeps",
+                                           "b39b17ed68897d18")}
+
+# The sources of the sweep kernels (the digest of DRAM_TRAFFIC).
+SWEEP_SOURCES = ["common.cuh", "cf_internal.cuh", "fft.cuh", "regfft.cuh", "sweeps_reg.cuh", "sweeps_launch.cuh",
+                 "sweeps_inst.cu", "tma.cuh", "../../include/nre.h"]
 
 
-def kernel_src_digest():
-    """sha256 (first 16 hex digits) of the library's CUDA / C++ sources."""
+def kernel_src_digest(files=SWEEP_SOURCES):
+    """sha256 (first 16 hex digits) of the given library sources."""
     import hashlib
     d = os.path.join(ROOT, "paper_2402_16683_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]

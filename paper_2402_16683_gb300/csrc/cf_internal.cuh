@@ -145,9 +145,11 @@ struct Epi {
   int bins;           // accumulate the per-bin sums
   AmpView<T> av;
   // EPI_AMP with bins: when set, the complete per-bin sums go into gsum[b][nb]
-  // (so that the reader sums nothing): every CTA writes its partial, and the
-  // last CTA of sample b to finish (counter gcnt[b], zero on entry and left
-  // zero) adds the partials in a fixed order
+  // (so that the reader sums nothing): every CTA writes its partial; the last
+  // CTA of each group of kBinGroup consecutive CTAs to finish adds its group's
+  // partials, and the last group to finish adds the group sums, each in a
+  // fixed order (counters gcnt[b * kGcntStride + ...], zero on entry and left
+  // zero)
   double* gsum;
   unsigned* gcnt;
   // EPI_AMP with base, last sweep of a metric product: per-CTA partials of
@@ -232,44 +234,128 @@ struct Mid {
 };
 
 // A CTA's per-bin sums, from nreg warp-private histograms (region r at
-// hist + r * rstride, folded in region order in FP64), as partial `part` of
-// nparts for sample b at partials[(b * nparts + part) * nb]; with e.gsum the
-// last CTA of sample b then adds the nparts partials in a fixed order into
-// e.gsum[b * nb] (see Epi::gsum).  Called by all threads of the CTA after its
-// last histogram update, with a __syncthreads() before.
+// hist + r * rstride, folded in region order in the histograms' type H), as
+// partial `part` of nparts for sample b at partials[(b * nparts + part) * nb]
+// (FP64); with e.gsum the partials are kept as pairs (sum, error) of H in the
+// same slots (the buffer read as H) and added in two fixed-order levels (the
+// CTAs of a group of kBinGroup, then the groups) into e.gsum[b * nb] (see
+// Epi::gsum).  All additions are compensated, so FP32 histograms fold to about
+// FP64 accuracy.  Called by all threads of the CTA after
+// its last histogram update, with a __syncthreads() before.
+// CTAs per group of the in-place bin sums, and the arrival counters per sample
+// (one for the groups, one per group; up to 128 CTAs per sample).
+constexpr int kBinGroup = 8;
+constexpr int kGcntStride = 1 + 128 / kBinGroup;
+
+// Compensated (Neumaier) addition of x into s with the rounding errors
+// collected in c: s + c carries the sum to about twice the working precision.
+template <typename H>
+__device__ __forceinline__ void comp_add(H& s, H& c, H x) {
+  const H t = s + x;
+  c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+// The two reduction levels of fold_bins for the in-place sums, out of line so
+// that the sweeps' main loops keep their registers.  hp: the partial pairs.
+template <typename H>
+__device__ __noinline__ void bins_complete(H* hp, double* gsum, unsigned* gcnt, int b, int nparts, int part,
+                                           int nb) {
+  // the last CTA of the group adds the group's partials into the slot of
+  // its first CTA; the last group then adds the group sums
+  const int g = part / kBinGroup, ng = (nparts + kBinGroup - 1) / kBinGroup;
+  const int g0 = g * kBinGroup, gn = min(kBinGroup, nparts - g0);
+  unsigned* cnt = gcnt + (int64_t)b * kGcntStride;
+  const H* src = hp + 2 * ((int64_t)b * nparts * nb);
+  H* gdst = hp + 2 * (((int64_t)b * nparts + g0) * nb);
+  // Arrival: the CTA's partial (written by all its threads, ordered before
+  // thread 0 by the barrier) is released by thread 0's fence before its
+  // counter add; only thread 0 fences, so the other warps do not wait for
+  // their own outstanding output stores.
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&cnt[1 + g], 1u) == (unsigned)(gn - 1);
+    if (s_last) __threadfence();  // acquire the other CTAs' partials
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the group's partials from L2 (ld.global.cg: not through this SM's L1), all
+  // in flight at once, added in CTA order
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    H ps[kBinGroup], pc[kBinGroup];
+#pragma unroll
+    for (int u = 0; u < kBinGroup; ++u) {
+      const int64_t o = 2 * ((int64_t)(g0 + u) * nb + i);
+      ps[u] = u < gn ? __ldcg(&src[o]) : H(0);
+      pc[u] = u < gn ? __ldcg(&src[o + 1]) : H(0);
+    }
+    H s = H(0), c = H(0);
+#pragma unroll
+    for (int u = 0; u < kBinGroup; ++u) {
+      comp_add(s, c, ps[u]);
+      c += pc[u];
+    }
+    gdst[2 * i] = s;
+    gdst[2 * i + 1] = c;
+  }
+  __syncthreads();  // the group sum, then the group's arrival (released as above)
+  if (threadIdx.x == 0) {
+    cnt[1 + g] = 0u;
+    __threadfence();
+    s_last = atomicAdd(&cnt[0], 1u) == (unsigned)(ng - 1);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    H s = H(0), c = H(0);
+    for (int q0 = 0; q0 < ng; q0 += kBinGroup) {
+      H ps[kBinGroup], pc[kBinGroup];
+#pragma unroll
+      for (int u = 0; u < kBinGroup; ++u) {
+        const int64_t o = 2 * ((int64_t)(q0 + u) * kBinGroup * nb + i);
+        ps[u] = q0 + u < ng ? __ldcg(&src[o]) : H(0);
+        pc[u] = q0 + u < ng ? __ldcg(&src[o + 1]) : H(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kBinGroup; ++u) {
+        comp_add(s, c, ps[u]);
+        c += pc[u];
+      }
+    }
+    gsum[(int64_t)b * nb + i] = double(s) + double(c);
+  }
+  if (threadIdx.x == 0) cnt[0] = 0u;
+}
+
 template <typename T, typename H>
 __device__ __forceinline__ void fold_bins(const Epi<T>& e, double* partials, int b, int nparts, int part,
                                           const H* hist, int nreg, int rstride, int nb) {
-  double* dst = partials + ((int64_t)b * nparts + part) * nb;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    double s = 0.0;
-    for (int r = 0; r < nreg; ++r) s += double(hist[r * rstride + i]);
-    dst[i] = s;
-  }
-  if (e.gsum == nullptr) return;
-  __shared__ bool s_last;
-  __threadfence();  // this CTA's partial before its arrival
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&e.gcnt[b], 1u) == (unsigned)(nparts - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // the other CTAs' partials from L2 (ld.global.cg: not through this SM's L1),
-  // eight loads in flight per thread, added in a fixed order
-  const double* src = partials + (int64_t)b * nparts * nb;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int c = 0;
-    for (; c + 8 <= nparts; c += 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] += __ldcg(&src[(int64_t)(c + u) * nb + i]);
+  // the warps' histograms in warp order, in the histograms' type with the
+  // rounding errors carried along (the FP64 units of this part run at a small
+  // fraction of the FP32 rate)
+  if (e.gsum == nullptr) {
+    double* dst = partials + ((int64_t)b * nparts + part) * nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      H s = H(0), c = H(0);
+      for (int r = 0; r < nreg; ++r) comp_add(s, c, hist[r * rstride + i]);
+      dst[i] = double(s) + double(c);
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (c + u < nparts) acc[u] += __ldcg(&src[(int64_t)(c + u) * nb + i]);
-    e.gsum[(int64_t)b * nb + i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    return;
   }
-  if (threadIdx.x == 0) e.gcnt[b] = 0u;
+  // complete sums in place: each CTA's partial as a pair (sum, error) of H in
+  // the buffer's slot, the last CTA adds them
+  H* hp = reinterpret_cast<H*>(partials);
+  H* dst = hp + 2 * (((int64_t)b * nparts + part) * nb);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    H s = H(0), c = H(0);
+    for (int r = 0; r < nreg; ++r) comp_add(s, c, hist[r * rstride + i]);
+    dst[2 * i] = s;
+    dst[2 * i + 1] = c;
+  }
+  bins_complete<H>(hp, e.gsum, e.gcnt, b, nparts, part, nb);
 }
 
 // Arguments of one row sweep (last axis, length L).

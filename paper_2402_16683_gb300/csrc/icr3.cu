@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) k_icr3_refine(int nc, const T* __restrict
 constexpr int ICR3_T = 128;
 
 template <typename T>
-__global__ void __launch_bounds__(ICR3_T, 3) k_icr3_refine4(int nc, const T* __restrict__ mats, const T* sc,
+__global__ void __launch_bounds__(ICR3_T, 4) k_icr3_refine4(int nc, const T* __restrict__ mats, const T* sc,
                                                             int64_t scs, const T* xif, int64_t xs, T* sf, int64_t sfs,
                                                             const T* __restrict__ scale) {
   extern __shared__ __align__(16) unsigned char sm3_raw[];

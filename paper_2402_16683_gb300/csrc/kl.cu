@@ -465,10 +465,10 @@ int kl_create(nre_kl** out, nre_cf_plan* plan, const nre_lik* lik, const double*
           (s = k->eye.alloc((size_t)nh * nh * sizeof(float))) != NRE_OK ||
           (s = k->Jt.alloc((size_t)nh * nb * sizeof(double))) != NRE_OK ||
           (s = k->gsum.alloc((size_t)S * nb * sizeof(double))) != NRE_OK ||
-          (s = k->gcnt.alloc((size_t)S * sizeof(unsigned))) != NRE_OK)
+          (s = k->gcnt.alloc((size_t)S * kGcntStride * sizeof(unsigned))) != NRE_OK)
         return fail(s);
       // the sweeps leave the arrival counters zero
-      e = cudaMemsetAsync(k->gcnt.p, 0, (size_t)S * sizeof(unsigned), st);
+      e = cudaMemsetAsync(k->gcnt.p, 0, (size_t)S * kGcntStride * sizeof(unsigned), st);
       if (e != cudaSuccess) return fail(set_error(NRE_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
     }
     // per-pixel bins (-1 at k = 0) for the register sweeps' tables

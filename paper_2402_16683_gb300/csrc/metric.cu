@@ -107,7 +107,7 @@ int cf_metric_setup(nre_metric* m, const void* xi_p_in, cudaStream_t st) {
       NRE_TRY(ensure(m->amp_eye, (size_t)nh * nh * sizeof(T)));
       NRE_TRY(ensure(m->amp_Jt, (size_t)nh * nb * sizeof(double)));
       NRE_TRY(ensure(m->gsum, (size_t)m->max_batch * nb * sizeof(double)));
-      const size_t cnt = (size_t)m->max_batch * sizeof(unsigned);
+      const size_t cnt = (size_t)m->max_batch * kGcntStride * sizeof(unsigned);
       if (m->gcnt.bytes < cnt) {
         NRE_TRY(ensure(m->gcnt, cnt));
         NRE_TRY_CUDA(cudaMemsetAsync(m->gcnt.p, 0, cnt, st));  // the sweeps leave them zero
@@ -203,7 +203,7 @@ int cf_metric_apply(nre_metric* m, const T* v, T* out, int B, cudaStream_t st, d
       if (eh.ps) eh.xi_p += (int64_t)b0 * eh.ps;
       if (eh.gsum) {
         eh.gsum += (int64_t)b0 * nb;
-        eh.gcnt += b0;
+        eh.gcnt += (int64_t)b0 * kGcntStride;
       }
       if (eh.dot) eh.dot += (int64_t)b0 * kDotStride;
       // each half's CTA partials in its own slab of the partials buffer

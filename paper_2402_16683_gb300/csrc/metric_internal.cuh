@@ -39,7 +39,7 @@ struct nre_metric {
   bool amp_lin = false;
   nre::DevBuf amp_G, amp_Gt, amp_eye, amp_Jt;
   nre::DevBuf gsum;  // [max_batch][n_bins] complete bin sums of the last sweep
-  nre::DevBuf gcnt;  // [max_batch] unsigned arrival counters of those sums (zero between sweeps)
+  nre::DevBuf gcnt;  // [max_batch][kGcntStride] unsigned arrival counters of those sums (zero between sweeps)
   nre::DevBuf tmp0, tmp1, part;
   // conjugate-gradient workspace (grown by cg_solve)
   nre::DevBuf cg_r, cg_p, cg_q, cg_sc, cg_part;

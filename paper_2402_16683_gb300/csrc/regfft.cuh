@@ -77,11 +77,7 @@ __host__ __device__ constexpr int scatter_off(int NS, int r, int Q) {
   return NS == 1 ? r : (NS < 16 ? r * NS + Q * ((r * NS) >> 4) : r * NS + Q * r * (NS >> 4));
 }
 
-// TWC: the pass's twiddles W^r (r = 2 .. R-1) come from W^1 by complex
-// products (W^2 = W W, W^3 = W^2 W, W^4 = W^2 W^2, ...) instead of shared
-// memory: for kernels bound by shared-memory issue (the column sweeps) one
-// load and six products per butterfly instead of seven loads.
-template <typename C, int L, int NS, int LPT, bool TWC = false>
+template <typename C, int L, int NS, int LPT>
 struct RegPass {
   static constexpr int REM = L / NS;
   static constexpr int R = REM >= 8 ? 8 : REM;
@@ -101,22 +97,11 @@ struct RegPass {
       if constexpr (NS > 1) {
         const int j = t + T8 * m;
         const C* tk = tw + tw_off(L, NS) + (j & (NS - 1)) - NS;  // entry (r - 1) NS + k at tk + r NS
-        if constexpr (TWC) {
-          C w[8];
-          w[1] = tk[NS];
 #pragma unroll
-          for (int r = 2; r < R; ++r) w[r] = (r & 1) ? cmul(w[r - 1], w[1]) : cmul(w[r / 2], w[r / 2]);
+        for (int r = 1; r < R; ++r) {
+          const C w = tk[r * NS];
 #pragma unroll
-          for (int r = 1; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < LPT; ++q) v[q][m * R + r] = cmul(v[q][m * R + r], w[r]);
-        } else {
-#pragma unroll
-          for (int r = 1; r < R; ++r) {
-            const C w = tk[r * NS];
-#pragma unroll
-            for (int q = 0; q < LPT; ++q) v[q][m * R + r] = cmul(v[q][m * R + r], w);
-          }
+          for (int q = 0; q < LPT; ++q) v[q][m * R + r] = cmul(v[q][m * R + r], w);
         }
       }
 #pragma unroll
@@ -134,7 +119,7 @@ struct RegPass {
         for (int s = 0; s < 8; ++s) v[q][s] = o[s];
       }
     } else {
-      typedef RegPass<C, L, NS * R, LPT, TWC> Next;
+      typedef RegPass<C, L, NS * R, LPT> Next;
       constexpr int R2 = Next::R, M2 = 8 / R2;
       constexpr int Q = exch_q<C, L, NS>();
 #pragma unroll
@@ -180,9 +165,9 @@ struct RegPass {
 };
 
 // Forward FFT of LPT lines; v[q][s] = line_q[t + s L/8] in and X_q[t + s L/8] out.
-template <typename C, int L, int LPT, bool TWC = false, class Sync>
+template <typename C, int L, int LPT, class Sync>
 __device__ __forceinline__ void reg_fft(C (&v)[LPT][8], C* const* sm, const C* tw, int t, Sync sync) {
-  RegPass<C, L, 1, LPT, TWC>::run(v, sm, tw, t, sync);
+  RegPass<C, L, 1, LPT>::run(v, sm, tw, t, sync);
 }
 
 // zm[q][s] = X_q[-(t + s L/8) mod L] through the shared line buffers.
@@ -246,8 +231,10 @@ __device__ __forceinline__ void warp_run_add(int key, V val, H* whist) {
   if (__all_sync(full, key < 0)) return;
   // first lane of this lane's run (lane 0 always heads a run)
   const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
+  // steps of the segmented scan up to the longest run of the warp (the offsets
+  // beyond it add nothing, so the sums are those of the full 5-step scan)
+  const int maxrun = (int)__reduce_max_sync(full, (unsigned)(lane - seg + 1));
+  for (int o = 1; o < maxrun; o <<= 1) {
     const V ov = __shfl_up_sync(full, val, o);
     if (lane - o >= seg) val += ov;
   }

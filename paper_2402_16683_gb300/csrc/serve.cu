@@ -106,8 +106,9 @@ uint64_t footprint(const nre_serve_req* r, const Geom& g, int dtype) {
   if (nb > 0)
     b += a256((size_t)amp_state_size((int)nb) * 8) + a256(B * nb * 8) + a256(B * 128 * nb * 8) + a256(N * E) +
          a256(N * 2);
-  if (nb > 0 && E == 4)  // amplitude Jacobian of the FP32 metric
-    b += 2 * a256(nb * nh * 4) + a256(nh * nh * E) + a256(nh * nb * 8) + a256(B * nb * 8);
+  if (nb > 0 && E == 4)  // amplitude Jacobian of the FP32 metric, in-place bin sums and their counters
+    b += 2 * a256(nb * nh * 4) + a256(nh * nh * E) + a256(nh * nb * 8) + a256(B * nb * 8) +
+         a256(B * kGcntStride * 4);
   // CG workspace (r, p, q and z) and scalars
   b += (pc ? 4 : 3) * a256(B * S * E) + a256(B * CG_SC_N * 8) + a256(3 * B * 64 * 8 + B * 4);
   if (pc && nb > 0)

@@ -9,6 +9,7 @@
 namespace nre {
 
 constexpr int kMaxGridX = 128;      // CTAs per sample of a sweep (bounds the partials buffer)
+static_assert(kMaxGridX <= kBinGroup * (kGcntStride - 1), "arrival counters of the in-place bin sums");
 
 // CTAs of a persistent register sweep resident at once: per SM the fewer of
 // the kernel's compiled minimum (row_min_ctas / col_min_ctas) and what its

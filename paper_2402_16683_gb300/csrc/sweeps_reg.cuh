@@ -510,10 +510,6 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   }
 }
 
-// The column sweeps compute their twiddle powers (RegPass TWC): they are bound
-// by shared-memory issue, the row sweeps by instruction issue overall.
-constexpr bool kColTwc = true;
-
 // Shared-memory plan of the column kernel (element counts in T).
 template <typename T, int L>
 struct ColSmem {
@@ -608,7 +604,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
     if (SM::ALIAS) __syncthreads();  // the whole tile is in registers: its space becomes the exchange lines
     C* sm[1] = {(SM::ALIAS ? reinterpret_cast<C*>(X) : lines_own) + u * LS};
     C* const* smc = sm;
-    reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+    reg_fft<C, L, 1>(v, smc, tw, t, sync);
     C zm[1][8];
     if constexpr (MID) {
       reg_mirror<C, L, 1>(v, zm, smc, t, sync);
@@ -619,7 +615,7 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
         const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
         v[0][s] = lval ? a.mid.apply2(b, flat, ha[0], hb[0]) : cmake<C>(T(0), T(0));
       }
-      reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+      reg_fft<C, L, 1>(v, smc, tw, t, sync);
     }
     reg_mirror<C, L, 1>(v, zm, smc, t, sync);
     __syncthreads();  // every line has read the input tile: reuse it for the output
@@ -744,7 +740,7 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
     __syncthreads();  // the whole tile is in registers: its buffer becomes the exchange lines
     C* sm[1] = {reinterpret_cast<C*>(X) + u * LS};
     C* const* smc = sm;
-    reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+    reg_fft<C, L, 1>(v, smc, tw, t, sync);
     C zm[1][8];
     if constexpr (MID) {
       reg_mirror<C, L, 1>(v, zm, smc, t, sync);
@@ -755,7 +751,7 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
         const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
         v[0][s] = a.mid.apply2(b, flat, ha[0], hb[0]);
       }
-      reg_fft<C, L, 1, kColTwc>(v, smc, tw, t, sync);
+      reg_fft<C, L, 1>(v, smc, tw, t, sync);
     }
     reg_mirror<C, L, 1>(v, zm, smc, t, sync);
     __syncthreads();  // every line has read the input tile: it takes the output
