@@ -399,6 +399,11 @@ int nre_device_bytes(int64_t *bytes);
  * synchronises the device.  A nonzero count means that some output of an
  * earlier call is incomplete. */
 int nre_wait_timeouts(unsigned *count, int reset);
+/* Test hook of those bounded waits (the paper has no counterpart): one CTA
+ * waits, with an iteration limit of `limit` (1 .. 2^20), on a shared-memory
+ * barrier that no copy completes; the wait runs out, the CTA counts one
+ * timeout (read with nre_wait_timeouts) and returns.  Enqueued on `stream`. */
+int nre_wait_selftest(unsigned limit, nre_stream_t stream);
 
 /* ================================================================ serving
  * A request loop for sampling solves: each request is one expansion point of

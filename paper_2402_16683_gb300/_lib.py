@@ -123,6 +123,7 @@ SIGNATURES = {
                          C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), _P],
     "nre_device_bytes": [_I64P],
     "nre_wait_timeouts": [C.POINTER(C.c_uint), C.c_int],
+    "nre_wait_selftest": [C.c_uint, _P],
     "serve_create": [C.POINTER(_P), C.POINTER(ServeCfg)],
     "serve_submit": [_P, C.POINTER(ServeReq), C.POINTER(C.c_uint64)],
     "serve_poll": [_P, C.c_uint64, C.POINTER(ServeResult), C.c_int],

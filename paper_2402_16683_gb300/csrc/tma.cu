@@ -96,3 +96,31 @@ extern "C" int nre_wait_timeouts(unsigned* count, int reset) {
   }
   return NRE_OK;
 }
+
+namespace {
+
+// A wait that nothing completes: the barrier expects 16 bytes that no copy
+// delivers, so every thread's bounded wait runs out and thread 0 counts it.
+__global__ void k_wait_selftest(unsigned limit, unsigned* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    nre::mbar_init(&bar, 1);
+    nre::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) nre::mbar_arrive_tx(&bar, 16u);
+  const bool ok = nre::mbar_wait(&bar, 0u, limit);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) nre::note_timeout(status);
+}
+
+}  // namespace
+
+extern "C" int nre_wait_selftest(unsigned limit, nre_stream_t stream) {
+  nre::clear_error();
+  if (limit < 1 || limit > (1u << 20)) return nre::set_error(NRE_EINVAL, "limit must be in [1, 2^20]");
+  unsigned* w = nre::timeout_word();
+  if (!w) return nre::set_error(NRE_ECUDA, "no timeout word on this device");
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(limit, w);
+  NRE_CHECK_LAUNCH();
+  return NRE_OK;
+}

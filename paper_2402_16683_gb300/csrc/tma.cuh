@@ -51,10 +51,10 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase of the given parity; false after kWaitLimit tries.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Bounded wait for the phase of the given parity; false after `limit` tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = kWaitLimit) {
   const unsigned a = smem_u32(bar);
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
