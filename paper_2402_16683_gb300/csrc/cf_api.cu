@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "cf_internal.cuh"
+#include "tma.cuh"
 
 namespace nre {
 
@@ -317,6 +318,9 @@ int cf_create(nre_cf_plan** plan, int ndim, const int64_t* shape, const double* 
   if (dtype != NRE_F32 && dtype != NRE_F64) return set_error(NRE_EINVAL, "dtype must be NRE_F32 or NRE_F64");
   if (amp->kind < NRE_AMP_ARRAY || amp->kind > NRE_AMP_MATERN_MODEL)
     return set_error(NRE_EINVAL, "unknown amplitude kind %d", amp->kind);
+  // the device's count of bounded waits that ran out, allocated here (outside
+  // any stream capture) before the first sweep takes it
+  (void)timeout_word();
   nre_cf_plan* p = new nre_cf_plan();
   p->ndim = ndim;
   p->dtype = dtype;

@@ -374,6 +374,7 @@ struct RowArgs {
   Mid<T> mid;
   int nb;              // bins of the histogram (epi.bins)
   double* partials;    // [B][gridDim.x][nb] (PM >= 2) or [B][1][nb] (PM == 1)
+  unsigned* status;    // count of bounded waits that ran out (may be null)
 };
 
 // Arguments of one sweep along a non-contiguous axis.

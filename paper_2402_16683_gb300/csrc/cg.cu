@@ -17,8 +17,10 @@ using namespace nre;
 namespace {
 
 constexpr int CG_THREADS = 256;
+// SC_XALPHA: the step alpha of the last update kernel whose x += alpha p the
+// next p-update kernel applies (0: none).
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
-       SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
+       SC_ITERS = CG_SC_ITERS, SC_XALPHA = 6, SC_N = CG_SC_N };
 
 // Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
@@ -171,6 +173,7 @@ __global__ void k_cg_start(double* sc, const double* part, int nblk, double rtol
   c[SC_BB] = s;
   c[SC_ALPHA] = 0.0;
   c[SC_BETA] = 0.0;
+  c[SC_XALPHA] = 0.0;
   c[SC_ITERS] = 0.0;
   c[SC_ACTIVE] = (s > 0.0 && rtol < 1.0) ? 1.0 : 0.0;
 }
@@ -198,18 +201,21 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_dot(const T* a, const T* q, i
   });
 }
 
-// x += alpha p, r -= alpha q; then (last block) beta = r'.r' / r.r, the
-// iteration count and the convergence test.  A system that has converged
-// keeps beta = 0 and its x, r frozen.
+// r -= alpha q; then (last block) beta = r'.r' / r.r, the iteration count and
+// the convergence test.  A system that has converged keeps beta = 0 and its
+// x, r frozen.  The step x += alpha p is left to the p-update kernel, which
+// reads p anyway (alpha in SC_XALPHA): one vector read less per iteration,
+// and x is complete after every p-update, the same values in the same
+// arithmetic as when the update kernel applied it.
 // With pq (the fused p.q partials of the metric product, kDotStride per
 // system) every block forms alpha = r.r / p.q itself; the last block of the
 // system, which alone rewrites r.r, starts only after every block has read it.
 // With hy.G (CGHyper): the vector loop covers the field entries; p.q gains the
 // hyper part p_h . p_h + dA . g (one warp per block, read from pn = the
 // current p_h), and each block takes a share of the hyper rows: q_h = p_h +
-// Gt[h] . g, x_h += alpha p_h, r_h -= alpha q_h, p_h copied from pn into p.
+// Gt[h] . g, r_h -= alpha q_h, p_h copied from pn into p.
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, const T* q, int64_t n,
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* r, T* p, const T* q, int64_t n,
                                                          int64_t S, double* sc, double* rr_part,
                                                          unsigned* counter, double rtol, const double* pq,
                                                          CGHyper hy, const T* pn) {
@@ -247,32 +253,25 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, c
   } else {
     alpha = T(c[SC_ALPHA]);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c[SC_XALPHA] = active ? double(alpha) : 0.0;
   RunSum<T> acc;
-  constexpr int U = 2;
+  constexpr int U = 4;
   for_vec_u<T, U>(
       fused ? hy.N : n, blockIdx.x, gridDim.x,
       [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
-        V16<T> ri[U], xi[U], pi[U], qi[U];
+        V16<T> ri[U], qi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (ok[u]) {
             ri[u] = ldv(r + off + idx[u]);
-            if (active) {
-              xi[u] = ldv(x + off + idx[u]);
-              pi[u] = ldv(p + off + idx[u]);
-              qi[u] = ldv(q + off + idx[u]);
-            }
+            if (active) qi[u] = ldv(q + off + idx[u]);
           }
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (ok[u]) {
             if (active) {
 #pragma unroll
-              for (int k = 0; k < V16<T>::W; ++k) {
-                xi[u].e[k] += alpha * pi[u].e[k];
-                ri[u].e[k] -= alpha * qi[u].e[k];
-              }
-              stv(x + off + idx[u], xi[u]);
+              for (int k = 0; k < V16<T>::W; ++k) ri[u].e[k] -= alpha * qi[u].e[k];
               stv(r + off + idx[u], ri[u]);
             }
             T run = T(0);  // one vector
@@ -284,7 +283,6 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, c
       [&](int64_t i) {
         T ri = r[off + i];
         if (active) {
-          x[off + i] += alpha * p[off + i];
           ri -= alpha * q[off + i];
           r[off + i] = ri;
         }
@@ -334,7 +332,6 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, c
         T rh = r[e];
         p[e] = ph;
         if (active) {
-          x[e] += alpha * ph;
           rh -= alpha * (ph + tq);
           r[e] = rh;
         }
@@ -358,13 +355,16 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_update(T* x, T* r, T* p, c
   });
 }
 
-// p = r + beta p with beta from the update kernel (0 for a frozen system).
-// With hy.G: the vector loop covers the field entries; every block forms the
-// next p_h = r_h + beta p_h in shared memory (p_h itself is not written here:
-// every block reads it), block 0 stores it to pn, and each block takes a
-// share of the bins: dA = G p_h, gsum = 0 (the next product's bin sums).
+// x += alpha p (the update kernel's step, SC_XALPHA; also for a system that
+// converged in that update), then p = r + beta p with beta from the update
+// kernel (0 for a frozen system).  With hy.G: the vector loop covers the
+// field entries; block 0 applies the step to x_h (p_h of the step is in p,
+// where the update kernel copied it); every block forms the next p_h = r_h +
+// beta p_h in shared memory (p_h itself is not written here: every block
+// reads it), block 0 stores it to pn, and each block takes a share of the
+// bins: dA = G p_h, gsum = 0 (the next product's bin sums).
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* p, const T* r, int64_t n, int64_t S,
+__global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* x, T* p, const T* r, int64_t n, int64_t S,
                                                           const double* sc, CGHyper hy, T* pn) {
   const int b = blockIdx.y;
   const double* c = sc + b * SC_N;
@@ -372,30 +372,50 @@ __global__ void __launch_bounds__(CG_THREADS, 4) k_cg_pupdate(T* p, const T* r, 
   const int rows = fused ? (hy.nb + gridDim.x - 1) / gridDim.x : 0;
   const int i0 = blockIdx.x * rows, i1 = fused ? min(hy.nb, i0 + rows) : 0;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) hy.gsum[(int64_t)b * hy.nb + i] = 0.0;
-  if (c[SC_ACTIVE] == 0.0) return;
+  const bool active = c[SC_ACTIVE] != 0.0;
+  const T xa = T(c[SC_XALPHA]);
+  const bool step = xa != T(0);
+  if (!active && !step) return;
   const T beta = T(c[SC_BETA]);
   const int64_t off = (int64_t)b * S;
-  constexpr int U = 4;
+  constexpr int U = 2;
   for_vec_u<T, U>(
       fused ? hy.N : n, blockIdx.x, gridDim.x,
       [&](const int64_t (&idx)[U], const bool (&ok)[U]) {
-        V16<T> ri[U], pi[U];
+        V16<T> ri[U], pi[U], xi[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (ok[u]) {
-            ri[u] = ldv(r + off + idx[u]);
             pi[u] = ldv(p + off + idx[u]);
+            if (active) ri[u] = ldv(r + off + idx[u]);
+            if (step) xi[u] = ldv(x + off + idx[u]);
           }
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (ok[u]) {
+            if (step) {
 #pragma unroll
-            for (int k = 0; k < V16<T>::W; ++k) pi[u].e[k] = ri[u].e[k] + beta * pi[u].e[k];
-            stv(p + off + idx[u], pi[u]);
+              for (int k = 0; k < V16<T>::W; ++k) xi[u].e[k] += xa * pi[u].e[k];
+              stv(x + off + idx[u], xi[u]);
+            }
+            if (active) {
+#pragma unroll
+              for (int k = 0; k < V16<T>::W; ++k) pi[u].e[k] = ri[u].e[k] + beta * pi[u].e[k];
+              stv(p + off + idx[u], pi[u]);
+            }
           }
       },
-      [&](int64_t i) { p[off + i] = r[off + i] + beta * p[off + i]; });
-  if (!fused || i0 >= i1) return;
+      [&](int64_t i) {
+        const T pv = p[off + i];
+        if (step) x[off + i] += xa * pv;
+        if (active) p[off + i] = r[off + i] + beta * pv;
+      });
+  if (fused && step && blockIdx.x == 0)
+    for (int h = threadIdx.x; h < hy.nh; h += blockDim.x) {
+      const int64_t e = off + hy.N + h;
+      x[e] += xa * p[e];
+    }
+  if (!fused || !active || i0 >= i1) return;
   __shared__ float4 sp4[256];
   float* sp = reinterpret_cast<float*>(sp4);
   const int nh4 = (hy.nh + 3) >> 2;
@@ -537,12 +557,12 @@ int cg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t s
       k_cg_dot<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.q, n, S, w.part_a, w.counter, w.sc);
       prof_end(st);
     }
-    prof_begin("cg_update", 6 * vb, st);
-    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(x, w.r, w.p, w.q, n, S, w.sc, w.part_b, w.counter, rtol, pq,
+    prof_begin("cg_update", 3 * vb, st);
+    k_cg_update<T><<<grid, CG_THREADS, 0, st>>>(w.r, w.p, w.q, n, S, w.sc, w.part_b, w.counter, rtol, pq,
                                                  pq ? w.hy : CGHyper{}, w.pn);
     prof_end(st);
-    prof_begin("cg_pupdate", 3 * vb, st);
-    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(w.p, w.r, n, S, w.sc, pq ? w.hy : CGHyper{}, w.pn);
+    prof_begin("cg_pupdate", 5 * vb, st);
+    k_cg_pupdate<T><<<grid, CG_THREADS, 0, st>>>(x, w.p, w.r, n, S, w.sc, pq ? w.hy : CGHyper{}, w.pn);
     prof_end(st);
     NRE_CHECK_LAUNCH();
   }

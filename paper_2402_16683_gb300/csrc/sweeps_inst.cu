@@ -47,6 +47,15 @@ int epi_kind(const Epi<T>& e) {
 template <typename T, int L>
 int row_reg_L(RowArgs<T> a, bool mid, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
   const char* name = row_name(a.pm, mid, sizeof(T));
+  // the staged rows (input, and the base rows where they are staged) are
+  // copied in 16-byte pieces or whole by bulk copies: rows and samples must
+  // start on 16-byte boundaries
+  auto al = [](const void* q, int64_t stride) {
+    return reinterpret_cast<uintptr_t>(q) % 16 == 0 && (stride * (int64_t)sizeof(T)) % 16 == 0;
+  };
+  if (!al(a.pro.x, a.pro.xs) || (a.epi.mode == EPI_AMP && a.epi.base != nullptr && !al(a.epi.base, a.epi.bs)))
+    return set_error(NRE_EINVAL, "internal: row sweep rows not 16-byte aligned");
+  a.status = timeout_word();
   prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, mid, a.B, N), st);
   int s;
   if (a.pm == 1) {

@@ -19,7 +19,10 @@
 //
 // Both kernels are persistent over their units: while a CTA transforms one
 // group, the inputs of its next group stream into the other half of a double
-// buffer with 16-byte cp.async copies, so HBM reads overlap the arithmetic.
+// buffer, so HBM reads overlap the arithmetic: whole rows by bulk copies
+// (one per lane of warp 0, completing on an mbarrier) in the row sweep,
+// tiles by bulk tensor copies in the FP32 column sweep (k_col_tma), 16-byte
+// cp.async copies elsewhere.
 // The threads of one line synchronise with warp or named barriers only.
 // Per-bin amplitude tables (A and the tangent's dA) of the CTA's sample sit in
 // shared memory; only the int16 bin index is read per pixel.  Log-|k| bin sums
@@ -147,12 +150,46 @@ __host__ __device__ constexpr int row_min_ctas(int nt, int pm, int ek, int es, i
 }
 // The row sweep with the metric's epilogue loads its base values straight from
 // global memory (with its other per-pixel loads) where that lets four CTAs
-// share an SM; elsewhere the base rows are staged with cp.async, which hides
-// their latency better at the lower occupancy.
+// share an SM; elsewhere the base rows are staged like the input rows, which
+// hides their latency better at the lower occupancy.
 __host__ __device__ constexpr bool row_direct_base(int nt, int pm, int ek, int es, int l) {
   return ek == SK_TAB && row_min_ctas(nt, pm, ek, es, l) >= 4;
 }
 __host__ __device__ constexpr int col_min_ctas(int nt, int es) { return nt <= 256 ? (es == 8 ? 3 : 4) : (nt <= 512 ? 2 : 1); }
+
+// Bulk copies of one stage of a row sweep, issued by warp 0: lane i copies
+// staged row i (unit group ug + i / SLOTS, slot i % SLOTS) of L elements from
+// global memory (rows of `src`, samples `ss` elements apart) to shared address
+// dst + i L elements, completing on the mbarrier at `bar`, whose transaction
+// count lane 0 sets to the bytes of the valid rows.  Out of line: it runs once
+// or twice per unit group and keeps its registers out of the sweep's.
+template <typename T, int L, int PM, int SLOTS, int NROWS>
+__device__ __noinline__ void row_issue_bulk(const T* src, int64_t ss, const int* grows, int n_units, int B, int ug,
+                                            int bsample, unsigned dst, unsigned bar) {
+  const int lane = threadIdx.x & 31;
+  bool ok = false;
+  const T* g = nullptr;
+  if (lane < NROWS) {
+    const int uu = lane / SLOTS, sl = lane - uu * SLOTS;
+    const int un = ug + uu;
+    const int samp = PM == 1 ? 2 * un + sl : bsample;
+    ok = un < n_units && (PM != 1 || samp < B);
+    if (ok) {
+      const int row = PM == 1 ? 0 : __ldg(&grows[un * SLOTS + sl]);
+      g = src + samp * ss + (int64_t)row * L;
+    }
+  }
+  const unsigned nv = __popc(__ballot_sync(0xffffffffu, ok));
+  constexpr unsigned RB = (unsigned)(L * sizeof(T));
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(nv * RB) : "memory");
+  __syncwarp();
+  if (ok)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     dst + (unsigned)lane * RB),
+                 "l"(g), "r"(RB), "r"(bar)
+                 : "memory");
+}
 
 template <typename T, int L, int PM, bool MID, int PK, int EK>
 __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT, PM, EK, sizeof(T), L))
@@ -196,7 +233,29 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   // input rows of unit group ug into stage half buf (prefetched one iteration
   // ahead); with base, the base rows of ug into bstage (issued at the start of
   // their own iteration: they are read only by the epilogue, so one buffer
-  // suffices and the staging plan stays small)
+  // suffices and the staging plan stays small).  BULK (at most 32 rows per
+  // stage): each lane of warp 0 copies one row with a bulk copy that
+  // completes on the half's (bstage's) mbarrier, whose waits are bounded;
+  // otherwise every thread copies 16-byte chunks with cp.async.
+  constexpr int NROWS = NU * SLOTS;
+  constexpr bool BULK = NROWS <= 32;
+  __shared__ __align__(8) uint64_t sbar[3];
+  if constexpr (BULK) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) mbar_init(&sbar[i], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+  }
+  auto issue_bulk = [&](int ug, int buf, bool base_only) {  // warp 0
+    if (base_only)
+      row_issue_bulk<T, L, PM, SLOTS, NROWS>(a.epi.base, a.epi.bs, a.grows, a.n_units, a.B, ug, bsample,
+                                             smem_u32(bstage), smem_u32(&sbar[2]));
+    else
+      row_issue_bulk<T, L, PM, SLOTS, NROWS>(a.pro.x, a.pro.xs, a.grows, a.n_units, a.B, ug, bsample,
+                                             smem_u32(stage + buf * SM::STGA), smem_u32(&sbar[buf]));
+  };
   auto issue = [&](int ug, int buf, bool base_only) {
     T* dst = stage + buf * SM::STGA;
     T* bdst = bstage;
@@ -224,16 +283,34 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   RunSum<T> dacc;
   const int ustride = gridDim.x * NU;
   int u0 = blockIdx.x * NU;
-  if (u0 < a.n_units) issue(u0, 0, false);
-  cp_commit();
-  for (int it = 0; u0 < a.n_units; u0 += ustride, ++it) {
+  int it = 0;
+  bool timed_out = false;
+  if constexpr (BULK) {
+    if (threadIdx.x < 32 && u0 < a.n_units) issue_bulk(u0, 0, false);
+  } else {
+    if (u0 < a.n_units) issue(u0, 0, false);
+    cp_commit();
+  }
+  for (; u0 < a.n_units && !timed_out; u0 += ustride, ++it) {
     const int cur = it & 1;
-    if (bstaged) issue(u0, 0, true);  // group B: this iteration's base rows
-    cp_commit();
-    if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1, false);  // group A: next input
-    cp_commit();
-    cp_wait<2>();  // everything but B and A: this iteration's input rows
-    __syncthreads();
+    if constexpr (BULK) {
+      if (threadIdx.x < 32) {
+        if (bstaged) issue_bulk(u0, 0, true);                                 // this iteration's base rows
+        if (u0 + ustride < a.n_units) issue_bulk(u0 + ustride, cur ^ 1, false);  // next input
+      }
+      // this iteration's input rows
+      const bool ok = mbar_wait(&sbar[cur], (unsigned)(it >> 1) & 1u);
+      // a wait that ran out ends the loop after this iteration (its results
+      // are void; the count in a.status tells the host)
+      if (__syncthreads_or(!ok)) timed_out = true;
+    } else {
+      if (bstaged) issue(u0, 0, true);  // group B: this iteration's base rows
+      cp_commit();
+      if (u0 + ustride < a.n_units) issue(u0 + ustride, cur ^ 1, false);  // group A: next input
+      cp_commit();
+      cp_wait<2>();  // everything but B and A: this iteration's input rows
+      __syncthreads();
+    }
     const int unit = u0 + u;
     const bool valid = unit < a.n_units;
     int row[SLOTS], samp[SLOTS];
@@ -335,14 +412,25 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
     }
     reg_mirror<C, L, LPU>(v, zm, smc, t, sync);
     if (bstaged) {
-      cp_wait<1>();  // everything but group A: the base rows
-      __syncthreads();
+      if constexpr (BULK) {
+        const bool ok = mbar_wait(&sbar[2], (unsigned)it & 1u);
+        if (__syncthreads_or(!ok)) timed_out = true;
+      } else {
+        cp_wait<1>();  // everything but group A: the base rows
+        __syncthreads();
+      }
     }
     const T* BV = bstage + u * SLOTS * L;
     if constexpr (EK == SK_TAB && PM >= 2) {
-      // The metric's epilogue in two phases so the per-pixel loads (bins,
-      // expansion point) are all in flight before they are used:
-      // A) loads and the P combination, B) stores and bin reductions.
+      // The metric's epilogue, one column pair per phase: column x = t + T8 s
+      // (s < 4, so x < L / 2) and its mirror x' = L - x.  Both outputs come
+      // from the pair (z(x), z(x')) that the unpack reads (the mirror's with
+      // the two columns' roles swapped: the same arithmetic as the unpack at
+      // x' itself), and the bins, which depend on |k| only, are the same at x
+      // and x', so each slot's two contributions go into one warp reduction.
+      // Thread 0's pair at s = 0 is x = 0 and L / 2, each its own mirror.
+      // Per phase: A) the per-pixel loads (bins, expansion point, base), all
+      // in flight before they are used, B) values, stores, bin reductions.
       const int16_t* bp = epi.av.bpix;
       const T* xp = epi.xi_p + (int64_t)bsample * epi.ps;
       const T* bsrc = epi.base + (int64_t)bsample * epi.bs;  // the TAB epilogue always has a base
@@ -350,63 +438,95 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       const int fl = valid ? __ldg(&a.gflags[unit]) : 0;
       const bool f0 = fl & 1, f1 = fl & 2;
       const T half = T(0.5), a0 = epi.av.a0t;
+      const bool t0 = t == 0;
       T dsum = T(0);
-      constexpr int CH = 2;  // columns per load/store phase pair (register budget)
 #pragma unroll
-      for (int c0 = 0; c0 < 8; c0 += CH) {
-        int bn[CH][SLOTS];
-        T xv[CH][SLOTS], val[CH][SLOTS], bvv[CH][SLOTS];
+      for (int s = 0; s < 4; ++s) {
+        const int x = t + T8 * s;
+        const bool sp = s == 0 && t0;
+        const int x2 = sp ? L / 2 : L - x;
+        int bn[SLOTS], bn2[SLOTS];
+        T xv[2][SLOTS], bvv[2][SLOTS], val[2][SLOTS];
 #pragma unroll
-        for (int s = 0; s < CH; ++s)
-#pragma unroll
-          for (int sl = 0; sl < SLOTS; ++sl) {
-            // mirror rows of the orbit share the canonical slot's bins
-            const int f = row[sl] * L + t + T8 * (c0 + s);
-            if (PM == 2 && sl == 1 && f0) bn[s][1] = bn[s][0];
-            else bn[s][sl] = valid ? (int)__ldg(&bp[f]) : -1;
-            xv[s][sl] = valid ? __ldg(&xp[f]) : T(0);
-            if constexpr (DIRECT_BASE) bvv[s][sl] = valid ? bsrc[f] : T(0);
-          }
-#pragma unroll
-        for (int s = 0; s < CH; ++s) {
-          if constexpr (PM == 2) {
-            T R[2][2];
-            hartley_unpack<T>(v[0][c0 + s], zm[0][c0 + s], R[0], R[1]);
-#pragma unroll
-            for (int sl = 0; sl < 2; ++sl) {
-              val[s][sl] = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
-            }
+        for (int sl = 0; sl < SLOTS; ++sl) {
+          // mirror rows of a 2-D orbit share the canonical slot's bins
+          const int f = row[sl] * L + x, f2 = row[sl] * L + x2;
+          if (PM == 2 && sl == 1 && f0) {
+            bn[1] = bn[0];
+            if (s == 0) bn2[1] = bn2[0];
           } else {
-            T R[4][2];
-            hartley_unpack<T>(v[0][c0 + s], zm[0][c0 + s], R[0], R[1]);
-            hartley_unpack<T>(v[1][c0 + s], zm[1][c0 + s], R[2], R[3]);
-#pragma unroll
-            for (int sl = 0; sl < 4; ++sl) {
-              val[s][sl] = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
-                                   pick4(R, sl, f0, f1, 1));
-            }
+            bn[sl] = valid ? (int)__ldg(&bp[f]) : -1;
+            if (s == 0) bn2[sl] = (valid && sp) ? (int)__ldg(&bp[f2]) : bn[sl];
+          }
+          if (s != 0) bn2[sl] = bn[sl];
+          xv[0][sl] = valid ? __ldg(&xp[f]) : T(0);
+          xv[1][sl] = valid ? __ldg(&xp[f2]) : T(0);
+          if constexpr (DIRECT_BASE) {
+            bvv[0][sl] = valid ? bsrc[f] : T(0);
+            bvv[1][sl] = valid ? bsrc[f2] : T(0);
+          } else {
+            bvv[0][sl] = BV[sl * L + x];
+            bvv[1][sl] = BV[sl * L + x2];
           }
         }
+        if constexpr (PM == 2) {
+          T R[2][2], R2[2][2];
+          hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+          if (s == 0) {
+            hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
+          } else {
 #pragma unroll
-        for (int s = 0; s < CH; ++s) {
-          const int x = t + T8 * (c0 + s);
-          T c[SLOTS];
-          int kb[SLOTS];
-#pragma unroll
-          for (int sl = 0; sl < SLOTS; ++sl) {
-            const int b_ = bn[s][sl];
-            T bv;
-            if constexpr (DIRECT_BASE) bv = bvv[s][sl];
-            else bv = BV[sl * L + x];
-            const T o = (b_ < 0 ? a0 : sA[b_]) * val[s][sl] + bv;
-            if (valid) {
-              yo[row[sl] * L + x] = o;
-              dsum += bv * o;
-            }
-            c[sl] = xv[s][sl] * val[s][sl];
-            kb[sl] = b_;
+            for (int i = 0; i < 2; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
           }
-          add_slots<SLOTS, T>(kb, c, whist);  // the TAB epilogue always sums the bins
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl) {
+            val[0][sl] = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
+            val[1][sl] = half * (R2[sl][1] + pick2(R2, sl, f0, 1) + R2[sl][0] - pick2(R2, sl, f0, 0));
+          }
+        } else {
+          T R[4][2], R2[4][2];
+          hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+          hartley_unpack<T>(v[1][s], zm[1][s], R[2], R[3]);
+          if (s == 0) {
+            hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
+            hartley_unpack<T>(sp ? v[1][4] : v[1][0], sp ? zm[1][4] : zm[1][0], R2[2], R2[3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
+          }
+#pragma unroll
+          for (int sl = 0; sl < 4; ++sl) {
+            val[0][sl] = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
+                                 pick4(R, sl, f0, f1, 1));
+            val[1][sl] = half * (pick4(R2, sl, f0, false, 1) + pick4(R2, sl, false, f1, 1) + R2[sl][0] -
+                                 pick4(R2, sl, f0, f1, 0));
+          }
+        }
+        T c[2 * SLOTS];
+        int kb[2 * SLOTS];
+#pragma unroll
+        for (int sl = 0; sl < SLOTS; ++sl) {
+          const T o = (bn[sl] < 0 ? a0 : sA[bn[sl]]) * val[0][sl] + bvv[0][sl];
+          const T o2 = (bn2[sl] < 0 ? a0 : sA[bn2[sl]]) * val[1][sl] + bvv[1][sl];
+          if (valid) {
+            yo[row[sl] * L + x] = o;
+            yo[row[sl] * L + x2] = o2;
+            dsum += bvv[0][sl] * o;
+            dsum += bvv[1][sl] * o2;
+          }
+          c[sl] = xv[0][sl] * val[0][sl];
+          c[SLOTS + sl] = xv[1][sl] * val[1][sl];
+          kb[sl] = bn[sl];
+          kb[SLOTS + sl] = bn2[sl];
+        }
+        // the TAB epilogue always sums the bins
+        if (s == 0) {
+          add_slots<2 * SLOTS, T>(kb, c, whist);  // thread 0's second column has its own bins
+        } else {
+          T cm[SLOTS];
+#pragma unroll
+          for (int sl = 0; sl < SLOTS; ++sl) cm[sl] = c[sl] + c[SLOTS + sl];
+          add_slots<SLOTS, T>(bn, cm, whist);
         }
       }
       if (dot) dacc.add(dsum);
@@ -478,9 +598,24 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
     }
     if (dot) dacc.add(dsum);
     }  // generic epilogue
-    __syncthreads();  // this half is refilled two iterations later
+    // this half is refilled two iterations later (and bstage in the next):
+    // the generic-proxy accesses come before the bulk copies' writes
+    if constexpr (BULK) fence_proxy_async();
+    __syncthreads();
   }
-  cp_wait<0>();
+  if constexpr (BULK) {
+    if (timed_out && threadIdx.x == 0) {
+      note_timeout(a.status);
+      // the copies that may still be in flight: those of the last iteration
+      // (lt) and the input it issued for the next unit group (at u0)
+      const int lt = it - 1;
+      mbar_wait(&sbar[lt & 1], (unsigned)(lt >> 1) & 1u);
+      if (bstaged) mbar_wait(&sbar[2], (unsigned)lt & 1u);
+      if (u0 < a.n_units) mbar_wait(&sbar[it & 1], (unsigned)(it >> 1) & 1u);
+    }
+  } else {
+    cp_wait<0>();
+  }
   if (dot) {
     const double tot = dacc.block_sum();
     double* dp = epi.dot + (int64_t)blockIdx.y * kDotStride;
