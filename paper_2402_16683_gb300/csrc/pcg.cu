@@ -27,8 +27,10 @@ using namespace nre;
 namespace {
 
 constexpr int PC_THREADS = 256;
+// SC_XALPHA: the update kernel's alpha, whose step x += alpha p the p-update
+// kernel applies (it reads p anyway: one vector read less per iteration).
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
-       SC_ITERS = CG_SC_ITERS, SC_N = CG_SC_N };
+       SC_ITERS = CG_SC_ITERS, SC_XALPHA = 6, SC_N = CG_SC_N };
 
 // Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
@@ -172,11 +174,12 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_init(const T* bsrc, T* x, T*
   if (pc.nb > 0) bins_out(pc, b, hist);
 }
 
-// alpha = r.z / p.q (p.q from npq partials per system); x += alpha p;
-// r -= alpha q; partials of r.r and of the bins of r.
+// alpha = r.z / p.q (p.q from npq partials per system), kept in SC_XALPHA
+// for the p-update kernel's x += alpha p; r -= alpha q; partials of r.r and
+// of the bins of r.
 template <typename T>
-__global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* p, const T* q, int64_t n,
-                                                          int64_t S, const double* sc, const double* pq_part,
+__global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* r, const T* q, int64_t n, int64_t S, double* sc,
+                                                          const double* pq_part,
                                                           int npq, double* rr_part, PCArgs<T> pc) {
   extern __shared__ double hist[];
   constexpr int W = PV<T>::W;
@@ -185,11 +188,15 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
   for (int i = threadIdx.x; i < (PC_THREADS / 32) * pc.nb; i += blockDim.x) hist[i] = 0.0;
   double* whist = hist + (threadIdx.x >> 5) * pc.nb;
   __syncthreads();
-  const double* c = sc + b * SC_N;
+  double* c = sc + b * SC_N;
   const bool active = c[SC_ACTIVE] != 0.0;
   __shared__ T s_alpha;  // one FP64 division per block, not per thread
   const double pq = block_sum_array(pq_part + (int64_t)b * npq, npq);
-  if (threadIdx.x == 0) s_alpha = T(active && pq != 0.0 ? c[SC_RZ] / pq : 0.0);
+  if (threadIdx.x == 0) {
+    const T al = T(active && pq != 0.0 ? c[SC_RZ] / pq : 0.0);
+    s_alpha = al;
+    if (blockIdx.x == 0) c[SC_XALPHA] = double(al);
+  }
   __syncthreads();
   const T alpha = s_alpha;
   const int64_t off = (int64_t)b * S;
@@ -200,14 +207,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
     if (full) {
       PV<T> ri = ldp(r + off + i);
       if (active) {
-        PV<T> xi = ldp(x + off + i);
-        const PV<T> pi = ldp(p + off + i), qi = ldp(q + off + i);
+        const PV<T> qi = ldp(q + off + i);
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          xi.e[k] += alpha * pi.e[k];
-          ri.e[k] -= alpha * qi.e[k];
-        }
-        stp(x + off + i, xi);
+        for (int k = 0; k < W; ++k) ri.e[k] -= alpha * qi.e[k];
         stp(r + off + i, ri);
       }
 #pragma unroll
@@ -222,7 +224,6 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_update(T* x, T* r, const T* 
         if (i + k < n) {
           T ri = r[off + i + k];
           if (active) {
-            x[off + i + k] += alpha * p[off + i + k];
             ri -= alpha * q[off + i + k];
             r[off + i + k] = ri;
           }
@@ -363,14 +364,17 @@ __global__ void k_pcg_start(double* sc, const double* rr_part, const double* rz_
   c[SC_BB] = rr;
   c[SC_RZ] = rz;
   c[SC_BETA] = 0.0;
+  c[SC_XALPHA] = 0.0;
   c[SC_ITERS] = 0.0;
   c[SC_ACTIVE] = (rr > 0.0 && rtol < 1.0) ? 1.0 : 0.0;
 }
 
-// beta = r'.z' / r.z and p = z + beta p (every block reads the old r.z; the
-// scalars are updated by k_pcg_finish afterwards).
+// x += alpha p (the update kernel's step), then beta = r'.z' / r.z and
+// p = z + beta p (every block reads the old r.z; the scalars, the activity
+// flag included, are updated by k_pcg_finish afterwards, so a system active
+// in the update kernel is active here).
 template <typename T>
-__global__ void __launch_bounds__(PC_THREADS) k_pcg_pupdate(T* p, const T* z, int64_t n, int64_t S,
+__global__ void __launch_bounds__(PC_THREADS) k_pcg_pupdate(T* x, T* p, const T* z, int64_t n, int64_t S,
                                                            const double* sc, const double* rz_part, int nblk) {
   constexpr int W = PV<T>::W;
   const int b = blockIdx.y;
@@ -380,18 +384,26 @@ __global__ void __launch_bounds__(PC_THREADS) k_pcg_pupdate(T* p, const T* z, in
   const double rz = block_sum_array(rz_part + (int64_t)b * nblk, nblk);
   if (threadIdx.x == 0) s_beta = T(rz / c[SC_RZ]);
   __syncthreads();
-  const T beta = s_beta;
+  const T beta = s_beta, xa = T(c[SC_XALPHA]);
   const int64_t off = (int64_t)b * S;
   for_pv<T>(n, [&](int64_t i, bool full) {
     if (full) {
       const PV<T> zi = ldp(z + off + i);
-      PV<T> pi = ldp(p + off + i);
+      PV<T> pi = ldp(p + off + i), xi = ldp(x + off + i);
 #pragma unroll
-      for (int k = 0; k < W; ++k) pi.e[k] = zi.e[k] + beta * pi.e[k];
+      for (int k = 0; k < W; ++k) {
+        xi.e[k] += xa * pi.e[k];
+        pi.e[k] = zi.e[k] + beta * pi.e[k];
+      }
+      stp(x + off + i, xi);
       stp(p + off + i, pi);
     } else {
       for (int k = 0; k < W; ++k)
-        if (i + k < n) p[off + i + k] = z[off + i + k] + beta * p[off + i + k];
+        if (i + k < n) {
+          const T pv = p[off + i + k];
+          x[off + i + k] += xa * pv;
+          p[off + i + k] = z[off + i + k] + beta * pv;
+        }
     }
   });
 }
@@ -818,15 +830,15 @@ int pcg_iter_t(nre_metric* m, T* x, int B, int iters, double rtol, cudaStream_t 
   for (int it = 0; it < iters; ++it) {
     // p.q comes fused with the metric product (kDotStride partials per system)
     NRE_TRY(metric_apply_impl(m, w.p, w.q, B, st, m->cg_dot.as<double>()));
-    prof_begin("pcg_update", 6 * vb, st);
+    prof_begin("pcg_update", 3 * vb, st);
     NRE_TRY(pc_smem(k_pcg_update<T>, w.hsm));
-    k_pcg_update<T><<<grid, PC_THREADS, w.hsm, st>>>(x, w.r, w.p, w.q, n, S, w.sc, m->cg_dot.as<double>(),
-                                                      kDotStride, w.part_rr, w.pc);
+    k_pcg_update<T><<<grid, PC_THREADS, w.hsm, st>>>(w.r, w.q, n, S, w.sc, m->cg_dot.as<double>(), kDotStride,
+                                                      w.part_rr, w.pc);
     prof_end(st);
     NRE_CHECK_LAUNCH();
     NRE_TRY(pcg_precondition<T>(m, w, B, 0, st));
-    prof_begin("cg_pupdate", 3 * vb, st);
-    k_pcg_pupdate<T><<<grid, PC_THREADS, 0, st>>>(w.p, w.z, n, S, w.sc, w.part_rz, w.nblk);
+    prof_begin("cg_pupdate", 5 * vb, st);
+    k_pcg_pupdate<T><<<grid, PC_THREADS, 0, st>>>(x, w.p, w.z, n, S, w.sc, w.part_rz, w.nblk);
     prof_end(st);
     prof_begin("cg_scalars", 0.0, st);
     k_pcg_finish<<<B, 32, 0, st>>>(w.sc, w.part_rr, w.part_rz, w.nblk, rtol);

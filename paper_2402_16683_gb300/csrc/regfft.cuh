@@ -36,10 +36,12 @@ template <typename C, int L, int NS>
 __host__ __device__ constexpr int exch_q() { return (sizeof(C) == 8 && L / 8 >= 32 && NS == 8) ? 2 : 1; }
 template <typename C, int L>
 __host__ __device__ constexpr int mirror_q() { return (sizeof(C) == 8 && L / 8 >= 32) ? 0 : 1; }
-// Line stride: room for the widest layout (Q = 2 from 256 points on) plus one;
+// Line stride: room for the widest layout (Q = 2 from 256 points on: highest
+// index L + L/8 - 3; the mirror exchange's extra element at qpad(L) with Q <= 1);
 // up to 128 points an odd number of complex elements, so that the lines that
-// share a warp sit on different banks.
-__host__ __device__ constexpr int rline(int L) { return L >= 256 ? L + L / 8 + 1 : L + L / 16 + 1; }
+// share a warp sit on different banks (from 256 points on a warp holds one
+// line, and the lines' relative banks do not matter).
+__host__ __device__ constexpr int rline(int L) { return L >= 256 ? L + L / 8 : L + L / 16 + 1; }
 // Line stride when NL lines are interleaved across the lanes of a warp: the
 // lines start 16/NL complex elements apart modulo 16.
 __host__ __device__ constexpr int rline_il(int L, int NL) { return L + L / 16 + (NL < 16 ? 16 / NL : 1); }

@@ -132,17 +132,33 @@ int col_reg_L(ColArgs<T> a, bool mid, int B, bool bins, int* nparts, cudaStream_
       const uint64_t sin[3] = {(uint64_t)a.inner * 4, (uint64_t)L * a.inner * 4, (uint64_t)a.pro.xs * 4};
       const uint64_t sout[3] = {(uint64_t)a.inner * 4, (uint64_t)L * a.inner * 4, (uint64_t)a.epi.ys * 4};
       const uint32_t box[4] = {(uint32_t)TM::W, (uint32_t)TM::RB, 1u, 1u};
-      CUtensorMap tin, tout;
+      CUtensorMap tin, tout, twt;
       int s = tmap_tiled(&tin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.pro.x, dims, sin, box, TM::SWB);
       if (s == NRE_OK) s = tmap_tiled(&tout, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.epi.y, dims, sout, box, TM::SWB);
+      int wb = 0;  // the weights' sample coordinate per sample: 0 when all samples share w
+      if (s == NRE_OK && mid) {
+        // the weights w ([N] shared, or [B][N]) in the tiles' geometry
+        if (!al(a.mid.w) || a.mid.ws % 4 != 0) {
+          s = NRE_EINVAL;
+        } else {
+          wb = a.mid.ws != 0 ? 1 : 0;
+          const uint64_t wd[4] = {dims[0], dims[1], dims[2], (uint64_t)(wb ? B : 1)};
+          const uint64_t sw[3] = {sin[0], sin[1], wb ? (uint64_t)a.mid.ws * 4 : sin[1] * (uint64_t)outer};
+          s = tmap_tiled(&twt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.mid.w, wd, sw, box, TM::SWB);
+        }
+      }
       if (s == NRE_OK) {
-        const size_t tsm = TM::bytes();
+        const size_t tsm = TM::bytes(mid);
+        // persistent grid for this kernel's own shared memory (no bin sums here)
+        const int gxt = persistent_gx(a.n_units, B, resident_ctas(col_min_ctas(NT, 4), tsm));
+        *nparts = gxt;
+        const dim3 gridt((unsigned)gxt, B);
         if (mid) {
           NRE_TRY(set_smem(k_col_tma<L, true>, tsm));
-          k_col_tma<L, true><<<grid, NT, tsm, st>>>(a, tin, tout, status);
+          k_col_tma<L, true><<<gridt, NT, tsm, st>>>(a, tin, tout, twt, wb, status);
         } else {
           NRE_TRY(set_smem(k_col_tma<L, false>, tsm));
-          k_col_tma<L, false><<<grid, NT, tsm, st>>>(a, tin, tout, status);
+          k_col_tma<L, false><<<gridt, NT, tsm, st>>>(a, tin, tout, tin, 0, status);
         }
         prof_end(st);
         NRE_CHECK_LAUNCH();

@@ -181,14 +181,9 @@ __device__ __noinline__ void row_issue_bulk(const T* src, int64_t ss, const int*
   }
   const unsigned nv = __popc(__ballot_sync(0xffffffffu, ok));
   constexpr unsigned RB = (unsigned)(L * sizeof(T));
-  if (lane == 0)
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(nv * RB) : "memory");
+  if (lane == 0) mbar_arrive_tx_at(bar, nv * RB);
   __syncwarp();
-  if (ok)
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     dst + (unsigned)lane * RB),
-                 "l"(g), "r"(RB), "r"(bar)
-                 : "memory");
+  if (ok) bulk_g2s(dst + (unsigned)lane * RB, g, RB, bar);
 }
 
 template <typename T, int L, int PM, bool MID, int PK, int EK>
@@ -802,6 +797,9 @@ __global__ void __launch_bounds__(ColShape<L, sizeof(T)>::NT, col_min_ctas(ColSh
 // keeps a half-warp's 8-byte column-pair accesses at two wavefronts.  Waits
 // are bounded: a wait that runs out (decided for the whole CTA) is counted in
 // *status and the CTA stops after waiting, again bounded, for its copies.
+// The metric's sweep (MID) also loads the unit's tile of the weights w (same
+// boxes and layout, one buffer) when the unit starts; it is first read after
+// the forward transform, which hides the copy.
 template <int L>
 struct ColTma {
   typedef ColShape<L, 4> CS;
@@ -812,7 +810,13 @@ struct ColTma {
   // lines; buffers start at multiples of 1024 bytes (the swizzle's alignment)
   static constexpr int LNSZ = CS::NL * rline(L) * 2;  // floats
   static constexpr int BUFB = ((XS > LNSZ ? XS : LNSZ) * 4 + 1023) / 1024 * 1024;
-  static size_t bytes() { return 1024 + (size_t)2 * BUFB + (size_t)L * 8; }
+  // bytes: the two buffers, the weights (MID), the twiddle tables, the three
+  // mbarriers; the dynamic shared memory (the kernel's only shared memory)
+  // starts on a 1024-byte boundary, which the kernel checks
+  static constexpr int TWB = (tw_total(L) * 8 + 15) / 16 * 16;
+  static constexpr size_t bytes(bool mid) { return (size_t)2 * BUFB + (mid ? (size_t)XS * 4 : 0) + TWB + 32; }
+  // four CTAs per SM (1 KB reserved per CTA, 228 KB per SM) for lines of up to 512 points
+  static_assert(L > 512 || 4 * (bytes(true) + 1024) <= 228 * 1024, "column tiles exceed a quarter SM");
   // float index of element (l, col) of a tile
   __device__ __forceinline__ static int at(int l, int col) {
     const unsigned A = (unsigned)(l * W + col) * 4u;
@@ -823,17 +827,23 @@ struct ColTma {
 template <int L, bool MID>
 __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4>::NT, 4))
     k_col_tma(ColArgs<float> a, const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-              unsigned* status) {
+              const __grid_constant__ CUtensorMap twt, int wb, unsigned* status) {
   typedef float T;
   typedef float2 C;
   typedef ColTma<L> TM;
   constexpr int T8 = L / 8, W = TM::W, XS = TM::XS, RB = TM::RB, NBOX = TM::NBOX, LS = rline(L);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
-  const unsigned s0 = smem_u32(smem_raw);
-  unsigned char* bufs = smem_raw + (((s0 + 1023u) & ~1023u) - s0);
+  extern __shared__ __align__(1024) unsigned char smem_tma[];
+  unsigned char* bufs = smem_tma;
+  // the swizzled tiles need 1024-byte alignment (the layout's assumption; a
+  // CTA that finds otherwise does nothing and is counted)
+  if ((smem_u32(bufs) & 1023u) != 0) {
+    if (threadIdx.x == 0) note_timeout(status);
+    return;
+  }
   auto tile = [&](int buf) { return reinterpret_cast<T*>(bufs + buf * TM::BUFB); };
-  C* tw = reinterpret_cast<C*>(bufs + 2 * TM::BUFB);
+  T* WT = reinterpret_cast<T*>(bufs + 2 * TM::BUFB);  // MID: the unit's weights (a multiple of 1024 bytes)
+  C* tw = reinterpret_cast<C*>(bufs + 2 * TM::BUFB + (MID ? XS * 4 : 0));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bufs + 2 * TM::BUFB + (MID ? XS * 4 : 0) + TM::TWB);  // halves, weights
   const int b = blockIdx.y;
   load_twiddles<L>(tw, a.tw, a.log2Lmax - a.log2L);
   const int u = threadIdx.x / T8, t = threadIdx.x - u * T8;
@@ -842,6 +852,7 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -861,13 +872,20 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
       bulk_wait_read0();  // the store of two units ago has read the other half
       issue(unit + gridDim.x, cur ^ 1);
     }
+    if (MID && threadIdx.x == 0) {
+      // this unit's weights (the last unit's reads of WT came before the
+      // proxy fence and barrier ahead of its store)
+      const int z = (int)(unit >> nblk_sh), x = (int)((unit & (a.nblk - 1)) * W);
+      mbar_arrive_tx(&bar[2], (unsigned)(XS * 4));
+#pragma unroll
+      for (int k = 0; k < NBOX; ++k) tma_load_4d(WT + k * RB * W, &twt, x, k * RB, z, wb * b, &bar[2]);
+    }
     const bool ok = mbar_wait(&bar[cur], (unsigned)(it >> 1) & 1u);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
     }
     const int64_t o = unit >> nblk_sh;
-    const int64_t base = o * L * a.inner + (unit & (a.nblk - 1)) * W;
     T* X = tile(cur);
     C v[1][8];
 #pragma unroll
@@ -879,12 +897,17 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
     C zm[1][8];
     if constexpr (MID) {
       reg_mirror<C, L, 1>(v, zm, smc, t, sync);
+      const bool okw = mbar_wait(&bar[2], (unsigned)it & 1u);
+      if (__syncthreads_or(!okw)) {
+        timed_out = true;
+        break;
+      }
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         T ha[2], hb[2];
         hartley_unpack<T>(v[0][s], zm[0][s], ha, hb);
-        const int64_t flat = base + (int64_t)(t + T8 * s) * a.inner + 2 * u;
-        v[0][s] = a.mid.apply2(b, flat, ha[0], hb[0]);
+        const C ww = *reinterpret_cast<const C*>(WT + TM::at(t + T8 * s, 2 * u));
+        v[0][s] = cmake<C>(ww.x * ha[0], ww.y * hb[0]);
       }
       reg_fft<C, L, 1>(v, smc, tw, t, sync);
     }
@@ -907,8 +930,10 @@ __global__ void __launch_bounds__(ColShape<L, 4>::NT, col_min_ctas(ColShape<L, 4
   }
   if (timed_out && threadIdx.x == 0) {
     note_timeout(status);
-    // the loads in flight: the current unit's and the one issued for the next
+    // the loads in flight: the current unit's (and its weights) and the one
+    // issued for the next
     mbar_wait(&bar[it & 1], (unsigned)(it >> 1) & 1u);
+    if (MID) mbar_wait(&bar[2], (unsigned)it & 1u);
     if (unit + gridDim.x < a.n_units) mbar_wait(&bar[(it + 1) & 1], (unsigned)((it + 1) >> 1) & 1u);
   }
   if (threadIdx.x == 0) bulk_wait0();

@@ -91,13 +91,17 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int
       : "memory");
 }
 
-// Bulk copy of `bytes` contiguous bytes (16-byte aligned, a multiple of 16)
-// from global into shared memory, completing on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+// Bulk copy of `bytes` contiguous bytes (both addresses 16-byte aligned, a
+// multiple of 16 bytes) from global memory to the shared address dst,
+// completing on the mbarrier at shared address bar.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+// mbar_arrive_tx on the barrier at shared address bar.
+__device__ __forceinline__ void mbar_arrive_tx_at(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // Bulk tensor store of a box from shared memory (this thread's bulk group).
