@@ -86,19 +86,19 @@ def parse():
 # from the current sources is stale and reported as null.
 # row_sweep_f32_2d at batch 32: the traced (unsplit) launches take the whole
 # batch; the capture ran the half-batch launches of the split product (16
-# samples): 18.18 MB (prologue sweep) and 34.95 MB (epilogue sweep) read,
-# 0.03 MB written, scaled by two (traffic grows with the samples; the shared
+# samples): 18.18 MB (prologue sweep) and 34.84 MB (epilogue sweep) read,
+# 0.02 MB written, scaled by two (traffic grows with the samples; the shared
 # bin and expansion-point tables, 1.5 MB, are then counted twice) and
 # averaged over the two variants (profiles/traffic_f32_2d_512x512_b32.md).
-DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.16e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.04e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                                     "half-batch launches x 2, mean of the two row sweeps",
-                                           "2fb294d269bc40d1")}
+                                           "4df23f8d79e2b4f7")}
 
 # The sources that define the row sweeps' device code (the digest of
-# DRAM_TRAFFIC); the C header and the bulk-copy helpers, which the column
-# sweeps use, do not enter it.
-SWEEP_SOURCES = ["common.cuh", "cf_internal.cuh", "fft.cuh", "regfft.cuh", "sweeps_reg.cuh", "sweeps_launch.cuh",
-                 "sweeps_inst.cu"]
+# DRAM_TRAFFIC), the bulk-copy helpers of their row staging included; the C
+# header does not enter it.
+SWEEP_SOURCES = ["common.cuh", "cf_internal.cuh", "fft.cuh", "regfft.cuh", "tma.cuh", "sweeps_reg.cuh",
+                 "sweeps_launch.cuh", "sweeps_inst.cu"]
 
 
 def kernel_src_digest(files=SWEEP_SOURCES):
