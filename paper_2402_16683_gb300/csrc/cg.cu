@@ -22,9 +22,11 @@ constexpr int CG_THREADS = 256;
 enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE = CG_SC_ACTIVE,
        SC_ITERS = CG_SC_ITERS, SC_XALPHA = 6, SC_N = CG_SC_N };
 
-// Blocks per system of the vector kernels: about four waves of the device's SMs
-// over the whole batch (enough loads in flight, few partials to fold), at
-// least 4 vectors per thread and at most 64 blocks.
+// Blocks per system of the vector kernels: four per SM over the whole batch,
+// one wave (each block forms alpha and its share of the hyper rows before and
+// after its vector loop; 8, 12 and 16 per SM measured 36, 54 and 65 % slower
+// update kernels at 512^2, batch 32), at least 4 vectors per thread and at
+// most 64 blocks.
 int cg_blocks(int64_t n, int B) {
   int64_t nb = (4 * (int64_t)sm_count() + B - 1) / B;
   const int64_t cap = (n + CG_THREADS * 16 - 1) / (CG_THREADS * 16);

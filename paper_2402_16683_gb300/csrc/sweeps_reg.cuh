@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   // otherwise every thread copies 16-byte chunks with cp.async.
   constexpr int NROWS = NU * SLOTS;
   constexpr bool BULK = NROWS <= 32;
-  __shared__ __align__(8) uint64_t sbar[3];
+  __shared__ __align__(8) uint64_t sbar[3];  // stage halves, base rows
   if constexpr (BULK) {
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -435,13 +435,22 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       const T half = T(0.5), a0 = epi.av.a0t;
       const bool t0 = t == 0;
       T dsum = T(0);
+      // ECH column pairs per phase: all their loads go out before the first
+      // is used (two pairs measured 0.6 % faster than one for FP32 2-D orbits
+      // of 512 points; one where two would spill more than a few bytes)
+      constexpr int ECH = (PM == 2 && sizeof(T) == 4 && L >= 128) ? 2 : 1;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
+      for (int s0 = 0; s0 < 4; s0 += ECH) {
+      int bnA[ECH][SLOTS], bn2A[ECH][SLOTS];
+      T xvA[ECH][2][SLOTS], bvvA[ECH][2][SLOTS];
+#pragma unroll
+      for (int cc = 0; cc < ECH; ++cc) {
+        const int s = s0 + cc;
         const int x = t + T8 * s;
         const bool sp = s == 0 && t0;
         const int x2 = sp ? L / 2 : L - x;
-        int bn[SLOTS], bn2[SLOTS];
-        T xv[2][SLOTS], bvv[2][SLOTS], val[2][SLOTS];
+        int(&bn)[SLOTS] = bnA[cc];
+        int(&bn2)[SLOTS] = bn2A[cc];
 #pragma unroll
         for (int sl = 0; sl < SLOTS; ++sl) {
           // mirror rows of a 2-D orbit share the canonical slot's bins
@@ -454,16 +463,28 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
             if (s == 0) bn2[sl] = (valid && sp) ? (int)__ldg(&bp[f2]) : bn[sl];
           }
           if (s != 0) bn2[sl] = bn[sl];
-          xv[0][sl] = valid ? __ldg(&xp[f]) : T(0);
-          xv[1][sl] = valid ? __ldg(&xp[f2]) : T(0);
+          xvA[cc][0][sl] = valid ? __ldg(&xp[f]) : T(0);
+          xvA[cc][1][sl] = valid ? __ldg(&xp[f2]) : T(0);
           if constexpr (DIRECT_BASE) {
-            bvv[0][sl] = valid ? bsrc[f] : T(0);
-            bvv[1][sl] = valid ? bsrc[f2] : T(0);
+            bvvA[cc][0][sl] = valid ? bsrc[f] : T(0);
+            bvvA[cc][1][sl] = valid ? bsrc[f2] : T(0);
           } else {
-            bvv[0][sl] = BV[sl * L + x];
-            bvv[1][sl] = BV[sl * L + x2];
+            bvvA[cc][0][sl] = BV[sl * L + x];
+            bvvA[cc][1][sl] = BV[sl * L + x2];
           }
         }
+      }
+#pragma unroll
+      for (int cc = 0; cc < ECH; ++cc) {
+        const int s = s0 + cc;
+        const int x = t + T8 * s;
+        const bool sp = s == 0 && t0;
+        const int x2 = sp ? L / 2 : L - x;
+        const int(&bn)[SLOTS] = bnA[cc];
+        const int(&bn2)[SLOTS] = bn2A[cc];
+        T (&xv)[2][SLOTS] = xvA[cc];
+        T (&bvv)[2][SLOTS] = bvvA[cc];
+        T val[2][SLOTS];
         if constexpr (PM == 2) {
           T R[2][2], R2[2][2];
           hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
@@ -523,6 +544,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
           for (int sl = 0; sl < SLOTS; ++sl) cm[sl] = c[sl] + c[SLOTS + sl];
           add_slots<SLOTS, T>(bn, cm, whist);
         }
+      }
       }
       if (dot) dacc.add(dsum);
     } else {
