@@ -392,9 +392,12 @@ int metric_set_precond(nre_metric *m, int kind, nre_stream_t stream);
  * metrics, CG workspaces, servers), summed over all devices. */
 int nre_device_bytes(int64_t *bytes);
 
-/* Kernels that stage tiles with bulk tensor copies (TMA) wait for them on a
+/* Kernels that stage tiles or rows with bulk copies (TMA tiles of the column
+ * sweeps and the ICR adjoint, whole rows of the row sweeps) wait for them on a
  * shared-memory barrier with an iteration limit (about a second); a wait that
- * runs out makes the kernel skip the rest of its work and counts here.  Writes
+ * runs out makes the kernel skip the rest of its work (the row sweeps: after
+ * finishing the current unit group with void results) and counts here, as
+ * does a column-sweep CTA whose shared memory is not 1024-byte aligned.  Writes
  * the count of the current device to *count and, if reset != 0, clears it;
  * synchronises the device.  A nonzero count means that some output of an
  * earlier call is incomplete. */

@@ -250,4 +250,18 @@ __device__ __forceinline__ double block_sum_array(const double* p, int n) {
   return r;
 }
 
+// Raises kernel k's dynamic shared-memory limit to `dyn` bytes where its
+// static plus dynamic shared memory exceed the default 48 KB (a kernel with
+// static barriers or reduction slots needs the raise below 48 KB of dynamic
+// memory already).
+template <typename K>
+int raise_smem(K k, size_t dyn) {
+  if (dyn <= 40 * 1024) return NRE_OK;
+  cudaFuncAttributes fa{};
+  NRE_TRY_CUDA(cudaFuncGetAttributes(&fa, k));
+  if (dyn + fa.sharedSizeBytes > 48 * 1024)
+    NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  return NRE_OK;
+}
+
 }  // namespace nre

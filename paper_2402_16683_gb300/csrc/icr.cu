@@ -878,8 +878,7 @@ int icr_forward_range(nre_icr_plan* p, const T* xi, T* s, int b0, int B, const T
     const bool all = sp.nlev == p->n_levels;
     const int ncl = sp.nc[sp.nlev - 1];
     const size_t smem = (size_t)small_smem(sp, false) * sizeof(T);
-    if (smem > 48 * 1024)
-      NRE_TRY_CUDA(cudaFuncSetAttribute(k_icr_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NRE_TRY(nre::raise_smem(k_icr_small<T>, smem));
     double xib = 0.0;
     for (int l = 0; l < sp.nlev; ++l) xib += 4.0 * sp.nc[l] * sp.nc[l];
     prof_begin("icr_small", (double)B * sizeof(T) * (n2 + xib + 4.0 * ncl * ncl * (all && scale ? 2 : 1)), st);
@@ -978,8 +977,7 @@ int icr_vjp_range(nre_icr_plan* p, const T* ct, int64_t cts, T* g, const T* base
     // the coarse refinements and level 0 in one CTA per sample
     const int ncl = sp.nc[sp.nlev - 1];
     const size_t smem = (size_t)small_smem(sp, true) * sizeof(T);
-    if (smem > 48 * 1024)
-      NRE_TRY_CUDA(cudaFuncSetAttribute(k_icr_small_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NRE_TRY(nre::raise_smem(k_icr_small_t<T>, smem));
     double xib = 0.0;
     for (int l = 0; l < sp.nlev; ++l) xib += 4.0 * sp.nc[l] * sp.nc[l];
     prof_begin("icr_small_t", (double)B * sizeof(T) * (4.0 * ncl * ncl + (xib + n2) * (base ? 2 : 1)), st);

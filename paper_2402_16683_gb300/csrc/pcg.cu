@@ -35,12 +35,11 @@ enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_RZ = 2, SC_BETA = 3, SC_ACTIVE = C
 // Blocks per system of the vector kernels: about four waves of the device's SMs
 // over the whole batch (enough loads in flight, few partials to fold), at
 // least 4 vectors per thread and at most 64 blocks.
-// Dynamic shared memory above the 48 KB default (warp-private histograms of
-// up to 1024 bins).
+// Dynamic shared memory beyond the 48 KB default with the static (warp-private
+// histograms of up to 1024 bins).
 template <typename K>
 int pc_smem(K k, size_t bytes) {
-  if (bytes > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return NRE_OK;
+  return raise_smem(k, bytes);
 }
 
 int pc_blocks(int64_t n, int B) {

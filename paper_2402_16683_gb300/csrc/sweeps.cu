@@ -265,7 +265,7 @@ size_t row_smem(int L, int nl, int nhist, int nb) {
 template <typename T, int PM, bool MID>
 int launch_row(const RowArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
   auto k = k_row_sweep<T, PM, MID>;
-  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NRE_TRY(raise_smem(k, smem));
   prof_begin(row_name(PM, MID, sizeof(T)), sweep_bytes<T>(a.pro, a.epi, &a.mid, MID, a.B, N), st);
   k<<<grid, SWEEP_THREADS, smem, st>>>(a);
   prof_end(st);
@@ -276,7 +276,7 @@ int launch_row(const RowArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int
 template <typename T, bool MID>
 int launch_col(const ColArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st, int64_t N) {
   auto k = k_col_sweep<T, MID>;
-  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NRE_TRY(raise_smem(k, smem));
   const char* name = sizeof(T) == 8 ? (MID ? "col_sweep_f64_metric" : "col_sweep_f64")
                                     : (MID ? "col_sweep_f32_metric" : "col_sweep_f32");
   prof_begin(name, sweep_bytes<T>(a.pro, a.epi, &a.mid, MID, (int)grid.y, N), st);

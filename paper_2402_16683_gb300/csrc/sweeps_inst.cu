@@ -10,8 +10,7 @@ namespace nre {
 
 template <typename K>
 static int set_smem(K k, size_t smem) {
-  if (smem > 48 * 1024) NRE_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return NRE_OK;
+  return raise_smem(k, smem);
 }
 
 template <typename T, int L, int PM, bool MID, int PK, int EK>

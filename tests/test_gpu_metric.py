@@ -72,6 +72,9 @@ def lanczos_kappa(om, xi_p, w, b, iters):
     ((32, 64), "power", "f64", "poisson"),
     ((16, 8, 32), "power", "f64", "gauss"),
     ((512, 512), "power", "f32", "poisson"),
+    # 256-point rows with 256 bins: the epilogue sweep's dynamic shared memory
+    # is exactly 48 KB, plus its static barriers
+    ((256, 256), "power", "f32", "poisson"),
     ((64, 64, 64), "power", "f32", "gauss"),
     ((4096,), "power", "f32", "gauss"),
     ((1024, 1024), "power", "f32", "gauss"),

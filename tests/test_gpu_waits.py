@@ -1,7 +1,7 @@
-"""Bounded waits of the kernels that stage tiles with bulk tensor copies: a wait
-that nothing completes (a barrier expecting bytes that no copy delivers) runs
-out after its iteration limit, the kernel counts it and returns, and the
-context stays usable."""
+"""Bounded waits of the kernels that stage tiles and rows with bulk copies: a
+wait that nothing completes (a barrier expecting bytes that no copy delivers)
+runs out after its iteration limit, the kernel counts it and returns, and the
+context stays usable.  (Every other GPU test checks that no wait ran out.)"""
 import ctypes as C
 
 import pytest
