@@ -87,12 +87,12 @@ def parse():
 # row_sweep_f32_2d at batch 32: the traced (unsplit) launches take the whole
 # batch; the capture ran the half-batch launches of the split product (16
 # samples): 18.18 MB (prologue sweep) and 34.84 MB (epilogue sweep) read,
-# 0.02 MB written, scaled by two (traffic grows with the samples; the shared
+# 0.01 MB written, scaled by two (traffic grows with the samples; the shared
 # bin and expansion-point tables, 1.5 MB, are then counted twice) and
 # averaged over the two variants (profiles/traffic_f32_2d_512x512_b32.md).
-DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.04e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.03e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                                     "half-batch launches x 2, mean of the two row sweeps",
-                                           "4df23f8d79e2b4f7")}
+                                           "afca50f459a2e6e7")}
 
 # The sources that define the row sweeps' device code (the digest of
 # DRAM_TRAFFIC), the bulk-copy helpers of their row staging included; the C
