@@ -71,6 +71,9 @@ def lanczos_kappa(om, xi_p, w, b, iters):
     ((256,), "power", "f64", "poisson"),
     ((32, 64), "power", "f64", "poisson"),
     ((16, 8, 32), "power", "f64", "gauss"),
+    # FP64 rows of 256 points: the bulk-copy row staging of 2-D and 3-D orbits
+    ((128, 256), "power", "f64", "poisson"),
+    ((4, 8, 256), "power", "f64", "gauss"),
     ((512, 512), "power", "f32", "poisson"),
     # 256-point rows with 256 bins: the epilogue sweep's dynamic shared memory
     # is exactly 48 KB, plus its static barriers
