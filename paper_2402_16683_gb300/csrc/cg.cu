@@ -25,8 +25,8 @@ enum { SC_RR = CG_SC_RR, SC_BB = CG_SC_BB, SC_ALPHA = 2, SC_BETA = 3, SC_ACTIVE 
 // Blocks per system of the vector kernels: four per SM over the whole batch,
 // one wave (each block forms alpha and its share of the hyper rows before and
 // after its vector loop; 8, 12 and 16 per SM measured 36, 54 and 65 % slower
-// update kernels at 512^2, batch 32), at least 4 vectors per thread and at
-// most 64 blocks.
+// update kernels at 512^2, batch 32, and 2 or 3 per SM 14 and 7 % slower), at
+// least 4 vectors per thread and at most 64 blocks.
 int cg_blocks(int64_t n, int B) {
   int64_t nb = (4 * (int64_t)sm_count() + B - 1) / B;
   const int64_t cap = (n + CG_THREADS * 16 - 1) / (CG_THREADS * 16);
