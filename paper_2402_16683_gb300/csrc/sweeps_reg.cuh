@@ -417,15 +417,16 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
     }
     const T* BV = bstage + u * SLOTS * L;
     if constexpr (EK == SK_TAB && PM >= 2) {
-      // The metric's epilogue, one column pair per phase: column x = t + T8 s
-      // (s < 4, so x < L / 2) and its mirror x' = L - x.  Both outputs come
+      // The metric's epilogue over column pairs: column x = t + T8 s (s < 4,
+      // so x < L / 2) and its mirror x' = L - x.  Both outputs come
       // from the pair (z(x), z(x')) that the unpack reads (the mirror's with
       // the two columns' roles swapped: the same arithmetic as the unpack at
       // x' itself), and the bins, which depend on |k| only, are the same at x
       // and x', so each slot's two contributions go into one warp reduction.
       // Thread 0's pair at s = 0 is x = 0 and L / 2, each its own mirror.
-      // Per phase: A) the per-pixel loads (bins, expansion point, base), all
-      // in flight before they are used, B) values, stores, bin reductions.
+      // Per phase of ECH pairs: A) the per-pixel loads (bins, expansion point,
+      // base), all in flight before they are used, B) values, stores, bin
+      // reductions.
       const int16_t* bp = epi.av.bpix;
       const T* xp = epi.xi_p + (int64_t)bsample * epi.ps;
       const T* bsrc = epi.base + (int64_t)bsample * epi.bs;  // the TAB epilogue always has a base
@@ -441,110 +442,110 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       constexpr int ECH = (PM == 2 && sizeof(T) == 4 && L >= 128) ? 2 : 1;
 #pragma unroll
       for (int s0 = 0; s0 < 4; s0 += ECH) {
-      int bnA[ECH][SLOTS], bn2A[ECH][SLOTS];
-      T xvA[ECH][2][SLOTS], bvvA[ECH][2][SLOTS];
+        int bnA[ECH][SLOTS], bn2A[ECH][SLOTS];
+        T xvA[ECH][2][SLOTS], bvvA[ECH][2][SLOTS];
 #pragma unroll
-      for (int cc = 0; cc < ECH; ++cc) {
-        const int s = s0 + cc;
-        const int x = t + T8 * s;
-        const bool sp = s == 0 && t0;
-        const int x2 = sp ? L / 2 : L - x;
-        int(&bn)[SLOTS] = bnA[cc];
-        int(&bn2)[SLOTS] = bn2A[cc];
+        for (int cc = 0; cc < ECH; ++cc) {
+          const int s = s0 + cc;
+          const int x = t + T8 * s;
+          const bool sp = s == 0 && t0;
+          const int x2 = sp ? L / 2 : L - x;
+          int(&bn)[SLOTS] = bnA[cc];
+          int(&bn2)[SLOTS] = bn2A[cc];
 #pragma unroll
-        for (int sl = 0; sl < SLOTS; ++sl) {
-          // mirror rows of a 2-D orbit share the canonical slot's bins
-          const int f = row[sl] * L + x, f2 = row[sl] * L + x2;
-          if (PM == 2 && sl == 1 && f0) {
-            bn[1] = bn[0];
-            if (s == 0) bn2[1] = bn2[0];
-          } else {
-            bn[sl] = valid ? (int)__ldg(&bp[f]) : -1;
-            if (s == 0) bn2[sl] = (valid && sp) ? (int)__ldg(&bp[f2]) : bn[sl];
-          }
-          if (s != 0) bn2[sl] = bn[sl];
-          xvA[cc][0][sl] = valid ? __ldg(&xp[f]) : T(0);
-          xvA[cc][1][sl] = valid ? __ldg(&xp[f2]) : T(0);
-          if constexpr (DIRECT_BASE) {
-            bvvA[cc][0][sl] = valid ? bsrc[f] : T(0);
-            bvvA[cc][1][sl] = valid ? bsrc[f2] : T(0);
-          } else {
-            bvvA[cc][0][sl] = BV[sl * L + x];
-            bvvA[cc][1][sl] = BV[sl * L + x2];
+          for (int sl = 0; sl < SLOTS; ++sl) {
+            // mirror rows of a 2-D orbit share the canonical slot's bins
+            const int f = row[sl] * L + x, f2 = row[sl] * L + x2;
+            if (PM == 2 && sl == 1 && f0) {
+              bn[1] = bn[0];
+              if (s == 0) bn2[1] = bn2[0];
+            } else {
+              bn[sl] = valid ? (int)__ldg(&bp[f]) : -1;
+              if (s == 0) bn2[sl] = (valid && sp) ? (int)__ldg(&bp[f2]) : bn[sl];
+            }
+            if (s != 0) bn2[sl] = bn[sl];
+            xvA[cc][0][sl] = valid ? __ldg(&xp[f]) : T(0);
+            xvA[cc][1][sl] = valid ? __ldg(&xp[f2]) : T(0);
+            if constexpr (DIRECT_BASE) {
+              bvvA[cc][0][sl] = valid ? bsrc[f] : T(0);
+              bvvA[cc][1][sl] = valid ? bsrc[f2] : T(0);
+            } else {
+              bvvA[cc][0][sl] = BV[sl * L + x];
+              bvvA[cc][1][sl] = BV[sl * L + x2];
+            }
           }
         }
-      }
 #pragma unroll
-      for (int cc = 0; cc < ECH; ++cc) {
-        const int s = s0 + cc;
-        const int x = t + T8 * s;
-        const bool sp = s == 0 && t0;
-        const int x2 = sp ? L / 2 : L - x;
-        const int(&bn)[SLOTS] = bnA[cc];
-        const int(&bn2)[SLOTS] = bn2A[cc];
-        T (&xv)[2][SLOTS] = xvA[cc];
-        T (&bvv)[2][SLOTS] = bvvA[cc];
-        T val[2][SLOTS];
-        if constexpr (PM == 2) {
-          T R[2][2], R2[2][2];
-          hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+        for (int cc = 0; cc < ECH; ++cc) {
+          const int s = s0 + cc;
+          const int x = t + T8 * s;
+          const bool sp = s == 0 && t0;
+          const int x2 = sp ? L / 2 : L - x;
+          const int(&bn)[SLOTS] = bnA[cc];
+          const int(&bn2)[SLOTS] = bn2A[cc];
+          T (&xv)[2][SLOTS] = xvA[cc];
+          T (&bvv)[2][SLOTS] = bvvA[cc];
+          T val[2][SLOTS];
+          if constexpr (PM == 2) {
+            T R[2][2], R2[2][2];
+            hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+            if (s == 0) {
+              hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 2; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
+            }
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+              val[0][sl] = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
+              val[1][sl] = half * (R2[sl][1] + pick2(R2, sl, f0, 1) + R2[sl][0] - pick2(R2, sl, f0, 0));
+            }
+          } else {
+            T R[4][2], R2[4][2];
+            hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
+            hartley_unpack<T>(v[1][s], zm[1][s], R[2], R[3]);
+            if (s == 0) {
+              hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
+              hartley_unpack<T>(sp ? v[1][4] : v[1][0], sp ? zm[1][4] : zm[1][0], R2[2], R2[3]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
+            }
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+              val[0][sl] = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
+                                   pick4(R, sl, f0, f1, 1));
+              val[1][sl] = half * (pick4(R2, sl, f0, false, 1) + pick4(R2, sl, false, f1, 1) + R2[sl][0] -
+                                   pick4(R2, sl, f0, f1, 0));
+            }
+          }
+          T c[2 * SLOTS];
+          int kb[2 * SLOTS];
+#pragma unroll
+          for (int sl = 0; sl < SLOTS; ++sl) {
+            const T o = (bn[sl] < 0 ? a0 : sA[bn[sl]]) * val[0][sl] + bvv[0][sl];
+            const T o2 = (bn2[sl] < 0 ? a0 : sA[bn2[sl]]) * val[1][sl] + bvv[1][sl];
+            if (valid) {
+              yo[row[sl] * L + x] = o;
+              yo[row[sl] * L + x2] = o2;
+              dsum += bvv[0][sl] * o;
+              dsum += bvv[1][sl] * o2;
+            }
+            c[sl] = xv[0][sl] * val[0][sl];
+            c[SLOTS + sl] = xv[1][sl] * val[1][sl];
+            kb[sl] = bn[sl];
+            kb[SLOTS + sl] = bn2[sl];
+          }
+          // the TAB epilogue always sums the bins
           if (s == 0) {
-            hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
+            add_slots<2 * SLOTS, T>(kb, c, whist);  // thread 0's second column has its own bins
           } else {
+            T cm[SLOTS];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
-          }
-#pragma unroll
-          for (int sl = 0; sl < 2; ++sl) {
-            val[0][sl] = half * (R[sl][0] + pick2(R, sl, f0, 0) + R[sl][1] - pick2(R, sl, f0, 1));
-            val[1][sl] = half * (R2[sl][1] + pick2(R2, sl, f0, 1) + R2[sl][0] - pick2(R2, sl, f0, 0));
-          }
-        } else {
-          T R[4][2], R2[4][2];
-          hartley_unpack<T>(v[0][s], zm[0][s], R[0], R[1]);
-          hartley_unpack<T>(v[1][s], zm[1][s], R[2], R[3]);
-          if (s == 0) {
-            hartley_unpack<T>(sp ? v[0][4] : v[0][0], sp ? zm[0][4] : zm[0][0], R2[0], R2[1]);
-            hartley_unpack<T>(sp ? v[1][4] : v[1][0], sp ? zm[1][4] : zm[1][0], R2[2], R2[3]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) R2[i][0] = R[i][0], R2[i][1] = R[i][1];
-          }
-#pragma unroll
-          for (int sl = 0; sl < 4; ++sl) {
-            val[0][sl] = half * (pick4(R, sl, f0, false, 0) + pick4(R, sl, false, f1, 0) + R[sl][1] -
-                                 pick4(R, sl, f0, f1, 1));
-            val[1][sl] = half * (pick4(R2, sl, f0, false, 1) + pick4(R2, sl, false, f1, 1) + R2[sl][0] -
-                                 pick4(R2, sl, f0, f1, 0));
+            for (int sl = 0; sl < SLOTS; ++sl) cm[sl] = c[sl] + c[SLOTS + sl];
+            add_slots<SLOTS, T>(bn, cm, whist);
           }
         }
-        T c[2 * SLOTS];
-        int kb[2 * SLOTS];
-#pragma unroll
-        for (int sl = 0; sl < SLOTS; ++sl) {
-          const T o = (bn[sl] < 0 ? a0 : sA[bn[sl]]) * val[0][sl] + bvv[0][sl];
-          const T o2 = (bn2[sl] < 0 ? a0 : sA[bn2[sl]]) * val[1][sl] + bvv[1][sl];
-          if (valid) {
-            yo[row[sl] * L + x] = o;
-            yo[row[sl] * L + x2] = o2;
-            dsum += bvv[0][sl] * o;
-            dsum += bvv[1][sl] * o2;
-          }
-          c[sl] = xv[0][sl] * val[0][sl];
-          c[SLOTS + sl] = xv[1][sl] * val[1][sl];
-          kb[sl] = bn[sl];
-          kb[SLOTS + sl] = bn2[sl];
-        }
-        // the TAB epilogue always sums the bins
-        if (s == 0) {
-          add_slots<2 * SLOTS, T>(kb, c, whist);  // thread 0's second column has its own bins
-        } else {
-          T cm[SLOTS];
-#pragma unroll
-          for (int sl = 0; sl < SLOTS; ++sl) cm[sl] = c[sl] + c[SLOTS + sl];
-          add_slots<SLOTS, T>(bn, cm, whist);
-        }
-      }
       }
       if (dot) dacc.add(dsum);
     } else {
