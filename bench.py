@@ -472,45 +472,73 @@ def run_ours(args, rank, world):
 
 
 def run_e2e(args, M, plan, xi_prime, eta, b, x, flush, stream, world, barrier):
-    """The same step through the public API with pinned host buffers: the
-    step's excitations are copied in and the samples copied out inside the
-    timed region."""
+    """The same step through the public API with pinned host buffers: every
+    step's excitations are copied in and its samples copied out inside the
+    timed region.  The copies run on a copy stream, pipelined with the compute
+    (the next step's inputs go in while this step solves, this step's samples
+    come out while the next one solves; device buffers alternate between two
+    steps), the way a caller streams batches through the API."""
     import torch
     B = xi_prime.shape[0]
     dev = xi_prime.device
     h_xi = torch.empty_like(xi_prime, device="cpu").pin_memory()
     h_eta = torch.empty_like(eta, device="cpu").pin_memory()
-    h_x = torch.empty_like(x, device="cpu").pin_memory()
+    h_x = [torch.empty_like(x, device="cpu").pin_memory() for _ in range(2)]
     h_xi.copy_(xi_prime)
     h_eta.copy_(eta)
-    d_xi = torch.empty_like(xi_prime)
-    d_eta = torch.empty_like(eta)
+    d_xi = [torch.empty_like(xi_prime) for _ in range(2)]
+    d_eta = [torch.empty_like(eta) for _ in range(2)]
+    d_x = [x, torch.empty_like(x)]
+    cs = torch.cuda.Stream(device=dev)
 
-    def e2e_step():
-        d_xi.copy_(h_xi, non_blocking=True)
-        d_eta.copy_(h_eta, non_blocking=True)
-        M.mgvi_rhs(d_xi, d_eta, out=b)
-        M.cg(b, rtol=0.0, maxiter=CG_ITERS, x=x)
-        h_x.copy_(x, non_blocking=True)
+    def run(n, e0=None):
+        """n pipelined steps on `stream` (compute) and `cs` (copies)."""
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = torch.cuda.Event()
 
-    e2e_step()
+        def put(k):  # inputs of step k into buffer k % 2 (after step k - 2 used it)
+            j = k % 2
+            with torch.cuda.stream(cs):
+                if k >= 2:
+                    cs.wait_event(ev_done[j])
+                d_xi[j].copy_(h_xi, non_blocking=True)
+                d_eta[j].copy_(h_eta, non_blocking=True)
+                ev_in[j].record(cs)
+
+        if e0 is not None:
+            cs.wait_event(e0)
+        put(0)
+        for k in range(n):
+            j = k % 2
+            if k + 1 < n:
+                put(k + 1)
+            stream.wait_event(ev_in[j])
+            M.mgvi_rhs(d_xi[j], d_eta[j], out=b)
+            M.cg(b, rtol=0.0, maxiter=CG_ITERS, x=d_x[j])
+            ev_done[j].record(stream)
+            with torch.cuda.stream(cs):
+                cs.wait_event(ev_done[j])
+                h_x[j].copy_(d_x[j], non_blocking=True)
+        ev_out.record(cs)
+        stream.wait_event(ev_out)
+
+    run(2)
     barrier()
-    e_steps = max(1, min(args.steps, 5))
-    ev = []
-    for _ in range(e_steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step()
-        e1.record(stream)
-        ev.append((e0, e1))
+    e_steps = max(2, min(args.steps, 5))
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run(e_steps, e0)
+    e1.record(stream)
     barrier()
-    e_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    e_ms = e0.elapsed_time(e1)
     e_t = max_over_ranks(e_ms / 1e3, world, dev)
     return {"value": replica_throughput(e_steps * B * CG_ITERS, world, e_t), "unit": UNIT,
             "h2d_bytes_per_step": int(h_xi.numel() * 4 + h_eta.numel() * 4),
-            "d2h_bytes_per_step": int(h_x.numel() * 4)}
+            "d2h_bytes_per_step": int(h_x[0].numel() * 4),
+            "pipelined": "copies on a second stream, overlapped with the neighbouring steps' solves"}
 
 
 # ----------------------------------------------------------------- metric roofline leg
