@@ -438,8 +438,9 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
       T dsum = T(0);
       // ECH column pairs per phase: all their loads go out before the first
       // is used (two pairs measured 0.6 % faster than one for FP32 2-D orbits
-      // of 512 points; one where two would spill more than a few bytes)
-      constexpr int ECH = (PM == 2 && sizeof(T) == 4 && L >= 128) ? 2 : 1;
+      // of 512 points and 4.5 % for 3-D orbits of 256; one where two would
+      // spill more than a few bytes)
+      constexpr int ECH = ((PM == 2 || PM == 3) && sizeof(T) == 4 && L >= 128) ? 2 : 1;
 #pragma unroll
       for (int s0 = 0; s0 < 4; s0 += ECH) {
         int bnA[ECH][SLOTS], bn2A[ECH][SLOTS];
