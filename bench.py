@@ -92,7 +92,7 @@ def parse():
 # averaged over the two variants (profiles/traffic_f32_2d_512x512_b32.md).
 DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.03e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                                     "half-batch launches x 2, mean of the two row sweeps",
-                                           "855353b07f19b7b1")}
+                                           "7cb204bde63f79b7")}
 
 # The sources that define the row sweeps' device code (the digest of
 # DRAM_TRAFFIC), the bulk-copy helpers of their row staging included; the C
