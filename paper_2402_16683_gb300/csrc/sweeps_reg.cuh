@@ -102,9 +102,11 @@ struct LineSync {
 // amplitude) into sA and the tangent's dA into sdA.  Returns whether the
 // prologue / epilogue should read them (*use_dA: the dA table).  Called by all
 // threads; a barrier must follow before use.
+// With zero_slot, also sA[-1] = the zero mode's amplitude and sdA[-1] = 0, so
+// that bin -1 (k = 0) indexes the tables like any other bin.
 template <typename T>
 __device__ __forceinline__ bool load_tables(const Pro<T>& pro, const Epi<T>& epi, int b, T* sA, T* sdA, int nb,
-                                            bool* use_dA) {
+                                            bool* use_dA, bool zero_slot = false) {
   const AmpView<T>& v = pro.mode == PRO_AMP ? pro.av : epi.av;
   *use_dA = false;
   if (v.abin == nullptr || (v.mode != AMPV_MODEL && v.mode != AMPV_PIX)) return false;
@@ -113,6 +115,10 @@ __device__ __forceinline__ bool load_tables(const Pro<T>& pro, const Epi<T>& epi
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     sA[i] = T(v.abin[b * v.astride + i]);
     if (dA) sdA[i] = T(pro.dA[b * pro.nb + i]);
+  }
+  if (zero_slot && threadIdx.x == 0) {
+    sA[-1] = v.a0t;
+    sdA[-1] = T(0);
   }
   *use_dA = dA;
   return true;
@@ -128,9 +134,10 @@ struct RowSmem {
   static constexpr int LNSZ = NU * LPU * rline(L) * 2;    // exchange lines (complex)
   static constexpr int STG = (XSZ > LNSZ ? XSZ : LNSZ);
   static constexpr int STGA = (STG + 3) / 4 * 4;          // 16-byte multiple
+  // the per-bin tables take 4 leading entries each (the zero mode at [-1])
   static size_t bytes(bool base, int nb, int nhist_bins) {
     return (size_t)2 * L * sizeof(T) + (size_t)2 * STGA * sizeof(T) + (base ? (size_t)XSZ * sizeof(T) : 0) +
-           (size_t)(2 * ((nb + 3) / 4 * 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(T);
+           (size_t)(2 * ((nb + 3) / 4 * 4 + 4)) * sizeof(T) + (size_t)nhist_bins * sizeof(T);
   }
 };
 
@@ -201,8 +208,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   const bool bstaged = sbase && !DIRECT_BASE;
   T* bstage = stage + 2 * SM::STGA;                          // [XSZ]: the current units' base rows
   const int nbp = (a.nb + 3) / 4 * 4;
-  T* sA = bstage + (bstaged ? SM::XSZ : 0);
-  T* sdA = sA + nbp;
+  T* sA = bstage + (bstaged ? SM::XSZ : 0) + 4;  // sA[-1], sdA[-1]: the zero mode (bin -1)
+  T* sdA = sA + nbp + 4;
   T* hist = sdA + nbp;  // warp-private per-bin sums in T (FP32: see warp_run_add)
   const bool bins = a.epi.mode == EPI_AMP && a.epi.bins;
   constexpr int NW = RowShape<L>::NW, WPU = T8 > 32 ? T8 / 32 : 1;  // warps, warps per unit
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
   const Epi<T>& epi = a.epi;
   load_twiddles<L>(tw, a.tw, a.log2Lmax - a.log2L);
   bool use_dA = false;
-  const bool use_tab = (PM != 1) && load_tables<T>(pro, epi, bsample, sA, sdA, a.nb, &use_dA);
+  const bool use_tab = (PM != 1) && load_tables<T>(pro, epi, bsample, sA, sdA, a.nb, &use_dA, true);
   const T* stab = use_tab ? sA : nullptr;
   const T* stdA = use_dA ? sdA : nullptr;
   if (bins)
@@ -376,8 +383,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int b_ = bn[q][h];
-            T val = (b_ < 0 ? a0 : sA[b_]) * X[(2 * q + h) * L + x];
-            if (b_ >= 0) val += sdA[b_] * xv[q][h];
+            T val = sA[b_] * X[(2 * q + h) * L + x];
+            val += sdA[b_] * xv[q][h];  // (sdA[-1] = 0)
             e[h] = sval[2 * q + h] ? val : T(0);
           }
           v[q][s] = cmake<C>(e[0], e[1]);
@@ -524,8 +531,8 @@ __global__ void __launch_bounds__(RowShape<L>::NT, row_min_ctas(RowShape<L>::NT,
           int kb[2 * SLOTS];
 #pragma unroll
           for (int sl = 0; sl < SLOTS; ++sl) {
-            const T o = (bn[sl] < 0 ? a0 : sA[bn[sl]]) * val[0][sl] + bvv[0][sl];
-            const T o2 = (bn2[sl] < 0 ? a0 : sA[bn2[sl]]) * val[1][sl] + bvv[1][sl];
+            const T o = sA[bn[sl]] * val[0][sl] + bvv[0][sl];  // (sA[-1] = a0)
+            const T o2 = sA[bn2[sl]] * val[1][sl] + bvv[1][sl];
             if (valid) {
               yo[row[sl] * L + x] = o;
               yo[row[sl] * L + x2] = o2;
