@@ -90,9 +90,9 @@ def parse():
 # 0.01 MB written, scaled by two (traffic grows with the samples; the shared
 # bin and expansion-point tables, 1.5 MB, are then counted twice) and
 # averaged over the two variants (profiles/traffic_f32_2d_512x512_b32.md).
-DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.03e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+DRAM_TRAFFIC = {("row_sweep_f32_2d", 32): (53.02e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                                     "half-batch launches x 2, mean of the two row sweeps",
-                                           "7cb204bde63f79b7")}
+                                           "7a55a704d9d23b42")}
 
 # The sources that define the row sweeps' device code (the digest of
 # DRAM_TRAFFIC), the bulk-copy helpers of their row staging included; the C
